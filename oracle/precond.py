@@ -1,0 +1,93 @@
+"""Block-circulant preconditioners and the Neumann series (Sections 2 and 3).
+
+P (heat) and R_BD2 (wave) are block circulant: P = I (x) A0 + Sigma (x) A1
+(+ Sigma^2 (x) A2 for BD2), the Kronecker form of Section 3, with Sigma the ell x ell cyclic
+down-shift, (Sigma x)_t = x_{t-1 mod ell} (the paper writes Sigma in
+R^{n x n}; its size is ell).  Sigma = U Lambda U^* with U the unitary DFT of
+size ell, U_{tk} = exp(+2 pi i t k / ell)/sqrt(ell), and Lambda_kk = w_k =
+exp(-2 pi i k/ell) (the printed U has lost the factor 2 and has n for ell).
+So the inverse of the diagonalised form in Section 3 reads P^{-1} = (U (x) I)[I (x) A0 + Lambda (x) A1]^{-1}(U^* (x) I).
+
+``circulant_inverse`` applies that formula in the order the paper gives it,
+with the dense U (Section 3, "method 1": each block row of (U (x) I) is a
+combination of all ell blocks), and a tridiagonal solve per frequency (the
+Thomas-algorithm step of Section 3, here LAPACK's banded LU).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .system import BlockSystem, constant_A0, neumann_E, solve_tridiag
+
+
+def fourier_matrix(ell: int) -> np.ndarray:
+    """Unitary U with U_{tk} = exp(2 pi i t k/ell)/sqrt(ell) (Section 3)."""
+    t = np.arange(ell)
+    return np.exp(2j * np.pi * np.outer(t, t) / ell) / np.sqrt(ell)
+
+
+def shift_eigenvalues(ell: int) -> np.ndarray:
+    """Diagonal of Lambda: Sigma = U Lambda U^*, w_k = exp(-2 pi i k/ell)."""
+    return np.exp(-2j * np.pi * np.arange(ell) / ell)
+
+
+def frequency_block(S: BlockSystem, w: complex):
+    """I (x) A0 + Lambda (x) A1 (+ Lambda^2 (x) A2) restricted to frequency w."""
+    B = constant_A0(S).astype(np.complex128)
+    for j, Aj in enumerate(S.lower, start=1):
+        B = B + (w ** j) * Aj
+    return B
+
+
+def circulant_inverse(S: BlockSystem, X: np.ndarray,
+                      transpose: bool = False) -> np.ndarray:
+    """Y = P^{-1} X (or P^{-T} X) by the diagonalised inverse of Section 3.
+
+    P^T = I (x) A0^T + Sigma^T (x) A1^T; the blocks are symmetric and
+    Sigma^T = U conj(Lambda) U^*, so the transpose uses conj(w_k).
+    """
+    ell = S.ell
+    U = fourier_matrix(ell)
+    w = shift_eigenvalues(ell)
+    if transpose:
+        w = np.conj(w)
+    Z = U.conj().T @ X.astype(np.complex128)       # (U^* (x) I) x
+    for k in range(ell):
+        Z[k] = solve_tridiag(frequency_block(S, w[k]), Z[k])
+    Y = U @ Z                                      # (U (x) I) y
+    return Y.real.copy()
+
+
+def dense_inverse_apply(C: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """Solve C y = x with a dense LU (tiny sizes; C from system.dense_*)."""
+    ell, n = X.shape
+    return np.linalg.solve(C, X.reshape(-1)).reshape(ell, n)
+
+
+def neumann_inverse(S: BlockSystem, X: np.ndarray, terms: int,
+                    transpose: bool = False) -> np.ndarray:
+    """Q_i^{-1} X with i = ``terms``, the Neumann approximation of Section 2:
+
+        Q_i^{-1} = sum_{m=0}^{i-1} (-1)^m P^{-1} ([sigma (x) K] P^{-1})^m.
+
+    E = sigma (x) kappa K is block diagonal and symmetric, so the transpose
+    is sum_m (-1)^m (P^{-T} E)^m P^{-T}, i.e. the same sum with P^{-T}
+    applied last.  terms = 1 gives P^{-1}.
+    """
+    if terms < 1:
+        raise ValueError("terms >= 1")
+    if not transpose:
+        total = np.zeros_like(X, dtype=np.float64)
+        W = X.astype(np.float64)
+        for m in range(terms):
+            PW = circulant_inverse(S, W)             # P^{-1} (E P^{-1})^m x
+            total += (-1.0) ** m * PW
+            W = neumann_E(S, PW)
+        return total
+    total = np.zeros_like(X, dtype=np.float64)
+    for m in range(terms):
+        V = circulant_inverse(S, X, transpose=True)   # P^{-T} x
+        for _ in range(m):
+            V = circulant_inverse(S, neumann_E(S, V), transpose=True)
+        total += (-1.0) ** m * V
+    return total
