@@ -1,0 +1,417 @@
+"""Benchmark: all-at-once heat solve, n = 4095, ell = 4096 (tau = 1/4096),
+8 seeded sine modes, FP64 flexible GMRES(30) to a true relative residual of
+1e-10 with the FP32 block-circulant preconditioner (the mixed form), timed on
+GB300 next to the all-FP64 form.
+
+One step = one complete solve of A U = b (right-hand side already resident
+in HBM): the FP32 circulant applies (time FFT, per-frequency tridiagonal
+solves, inverse FFT), the FP64 matvecs, the Arnoldi kernels and the true
+residual.  `value` is seconds per solve (max over ranks).  Extra keys report
+the preconditioner apply's HBM throughput against the measured peak, the
+all-FP64 solve time, a roofline for the dominant kernel, the CPU oracle on
+the host cores, an end-to-end solve through host buffers, and the SM clocks
+sampled during the timed region.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "all-at-once solve s & precond-apply HBM GB/s, mixed vs FP64 at 1e-10 residual"
+N_SPACE, ELL = 4095, 4096
+RESTART, RTOL, MAXIT = 30, 1e-10, 300
+WORKLOAD = "heat1d_p1_implicit_euler_n4095_ell4096_8modes_fgmres30_rtol1e-10"
+L2_BYTES = 135528448
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons (read-only)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower() in ("active", "yes", "1"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- helpers
+def _dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _barrier(dist_on):
+    if dist_on:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(val, dist_on, device):
+    if not dist_on:
+        return val
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([val], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_solve_seconds():
+    """The CPU oracle's own solve of the same system: right-preconditioned
+    GMRES(30) with the exact circulant applied by the dense DFT (the paper's
+    method 1) and banded LU per frequency, FP64, to 1e-10.  One full solve is
+    the sample (tens of seconds on the host cores)."""
+    import synthetic as syn
+    from oracle import gmres, precond, system
+    S = system.heat(N_SPACE, ELL, 1.0 / ELL)
+    u0 = syn.heat_initial(N_SPACE, modes=8)
+    B = system.rhs_heat(S, u0)
+    t0 = time.perf_counter()
+    _, info = gmres.gmres(lambda v: system.matvec(S, v), B,
+                          apply_P=lambda v: precond.circulant_inverse(S, v),
+                          restart=RESTART, rtol=RTOL, side="right")
+    return time.perf_counter() - t0, info
+
+
+def _blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max((d.get("num_threads", 1) for d in threadpool_info()), default=1)
+    except Exception:
+        return _cpu_cores()
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args):
+    world, rank, _ = _dist_env()
+    if rank != 0:
+        return 0
+    times = []
+    info = None
+    for _ in range(args.warmup):
+        _oracle_solve_seconds()
+    for _ in range(args.steps):
+        dt, info = _oracle_solve_seconds()
+        times.append(dt)
+    v = float(np.mean(times))
+    cores = _blas_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * v, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_SPACE, "ell": ELL, "restart": RESTART,
+                   "rtol": RTOL},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
+                         "sample": "one full solve per step: oracle right-preconditioned "
+                                   "GMRES(30), dense-DFT circulant, FP64"},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "iters": info.iters if info else None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    import synthetic as syn
+    from paper_1810_00615_gb300 import AllAtOnce
+    from paper_1810_00615_gb300._capi import KERNEL_CLASSES
+
+    world, rank, local = _dist_env()
+    dist_on = world > 1
+    if dist_on:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    hbm_peak, peak_kind = _peaks()
+
+    u0 = syn.heat_initial(N_SPACE, modes=8)
+    solver = AllAtOnce(N_SPACE, ELL, 1.0 / ELL, precision="fp32", restart=RESTART,
+                       device=device)
+    u0_d = torch.from_numpy(u0).to(device)
+    b = solver.build_rhs(u0_d)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream()
+
+    def step(prec):
+        solver.set_precision(prec)
+        x, info = solver.solve(b, restart=RESTART, rtol=RTOL, maxit=MAXIT, precond=1)
+        return x, info
+
+    for _ in range(max(args.warmup, 1)):
+        step("fp32")
+    torch.cuda.synchronize()
+
+    # ---- timed region: K mixed-precision solves
+    clocks = ClockSampler(torch.cuda.current_device() if not os.environ.get(
+        "CUDA_VISIBLE_DEVICES") else int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local]))
+    clocks.start()
+    launches0 = solver.kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    infos = []
+    _barrier(dist_on)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))                      # L2 flush outside the step's events
+        ev[k][0].record(stream)
+        x, info = step("fp32")
+        ev[k][1].record(stream)
+        infos.append(info)
+    torch.cuda.synchronize()
+    _barrier(dist_on)
+    wall = time.perf_counter() - wall0
+    launches = solver.kernel_launches() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b_) for a, b_ in ev]
+    ms = float(np.mean(step_ms))
+    ms = _max_over_ranks(ms, dist_on, device)
+    value = ms / 1e3
+
+    # accuracy of the last solve (device-side check against the FP64 matvec)
+    r = b - solver.matvec(x)
+    relres = float(torch.linalg.norm(r) / torch.linalg.norm(b))
+
+    # ---- the all-FP64 form (same solve, FP64 preconditioner)
+    step("fp64")
+    torch.cuda.synchronize()
+    t64 = []
+    it64 = None
+    for k in range(max(1, min(args.steps, 3))):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, inf64 = step("fp64")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64.append(e0.elapsed_time(e1))
+        it64 = inf64["iters"]
+    solver.set_precision("fp32")
+
+    # ---- per-kernel profile of K more mixed solves (events around each kernel)
+    solver.profile_read(reset=True)
+    solver.profile(True)
+    nprof = max(1, min(args.steps, 3))
+    for k in range(nprof):
+        flush.fill_(float(k))
+        step("fp32")
+    torch.cuda.synchronize()
+    prof = solver.profile_read(reset=True)
+    solver.profile(False)
+
+    # ---- preconditioner apply throughput (FP32), inputs larger than L2
+    xs = [torch.randn(ELL, N_SPACE, dtype=torch.float64, device=device) for _ in range(2)]
+    ys = [torch.empty_like(xs[0]) for _ in range(2)]
+    for i in range(3):
+        solver.precond_apply(xs[i % 2], out=ys[i % 2])
+    napp = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    solver.profile_read(reset=True)
+    solver.profile(True)
+    e0.record(stream)
+    for i in range(napp):
+        solver.precond_apply(xs[i % 2], out=ys[i % 2])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    app_prof = solver.profile_read(reset=True)
+    solver.profile(False)
+    apply_ms = e0.elapsed_time(e1) / napp
+    nk = ELL // 2 + 1
+    Nel = N_SPACE * ELL
+    spec_bytes = 8 * N_SPACE * nk                       # complex64 half spectrum
+    bytes_apply = (8 * Nel + spec_bytes) + 2 * spec_bytes + (spec_bytes + 8 * Nel)
+    apply_gbs = bytes_apply / (apply_ms * 1e-3) / 1e9
+
+    # per-kernel algorithmic bytes (per launch) for the preconditioner stages
+    k_bytes = {"fft_forward": 8 * Nel + spec_bytes, "tridiag": 2 * spec_bytes,
+               "fft_inverse": spec_bytes + 8 * Nel}
+    per_kernel = {}
+    for name in ("fft_forward", "tridiag", "fft_inverse"):
+        t_ms, nl = app_prof[name]
+        if nl:
+            avg = t_ms / nl
+            gbs = k_bytes[name] / (avg * 1e-3) / 1e9
+            per_kernel[name] = {"us": round(1e3 * avg, 2), "GB_s": round(gbs, 1),
+                                "frac": round(gbs / hbm_peak, 3)}
+
+    # dominant kernel class of the solve profile
+    total_prof = sum(v[0] for v in prof.values()) or 1.0
+    shares = {k: round(v[0] / total_prof, 3) for k, v in prof.items()}
+    dom = max(prof, key=lambda k: prof[k][0])
+
+    if dom in per_kernel:
+        pk = per_kernel[dom]
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": pk["GB_s"], "peak": hbm_peak,
+                    "unit": "GB/s", "frac": pk["frac"], "traffic": None,
+                    "peak_kind": peak_kind}
+    else:
+        # FP64 kernels of the outer loop: report bytes against HBM and FP64 ops
+        # against the FP64 issue rate (2 per clock per SM, 152 SMs)
+        t_ms, nl = prof[dom]
+        avg_s = t_ms / max(nl, 1) / 1e3
+        sm_mhz = clk.get("sm_mhz") or 2070.0
+        fp64_peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12      # TFLOP/s (FMA = 2 flops)
+        flops_per_launch = {"matvec": 14 * Nel}.get(dom)
+        roofline = {"bound": "alu", "kernel": dom,
+                    "achieved": (flops_per_launch / avg_s / 1e12) if flops_per_launch else None,
+                    "peak": round(fp64_peak, 3), "unit": "TFLOP/s",
+                    "frac": (flops_per_launch / avg_s / 1e12 / fp64_peak)
+                    if flops_per_launch else None, "traffic": None,
+                    "note": "FP64 pipe bound; peak = 152 SMs x 2 DFMA/clk x sampled SM clock"}
+
+    # ---- end to end through the C ABI with host buffers (u0 in, U out)
+    u0_h = torch.from_numpy(u0).pin_memory()
+    U_h = torch.empty(ELL, N_SPACE, dtype=torch.float64).pin_memory()
+    solver.solve_host(u0_h, out=U_h, restart=RESTART, rtol=RTOL)
+    torch.cuda.synchronize()
+    e2e = []
+    for k in range(max(1, min(args.steps, 3))):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, inf_h = solver.solve_host(u0_h, out=U_h, restart=RESTART, rtol=RTOL)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    e2e_v = _max_over_ranks(float(np.mean(e2e)), dist_on, device)
+
+    # ---- CPU oracle on the host cores (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        dt, cinfo = _oracle_solve_seconds()
+        cpu = {"value": dt, "unit": "s", "cores": _blas_threads(), "kind": "oracle",
+               "sample": "one full solve of the same workload: oracle right-preconditioned "
+                         f"GMRES(30), dense-DFT circulant, FP64 ({cinfo.iters} iterations)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_SPACE, "ell": ELL, "restart": RESTART,
+                       "rtol": RTOL, "preconditioner": "fp32 circulant",
+                       "parallelism": f"replicas{world}",
+                       "l2": "256 MiB buffer written before every step, outside its events"},
+            "iters": infos[-1]["iters"], "relres_true": relres,
+            "fp64_solve_s": float(np.mean(t64)) / 1e3, "fp64_iters": it64,
+            "speedup_mixed_vs_fp64": float(np.mean(t64)) / ms,
+            "precond_apply": {"us": round(1e3 * apply_ms, 2), "GB_s": round(apply_gbs, 1),
+                              "frac_of_hbm": round(apply_gbs / hbm_peak, 3),
+                              "bytes": bytes_apply, "peak_GB_s": hbm_peak,
+                              "peak_kind": peak_kind, "kernels": per_kernel},
+            "kernel_share": shares, "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_v, "unit": "s", "h2d_bytes_per_step": 8 * N_SPACE,
+                    "d2h_bytes_per_step": 8 * Nel},
+            "gpu_launches": launches, "wall_s": wall, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist_on:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,214 @@
+/*
+ * aao.h -- C ABI of the GB300 all-at-once solver.
+ *
+ * The library solves the all-at-once ("monolithic") system A U = b of
+ * Goddard & Wathen, "A note on parallel preconditioning for all-at-once
+ * evolutionary PDEs", Section 2, for
+ *   - the 1D heat equation, P1 finite elements in space and implicit Euler in
+ *     time (block lower-bidiagonal A with A0 = M + tau*kappa*K, A1 = -M, or
+ *     per-step A0^t = M + tau_t*kappa*K for the variable-step system B), and
+ *   - the 1D wave equation with the BD2 scheme (three block bands,
+ *     A0 = M + tau^2 K, A1 = -2M, A2 = M),
+ * by flexible GMRES preconditioned with the McDonald-Pestana-Wathen block
+ * circulant P (Section 2; R_BD2 for the wave equation) or its Neumann-series
+ * extension Q_i^{-1} (Section 2).  P^{-1} is applied through its Fourier
+ * diagonalisation (Section 3): a real FFT along the time axis, one complex
+ * tridiagonal solve per frequency, an inverse FFT.
+ *
+ * Conventions shared by every entry point:
+ *   - n   = number of interior spatial nodes (h = 1/(n+1)); ell = number of
+ *           time steps.  N = n*ell.
+ *   - A block vector is a device array of N doubles in time-block-major
+ *     layout: element (t, i) at offset t*n + i, t = 0..ell-1 holding u_{t+1}.
+ *   - Vectors are owned by the caller; the library never frees them.  Input
+ *     and output vectors must not overlap (AAO_EINVAL).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Apply and matvec calls are asynchronous on that stream;
+ *     the solve calls synchronise it before they return.
+ *   - Status codes: 0 success; > 0 the result was written but did not meet
+ *     the request; < 0 an error, nothing meaningful was written.
+ *   - A context is not thread-safe; use one per host thread.
+ *   - No call spins on device memory; no kernel waits on another.
+ */
+#ifndef AAO_H
+#define AAO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct aao_ctx aao_ctx;
+
+/* Equations (Section 2).
+ * AAO_HEAT          implicit Euler, A0 = M + tau*kappa*K, A1 = -M.  The
+ *                   paper prints A0 = K + tau*M; that is not implicit Euler
+ *                   for M u' = -K u and contradicts its splitting
+ *                   Q = P + sigma (x) K, so the time step multiplies K here.
+ * AAO_WAVE_BD2      BD2 for M u'' = -K u: A0 = M + tau^2 K, A1 = -2M, A2 = M.
+ * AAO_HEAT_LITERAL  the printed blocks A0 = K + tau*M, A1 = -M (kept to show
+ *                   the difference; kappa is ignored). */
+enum { AAO_HEAT = 0, AAO_WAVE_BD2 = 1, AAO_HEAT_LITERAL = 2 };
+
+/* Arithmetic of the preconditioner (FFTs and tridiagonal solves).  The outer
+ * GMRES, the matvec and the true residual are FP64 in both cases. */
+enum { AAO_PREC_FP64 = 0, AAO_PREC_FP32 = 1 };
+
+enum {
+  AAO_OK = 0,
+  AAO_ENOCONV = 1,      /* solve: max iterations reached, best iterate written */
+  AAO_EINVAL = -1,      /* bad argument, aliasing, missing workspace          */
+  AAO_ENOMEM = -2,      /* host or device allocation failed in create         */
+  AAO_ECUDA = -3,       /* a CUDA call failed; aao_last_error has the text    */
+  AAO_ENUMERIC = -4,    /* non-finite residual or breakdown with no progress  */
+  AAO_EUNSUPPORTED = -5 /* shape not supported (e.g. ell not a power of 2)    */
+};
+
+/* Solve statistics.  `history` (caller-owned host array of history_cap
+ * doubles, may be NULL) receives the estimated relative residual after each
+ * Arnoldi step. */
+typedef struct {
+  int iters;            /* Arnoldi steps = products with A                   */
+  int restarts;         /* outer cycles (each recomputes b - A x in FP64)    */
+  double relres_true;   /* ||b - A x||_2 / ||b||_2 at return, FP64           */
+  double relres_est;    /* last GMRES estimate |g_{j+1}| / ||b||             */
+  double *history;
+  int history_cap;
+  int history_len;
+} aao_solve_info;
+
+/* Create a context for an n x ell all-at-once system with constant step tau
+ * (Section 2; tau = T/ell with T = 1 in the paper).  ell must be a power of
+ * two, 1 <= ell <= 4096; 1 <= n <= 16383.  Computes the per-frequency
+ * tridiagonal symbols A0 + w_k A1 (+ w_k^2 A2), w_k = exp(-2 pi i k/ell),
+ * k = 0..ell/2 (Section 3, Fourier diagonalisation of P), in FP64 on the
+ * host and uploads them; the context owns that device memory.
+ * Defaults: kappa = 1, uniform steps, AAO_PREC_FP32.
+ * Errors: AAO_EINVAL (n < 1, tau <= 0, bad equation, out == NULL),
+ * AAO_EUNSUPPORTED (ell), AAO_ENOMEM, AAO_ECUDA. */
+int aao_create(int64_t n, int64_t ell, double tau, int equation, aao_ctx **out);
+
+/* Destroy a context (frees the symbols; never the caller's workspace). */
+void aao_destroy(aao_ctx *ctx);
+
+/* Diffusion coefficient kappa > 0 of the heat equation (A0 = M + tau kappa K).
+ * Recomputes the symbols.  AAO_EINVAL for the wave equation or kappa <= 0. */
+int aao_set_kappa(aao_ctx *ctx, double kappa);
+
+/* Variable steps tau_1..tau_ell (host array of ell positive doubles): the
+ * system becomes B of Section 2 (A0^t = M + tau_t kappa K), the
+ * preconditioner stays P with the constant tau given at create, and the
+ * Neumann terms use E = sigma (x) kappa K, sigma_t = tau_t - tau (Section 2).
+ * NULL restores uniform steps.  Heat only (AAO_EINVAL otherwise). */
+int aao_set_steps(aao_ctx *ctx, const double *tau_steps_host);
+
+/* AAO_PREC_FP32 or AAO_PREC_FP64 for the preconditioner. */
+int aao_set_precision(aao_ctx *ctx, int prec);
+
+/* Bytes of device workspace that the solve calls need for GMRES(restart)
+ * (restart >= 1).  The apply calls need aao_workspace_bytes(ctx, 0). */
+size_t aao_workspace_bytes(const aao_ctx *ctx, int restart);
+
+/* Hand the context a caller-allocated device workspace (256-byte aligned,
+ * at least aao_workspace_bytes bytes for the restart lengths used later).
+ * The caller keeps ownership and must keep it alive while the context uses
+ * it.  AAO_EINVAL on NULL or misalignment. */
+int aao_set_workspace(aao_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* y = P^{-1} x (transpose = 0) or P^{-T} x (transpose = 1), Section 3:
+ * P^{-1} = (U (x) I)[I (x) A0 + Lambda (x) A1]^{-1}(U^* (x) I).  P^T is
+ * diagonalised by the same DFT with conj(w_k).  Runs a real FFT along the
+ * time axis, ell/2+1 complex tridiagonal solves and the inverse FFT, in the
+ * context's precision.  For the wave equation P is R_BD2.  Needs the
+ * workspace.  x, y: device, N doubles, no overlap. */
+int aao_precond_apply(aao_ctx *ctx, const double *x, double *y, int transpose,
+                      void *stream);
+
+/* y = Q_i^{-1} x with i = terms >= 1 (Section 2, Neumann approximation of the
+ * inverse of Q = P + sigma (x) K), evaluated in Horner form
+ * y_0 = P^{-1} x, y_m = P^{-1}(x - E y_{m-1}); the residual x - E y is fused
+ * into the forward FFT's load.  transpose = 1 gives Q_i^{-T} by the same
+ * recursion with P^{-T}.  With uniform steps E = 0 and every term equals
+ * P^{-1} x. */
+int aao_neumann_apply(aao_ctx *ctx, int terms, const double *x, double *y,
+                      int transpose, void *stream);
+
+/* y = A x (transpose = 0) or A^T x (transpose = 1) in FP64 (Section 2; the
+ * monolithic matrix is never formed).  Heat: y_t = M(x_t - x_{t-1}) +
+ * tau_t kappa K x_t; BD2: y_t = M(x_t - 2x_{t-1} + x_{t-2}) + tau^2 K x_t;
+ * the transpose shifts the other way.  No workspace needed. */
+int aao_matvec(aao_ctx *ctx, const double *x, double *y, int transpose,
+               void *stream);
+
+/* Right-hand side from initial data (Section 2): heat b = [M u0; 0; ...];
+ * BD2 b = [A0 (u0 + tau v0); -M u0; 0; ...] (v0 may be NULL = at rest, which
+ * is the paper's b_BD2).  u0, v0: device, n doubles; b: device, N doubles. */
+int aao_build_rhs(aao_ctx *ctx, const double *u0, const double *v0, double *b,
+                  void *stream);
+
+/* Solve A x = b by flexible GMRES(restart), right-preconditioned, FP64
+ * Arnoldi with classical Gram-Schmidt and re-orthogonalisation, Givens
+ * rotations on the host, the true residual recomputed in FP64 at every
+ * restart.  precond: 0 none, 1 the circulant P (R_BD2), i >= 2 the Neumann
+ * series Q_i^{-1}.  Stops when ||b - A x|| <= rtol ||b|| (true residual) or
+ * after maxit Arnoldi steps (AAO_ENOCONV, x holds the last iterate).  x is
+ * the initial guess on entry.  info may be NULL.  Needs
+ * aao_workspace_bytes(ctx, restart) of workspace.  Synchronises `stream`. */
+int aao_gmres_solve(aao_ctx *ctx, const double *b, double *x, int restart,
+                    double rtol, int maxit, int precond, aao_solve_info *info,
+                    void *stream);
+
+/* Solve A^T lambda = g (the adjoint system; block upper-triangular) by the
+ * same flexible GMRES with the transposed preconditioner P^{-T} (or
+ * Q_i^{-T}).  Not in the paper; used for gradients of a loss of U. */
+int aao_adjoint_solve(aao_ctx *ctx, const double *g, double *lambda, int restart,
+                      double rtol, int maxit, int precond, aao_solve_info *info,
+                      void *stream);
+
+/* Gradients of a loss L(U) through A(kappa) U = [M u0; 0; ...] (heat only),
+ * given the adjoint lambda = A^{-T} dL/dU and the solution U:
+ *   g_u0[i]  = (M lambda_1)_i                       (device, n doubles)
+ *   *g_kappa = -sum_t tau_t lambda_t^T K u_t         (host double)
+ * Synchronises `stream`. */
+int aao_adjoint_grads(aao_ctx *ctx, const double *lambda, const double *U,
+                      double *g_u0, double *g_kappa, void *stream);
+
+/* End-to-end solve through host memory: copies u0 (and v0, may be NULL) from
+ * host to device, builds b, solves A U = b from U = 0 with flexible
+ * GMRES(restart) as aao_gmres_solve, and copies U (N doubles) back to the
+ * host array U_host.  Page-locked host buffers give the fastest copies.
+ * Uses two extra device vectors of the workspace (included in
+ * aao_workspace_bytes).  Synchronises `stream`. */
+int aao_solve_host(aao_ctx *ctx, const double *u0_host, const double *v0_host,
+                   double *U_host, int restart, double rtol, int maxit,
+                   int precond, aao_solve_info *info, void *stream);
+
+/* Kernel classes for aao_profile_read: the three stages of a preconditioner
+ * apply, the matvec, and the Arnoldi kernels. */
+enum {
+  AAO_K_FFT_FORWARD = 0, AAO_K_TRIDIAG = 1, AAO_K_FFT_INVERSE = 2, AAO_K_MATVEC = 3,
+  AAO_K_DOTS = 4, AAO_K_UPDATE = 5, AAO_K_COMBINE = 6, AAO_K_OTHER = 7, AAO_K_COUNT = 8
+};
+
+/* Profiling (not in the paper): while on != 0 every kernel the context
+ * launches is bracketed by two CUDA events on its stream.  aao_profile_read
+ * waits for the recorded events, adds their durations per class to ms[8]
+ * (milliseconds) and the number of kernel launches per class to launches[8]
+ * (either may be NULL), and clears the totals if reset != 0.  Launches are
+ * counted whether or not timing is on. */
+int aao_profile_enable(aao_ctx *ctx, int on);
+int aao_profile_read(aao_ctx *ctx, double *ms, int64_t *launches, int reset);
+
+/* Total kernel launches made through this context since it was created. */
+int64_t aao_kernel_launches(const aao_ctx *ctx);
+
+/* Text for a status code, and the last CUDA error seen by ctx ("" if none). */
+const char *aao_strerror(int status);
+const char *aao_last_error(const aao_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AAO_H */

@@ -20,6 +20,21 @@ import numpy as np
 from .system import BlockSystem, constant_A0, neumann_E, solve_tridiag
 
 
+def circulant_matvec(S: BlockSystem, X: np.ndarray, transpose: bool = False) -> np.ndarray:
+    """Y = P X (or P^T X) from the definition of the block circulant
+    (Section 2): (P x)_t = A0 x_t + sum_j A_j x_{(t - j) mod ell}; the
+    transpose takes x_{(t + j) mod ell} (all blocks are symmetric)."""
+    A0 = constant_A0(S)
+    Y = np.empty_like(X, dtype=np.float64)
+    for t in range(S.ell):
+        y = A0 @ X[t]
+        for j, Aj in enumerate(S.lower, start=1):
+            src = (t + j) % S.ell if transpose else (t - j) % S.ell
+            y = y + Aj @ X[src]
+        Y[t] = y
+    return Y
+
+
 def fourier_matrix(ell: int) -> np.ndarray:
     """Unitary U with U_{tk} = exp(2 pi i t k/ell)/sqrt(ell) (Section 3)."""
     t = np.arange(ell)

@@ -1,0 +1,203 @@
+// Internal declarations of the GB300 all-at-once solver (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <string>
+#include <vector>
+
+#include "../../include/aao.h"
+
+namespace aao {
+
+// Kernel launches made by the calling host thread (every launch site bumps
+// it); the context turns deltas into per-class counts.
+extern thread_local int64_t tl_launches;
+inline void note_launch() { ++tl_launches; }
+
+// ------------------------------------------------------------------ complex
+template <typename R>
+struct __align__(2 * sizeof(R)) cx {
+  R re, im;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> mk(R a, R b) { cx<R> z; z.re = a; z.im = b; return z; }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return mk(s * a.re, s * a.im); }
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> conjx(cx<R> a) { return mk(a.re, -a.im); }
+// a - b*c
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> cfnms(cx<R> a, cx<R> b, cx<R> c) {
+  return mk(a.re - b.re * c.re + b.im * c.im, a.im - b.re * c.im - b.im * c.re);
+}
+// a + b*c
+template <typename R>
+__host__ __device__ __forceinline__ cx<R> cfma(cx<R> a, cx<R> b, cx<R> c) {
+  return mk(a.re + b.re * c.re - b.im * c.im, a.im + b.re * c.im + b.im * c.re);
+}
+
+// ------------------------------------------------- precision conversions
+// On this part the FP64<->FP32 conversion instructions issue at the FP64
+// rate (2 per clock per SM), as slow as a DFMA.  The FP32 preconditioner
+// converts every element twice, so the two directions are done here with
+// 32-bit integer operations, which issue at the full rate.  Both are exact
+// re-implementations of IEEE-754 round-to-nearest-even (double -> float) and
+// of the exact widening (float -> double) for normal numbers and zeros; the
+// rare subnormal, infinite and NaN inputs fall back to the hardware
+// conversion.
+__device__ __forceinline__ float to_f32(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  const unsigned sign = hi & 0x80000000u;
+  if (e == 0u) return __uint_as_float(sign);          // zero or FP64 subnormal
+  if (e - 897u > 253u) return __double2float_rn(x);   // outside FP32 normals
+  unsigned bits = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;              // 29 dropped bits
+  bits += (rem > 0x10000000u) | ((rem == 0x10000000u) & (bits & 1u));
+  return __uint_as_float(sign | bits);
+}
+
+__device__ __forceinline__ double to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e - 1u > 253u) {                                // zero, subnormal, inf, NaN
+    if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return (double)f;
+  }
+  const unsigned hi = (u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + (896u << 20));
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+template <typename R> __device__ __forceinline__ R from_f64(double x);
+template <> __device__ __forceinline__ float from_f64<float>(double x) { return to_f32(x); }
+template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
+template <typename R> __device__ __forceinline__ double to_double(R x);
+template <> __device__ __forceinline__ double to_double<float>(float x) { return to_f64(x); }
+template <> __device__ __forceinline__ double to_double<double>(double x) { return x; }
+
+// ------------------------------------------------- per-frequency tables
+// Tridiagonal solve of one frequency block T_k = tridiag(e, d, e), n x n,
+// stored by its row excess sigma = d + 2e and off-diagonal e (Section 3: one
+// tridiagonal system per frequency).  The row is cut into chunks of CH-1
+// unknowns separated by single "separator" unknowns; chunks are solved
+// locally (Thomas with the shared pivots of the constant-coefficient chunk),
+// the separators form a smaller tridiagonal system (Schur complement) solved
+// by cyclic reduction, and each chunk is corrected with its Green's
+// functions.  Everything here is per frequency k and RHS-independent, so the
+// host computes it once in FP64.
+template <typename R, int CH>
+struct TriTab {
+  cx<R> invp[CH];   // 1/p_i, pivots of the chunk LU (prefix-shared by all sizes)
+  cx<R> bp[CH];     // e/p_i
+  cx<R> fc[CH];     // -e * (T_c^{-1} e_1)_i, regular chunk size c = CH-1
+  cx<R> fl[CH];     // -e * (T_cl^{-1} e_1)_i, last chunk size cl
+  cx<R> e;          // off-diagonal
+  cx<R> sig_reg, off_reg;    // separator rows with regular chunks on both sides
+  cx<R> sig_last, off_last;  // last separator row (regular | last chunk)
+};
+
+// ------------------------------------------------------------ context
+struct Ctx {
+  int64_t n = 0, ell = 0, N = 0;
+  double tau = 0, kappa = 1.0, h = 0;
+  int equation = AAO_HEAT;
+  int prec = AAO_PREC_FP32;
+  bool variable_steps = false;
+  std::vector<double> taus;          // per-step tau (variable steps)
+  int device = 0;
+
+  // spectrum layout
+  int64_t nk = 0;        // ell/2 + 1 frequencies stored
+  int64_t n_pad = 0;     // row stride of the spectrum (elements)
+  int ch32 = 16, ch64 = 8;   // chunk lengths of the tridiagonal kernels
+  int P32 = 1, P64 = 1;      // chunks per row
+
+  // device-side constants (owned)
+  void *tab32 = nullptr;   // TriTab<float, ch32>[nk]; the transposed symbols are their conjugates
+  void *tab64 = nullptr;   // TriTab<double, ch64>[nk]
+  cx<float> *tw32 = nullptr;      // exp(-2 pi i m/ell), m < ell
+  cx<double> *tw64 = nullptr;
+  double *beta = nullptr;         // per-step K coefficient of the matvec (ell)
+  double *sigk = nullptr;         // per-step Neumann coefficient (tau_t - tau) kappa / h
+  float *sigk32 = nullptr;
+  double *host_small = nullptr;   // pinned host scratch for small results (1024 doubles)
+
+  // caller workspace
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+
+  std::string last_error;
+
+  // launch counts and (optional) CUDA-event timing per kernel class
+  int64_t launches[AAO_K_COUNT] = {0};
+  double prof_ms[AAO_K_COUNT] = {0};
+  bool prof_on = false;
+  struct Pending { int cls; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+// Workspace layout (offsets in bytes from ws, each 256-byte aligned).
+struct WsLayout {
+  size_t spec = 0, spec_bytes = 0;
+  size_t red = 0, red_bytes = 0;
+  size_t vecs = 0;        // first FP64 vector (V_0 ...)
+  size_t vec_bytes = 0;   // bytes per vector (rounded)
+  size_t total = 0;
+};
+WsLayout ws_layout(const Ctx &c, int restart);
+
+// ------------------------------------------------------------ launchers
+// All return cudaGetLastError() of the launch.
+// Time-axis FFTs: x (and, for a Neumann term, the previous iterate y) ->
+// half spectrum; half spectrum -> y.  One instantiation per precision.
+cudaError_t fft_forward_f32(const Ctx &c, const double *x, const double *yprev, void *spec,
+                            cudaStream_t s);
+cudaError_t fft_inverse_f32(const Ctx &c, const void *spec, double *y, cudaStream_t s);
+cudaError_t fft_forward_f64(const Ctx &c, const double *x, const double *yprev, void *spec,
+                            cudaStream_t s);
+cudaError_t fft_inverse_f64(const Ctx &c, const void *spec, double *y, cudaStream_t s);
+cudaError_t launch_tridiag(const Ctx &c, void *spec, int prec, int transpose,
+                           cudaStream_t s);
+cudaError_t launch_matvec(const Ctx &c, const double *x, double *y, int transpose,
+                          cudaStream_t s);
+cudaError_t launch_rhs(const Ctx &c, const double *u0, const double *v0, double *b,
+                       cudaStream_t s);
+
+// Arnoldi / BLAS-1 on FP64 vectors of length N.
+// dots: out[j] = <V_j, w> for j < nv, plus out[nv] = <w, w> if with_norm.
+// Uses `red` (device scratch of at least red_bytes) for block partials and
+// writes the final sums to out (device).
+int  red_blocks(int64_t N);
+cudaError_t launch_multidot(const double *const *V, int nv, const double *w, int64_t N,
+                            bool with_norm, double *partials, double *out, cudaStream_t s);
+// w -= sum_j h[j] V_j (h on device); optionally fused: dots of the updated w
+// with V_j (out2[j]) and its squared norm (out2[nv]).
+cudaError_t launch_update_dots(const double *const *V, int nv, const double *h,
+                               double *w, int64_t N, bool want_dots, double *partials,
+                               double *out2, cudaStream_t s);
+// x += sum_j y[j] Z_j (y on device)
+cudaError_t launch_combine(const double *const *Z, int nv, const double *y, double *x,
+                           int64_t N, cudaStream_t s);
+// y = a*x (a on device, *a_scale of index)
+cudaError_t launch_scale(const double *x, double *y, const double *a, int64_t N,
+                         bool invert, cudaStream_t s);
+// r = b - r (in place on r)
+cudaError_t launch_sub_from(const double *b, double *r, int64_t N, cudaStream_t s);
+cudaError_t launch_adjoint_grads(const Ctx &c, const double *lam, const double *U,
+                                 double *g_u0, double *partials, double *out,
+                                 cudaStream_t s);
+
+}  // namespace aao

@@ -1,0 +1,414 @@
+// FP64 kernels of the outer Krylov loop: the all-at-once matvec (Section 2,
+// the monolithic A is never formed), the right-hand side, the Arnoldi
+// multi-dot / update / norm kernels, and the adjoint-gradient reductions.
+//
+// On GB300 FP64 issues at 2 operations per clock per SM (about 1.2 TFLOP/s,
+// 1/64 of FP32), so these kernels are bounded by the FP64 pipe rather than by
+// HBM once they do more than ~0.2 FP64 operations per byte; they are written
+// to minimise FP64 operations per element.  All reductions are
+// deterministic: fixed per-block order, then a fixed-order pass over the
+// block partials.
+#include "aao_internal.cuh"
+
+namespace aao {
+
+namespace {
+constexpr int kThreads = 256;
+constexpr int kMaxRedBlocks = 152 * 8;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-reduce NV values per thread into partials[blockIdx.x * NV + j].
+template <int NV>
+__device__ __forceinline__ void block_store(double (&acc)[NV], double *partials) {
+  __shared__ double sm[kThreads / 32][NV > 0 ? NV : 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; j++) {
+    const double s = warp_sum(acc[j]);
+    if (lane == 0) sm[wid][j] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; w++) s += sm[w][threadIdx.x];
+    partials[(size_t)blockIdx.x * NV + threadIdx.x] = s;
+  }
+}
+
+// out[j] = sum_b partials[b * nv + j] in a fixed order (one warp per output).
+__global__ void k_finish(const double *__restrict__ partials, int nb, int nv,
+                         double *__restrict__ out) {
+  const int j = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 32) s += partials[(size_t)b * nv + j];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) out[j] = s;
+}
+
+struct Ptrs8 {
+  const double *p[8];
+};
+}  // namespace
+
+int red_blocks(int64_t N) {
+  int64_t b = (N + (int64_t)kThreads * 8 - 1) / ((int64_t)kThreads * 8);
+  if (b < 1) b = 1;
+  if (b > kMaxRedBlocks) b = kMaxRedBlocks;
+  return (int)b;
+}
+
+// ------------------------------------------------------------------ matvec
+// y_t = M d_t + beta_t (K x_t) with d_t = sum_j alpha_j x_{t -+ j}; the K
+// term is evaluated as differences of neighbours, (x_i - x_{i-1}) -
+// (x_{i+1} - x_i), which keeps the rounding relative to the (small)
+// second difference of a smooth field instead of to the field itself.
+template <int NB, bool TR>
+__global__ void __launch_bounds__(kThreads)
+k_matvec(const double *__restrict__ x, double *__restrict__ y, int n, int ell,
+         double a0, double a1, double a2, double mh, const double *__restrict__ beta) {
+  const int64_t N = (int64_t)n * ell;
+  for (int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x; g < N;
+       g += (int64_t)gridDim.x * kThreads) {
+    const int t = (int)(g / n);
+    const int i = (int)(g - (int64_t)t * n);
+    const double *xt = x + (int64_t)t * n;
+    const double xc = xt[i];
+    const double xl = (i > 0) ? xt[i - 1] : 0.0;
+    const double xr = (i + 1 < n) ? xt[i + 1] : 0.0;
+    double dc = a0 * xc, dl = a0 * xl, dr = a0 * xr;
+    const int t1 = TR ? t + 1 : t - 1;
+    if (t1 >= 0 && t1 < ell) {
+      const double *xs = x + (int64_t)t1 * n;
+      dc = fma(a1, xs[i], dc);
+      if (i > 0) dl = fma(a1, xs[i - 1], dl);
+      if (i + 1 < n) dr = fma(a1, xs[i + 1], dr);
+    }
+    if (NB > 2) {
+      const int t2 = TR ? t + 2 : t - 2;
+      if (t2 >= 0 && t2 < ell) {
+        const double *xs = x + (int64_t)t2 * n;
+        dc = fma(a2, xs[i], dc);
+        if (i > 0) dl = fma(a2, xs[i - 1], dl);
+        if (i + 1 < n) dr = fma(a2, xs[i + 1], dr);
+      }
+    }
+    const double kx = (xc - xl) - (xr - xc);
+    const double md = fma(4.0, dc, dl + dr);
+    y[g] = fma(mh, md, __ldg(&beta[t]) * kx);
+  }
+}
+
+cudaError_t launch_matvec(const Ctx &c, const double *x, double *y, int transpose,
+                          cudaStream_t s) {
+  const int64_t N = c.N;
+  int64_t blocks = (N + kThreads - 1) / kThreads;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  const double mh = c.h / 6.0;
+  double a0 = 1.0, a1 = -1.0, a2 = 0.0;
+  if (c.equation == AAO_HEAT_LITERAL) a0 = c.tau;
+  if (c.equation == AAO_WAVE_BD2) { a1 = -2.0; a2 = 1.0; }
+  const bool bd2 = c.equation == AAO_WAVE_BD2;
+  const unsigned g = (unsigned)blocks;
+  const int n = (int)c.n, ell = (int)c.ell;
+  if (bd2 && transpose)
+    k_matvec<3, true><<<g, kThreads, 0, s>>>(x, y, n, ell, a0, a1, a2, mh, c.beta);
+  else if (bd2)
+    k_matvec<3, false><<<g, kThreads, 0, s>>>(x, y, n, ell, a0, a1, a2, mh, c.beta);
+  else if (transpose)
+    k_matvec<2, true><<<g, kThreads, 0, s>>>(x, y, n, ell, a0, a1, a2, mh, c.beta);
+  else
+    k_matvec<2, false><<<g, kThreads, 0, s>>>(x, y, n, ell, a0, a1, a2, mh, c.beta);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------- rhs
+// Heat: b_0 = M u0.  BD2: b_0 = A0 (u0 + tau v0) = M w + tau^2 K w,
+// b_1 = -M u0.  Literal heat: b_0 = M u0.  Other blocks zero.
+__global__ void k_rhs(const double *__restrict__ u0, const double *__restrict__ v0,
+                      double *__restrict__ b, int n, int ell, int bd2, double tau,
+                      double mh, double kh) {
+  const int64_t N = (int64_t)n * ell;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(g / n);
+    const int i = (int)(g - (int64_t)t * n);
+    double out = 0.0;
+    if (t <= 1) {
+      auto at = [&](const double *v, int j) { return (j >= 0 && j < n) ? v[j] : 0.0; };
+      auto w = [&](int j) {
+        double r = at(u0, j);
+        if (bd2 && v0 && t == 0) r = fma(tau, at(v0, j), r);
+        return r;
+      };
+      const double wc = w(i), wl = w(i - 1), wr = w(i + 1);
+      const double m = mh * fma(4.0, wc, wl + wr);
+      if (t == 0) {
+        out = m;
+        if (bd2) out = fma(tau * tau * kh, (wc - wl) - (wr - wc), out);
+      } else if (bd2) {
+        const double uc = at(u0, i), ul = at(u0, i - 1), ur = at(u0, i + 1);
+        out = -mh * fma(4.0, uc, ul + ur);
+      }
+    }
+    b[g] = out;
+  }
+}
+
+cudaError_t launch_rhs(const Ctx &c, const double *u0, const double *v0, double *b,
+                       cudaStream_t s) {
+  int64_t blocks = (c.N + kThreads - 1) / kThreads;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_rhs<<<(unsigned)blocks, kThreads, 0, s>>>(u0, v0, b, (int)c.n, (int)c.ell,
+                                              c.equation == AAO_WAVE_BD2, c.tau, c.h / 6.0,
+                                              1.0 / c.h); note_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ multi-dot
+template <int NV, bool NORM>
+__global__ void __launch_bounds__(kThreads)
+k_multidot(Ptrs8 V, const double *__restrict__ w, int64_t N, double *__restrict__ partials) {
+  constexpr int NO = NV + (NORM ? 1 : 0);
+  double acc[NO];
+#pragma unroll
+  for (int j = 0; j < NO; j++) acc[j] = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x; g < N;
+       g += (int64_t)gridDim.x * kThreads) {
+    const double wv = w[g];
+#pragma unroll
+    for (int j = 0; j < NV; j++) acc[j] = fma(__ldg(&V.p[j][g]), wv, acc[j]);
+    if (NORM) acc[NO - 1] = fma(wv, wv, acc[NO - 1]);
+  }
+  block_store<NO>(acc, partials);
+}
+
+template <int NV, bool NORM>
+static void run_multidot(const Ptrs8 &P, const double *w, int64_t N, int nb, double *partials,
+                         cudaStream_t s) {
+  k_multidot<NV, NORM><<<nb, kThreads, 0, s>>>(P, w, N, partials); note_launch();
+}
+
+cudaError_t launch_multidot(const double *const *V, int nv, const double *w, int64_t N,
+                            bool with_norm, double *partials, double *out, cudaStream_t s) {
+  const int nb = red_blocks(N);
+  int done = 0;
+  if (nv == 0 && with_norm) {
+    Ptrs8 P{};
+    run_multidot<0, true>(P, w, N, nb, partials, s);
+    k_finish<<<1, 32, 0, s>>>(partials, nb, 1, out); note_launch();
+    return cudaGetLastError();
+  }
+  while (done < nv) {
+    const int g = (nv - done) > 8 ? 8 : (nv - done);
+    const bool norm = with_norm && (done + g == nv);
+    Ptrs8 P{};
+    for (int j = 0; j < g; j++) P.p[j] = V[done + j];
+#define AAO_MD(G)                                                         \
+  case G:                                                                 \
+    if (norm) run_multidot<G, true>(P, w, N, nb, partials, s);            \
+    else run_multidot<G, false>(P, w, N, nb, partials, s);                \
+    break;
+    switch (g) {
+      AAO_MD(1) AAO_MD(2) AAO_MD(3) AAO_MD(4) AAO_MD(5) AAO_MD(6) AAO_MD(7) AAO_MD(8)
+    }
+#undef AAO_MD
+    const int no = g + (norm ? 1 : 0);
+    k_finish<<<no, 32, 0, s>>>(partials, nb, no, out + done); note_launch();
+    done += g;
+  }
+  return cudaGetLastError();
+}
+
+// --------------------------------------------- update (+ dots + norm) pass
+// w -= sum_j h_j V_j; then, if DOTS, acc_j += V_j . w_new, and always
+// acc_nv += w_new . w_new.
+template <int NV, bool DOTS>
+__global__ void __launch_bounds__(kThreads)
+k_update(Ptrs8 V, const double *__restrict__ h, double *__restrict__ w, int64_t N,
+         double *__restrict__ partials) {
+  constexpr int NO = (DOTS ? NV : 0) + 1;
+  double hv[NV];
+#pragma unroll
+  for (int j = 0; j < NV; j++) hv[j] = h[j];
+  double acc[NO];
+#pragma unroll
+  for (int j = 0; j < NO; j++) acc[j] = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x; g < N;
+       g += (int64_t)gridDim.x * kThreads) {
+    double v[NV];
+    double wv = w[g];
+#pragma unroll
+    for (int j = 0; j < NV; j++) {
+      v[j] = __ldg(&V.p[j][g]);
+      wv = fma(-hv[j], v[j], wv);
+    }
+    w[g] = wv;
+    if (DOTS) {
+#pragma unroll
+      for (int j = 0; j < NV; j++) acc[j] = fma(v[j], wv, acc[j]);
+    }
+    acc[NO - 1] = fma(wv, wv, acc[NO - 1]);
+  }
+  block_store<NO>(acc, partials);
+}
+
+cudaError_t launch_update_dots(const double *const *V, int nv, const double *h, double *w,
+                               int64_t N, bool want_dots, double *partials, double *out2,
+                               cudaStream_t s) {
+  // Groups of 8 vectors: every group but the last only updates; the dots of
+  // the final w with all vectors are then taken by a multi-dot pass when
+  // nv > 8 (the fused path covers nv <= 8, the common case).
+  const int nb = red_blocks(N);
+  if (nv <= 8) {
+    Ptrs8 P{};
+    for (int j = 0; j < nv; j++) P.p[j] = V[j];
+#define AAO_UP(G)                                                                          \
+  case G:                                                                                  \
+    if (want_dots) k_update<G, true><<<nb, kThreads, 0, s>>>(P, h, w, N, partials);        \
+    else k_update<G, false><<<nb, kThreads, 0, s>>>(P, h, w, N, partials);                 \
+    note_launch();                                                                         \
+    break;
+    switch (nv) {
+      AAO_UP(1) AAO_UP(2) AAO_UP(3) AAO_UP(4) AAO_UP(5) AAO_UP(6) AAO_UP(7) AAO_UP(8)
+      default: return cudaErrorInvalidValue;
+    }
+    const int no = (want_dots ? nv : 0) + 1;
+    if (want_dots) {
+      k_finish<<<no, 32, 0, s>>>(partials, nb, no, out2); note_launch();
+    } else {
+      k_finish<<<1, 32, 0, s>>>(partials, nb, 1, out2 + nv); note_launch();
+    }
+    return cudaGetLastError();
+  }
+  int done = 0;
+  while (done < nv) {
+    const int g = (nv - done) > 8 ? 8 : (nv - done);
+    Ptrs8 P{};
+    for (int j = 0; j < g; j++) P.p[j] = V[done + j];
+    switch (g) {
+#define AAO_UP2(G) case G: k_update<G, false><<<nb, kThreads, 0, s>>>(P, h + done, w, N, partials); note_launch(); break;
+      AAO_UP2(1) AAO_UP2(2) AAO_UP2(3) AAO_UP2(4) AAO_UP2(5) AAO_UP2(6) AAO_UP2(7) AAO_UP2(8)
+#undef AAO_UP2
+    }
+    done += g;
+  }
+  if (want_dots) return launch_multidot(V, nv, w, N, true, partials, out2, s);
+  k_finish<<<1, 32, 0, s>>>(partials, nb, 1, out2 + nv); note_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ x += Z y
+template <int NV>
+__global__ void __launch_bounds__(kThreads)
+k_combine(Ptrs8 Z, const double *__restrict__ yv, double *__restrict__ x, int64_t N) {
+  double c[NV];
+#pragma unroll
+  for (int j = 0; j < NV; j++) c[j] = yv[j];
+  for (int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x; g < N;
+       g += (int64_t)gridDim.x * kThreads) {
+    double a = x[g];
+#pragma unroll
+    for (int j = 0; j < NV; j++) a = fma(c[j], __ldg(&Z.p[j][g]), a);
+    x[g] = a;
+  }
+}
+
+cudaError_t launch_combine(const double *const *Z, int nv, const double *y, double *x,
+                           int64_t N, cudaStream_t s) {
+  int64_t blocks = (N + kThreads - 1) / kThreads;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  int done = 0;
+  while (done < nv) {
+    const int g = (nv - done) > 8 ? 8 : (nv - done);
+    Ptrs8 P{};
+    for (int j = 0; j < g; j++) P.p[j] = Z[done + j];
+    switch (g) {
+#define AAO_CB(G) case G: k_combine<G><<<(unsigned)blocks, kThreads, 0, s>>>(P, y + done, x, N); note_launch(); break;
+      AAO_CB(1) AAO_CB(2) AAO_CB(3) AAO_CB(4) AAO_CB(5) AAO_CB(6) AAO_CB(7) AAO_CB(8)
+#undef AAO_CB
+    }
+    done += g;
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ misc
+// y = a * x with a = *ap (or 1/sqrt(*ap) when invert: a norm^2 on device)
+__global__ void k_scale(const double *__restrict__ x, double *__restrict__ y,
+                        const double *__restrict__ ap, int64_t N, int invert) {
+  double a = *ap;
+  if (invert) a = 1.0 / sqrt(a);
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N;
+       g += (int64_t)gridDim.x * blockDim.x)
+    y[g] = a * x[g];
+}
+
+cudaError_t launch_scale(const double *x, double *y, const double *a, int64_t N, bool invert,
+                         cudaStream_t s) {
+  int64_t blocks = (N + kThreads - 1) / kThreads;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_scale<<<(unsigned)blocks, kThreads, 0, s>>>(x, y, a, N, invert ? 1 : 0); note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_sub_from(const double *__restrict__ b, double *__restrict__ r, int64_t N) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N;
+       g += (int64_t)gridDim.x * blockDim.x)
+    r[g] = b[g] - r[g];
+}
+
+cudaError_t launch_sub_from(const double *b, double *r, int64_t N, cudaStream_t s) {
+  int64_t blocks = (N + kThreads - 1) / kThreads;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_sub_from<<<(unsigned)blocks, kThreads, 0, s>>>(b, r, N); note_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------- adjoint gradients
+// g_u0 = M lam_1; sum_t tau_t lam_t^T K u_t (reduced; the caller negates).
+__global__ void k_grad_u0(const double *__restrict__ lam, double *__restrict__ g, int n,
+                          double mh) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double c = lam[i], l = (i > 0) ? lam[i - 1] : 0.0, r = (i + 1 < n) ? lam[i + 1] : 0.0;
+    g[i] = mh * fma(4.0, c, l + r);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_grad_kappa(const double *__restrict__ lam, const double *__restrict__ U, int n, int ell,
+             const double *__restrict__ tauk, double *__restrict__ partials) {
+  const int64_t N = (int64_t)n * ell;
+  double acc[1] = {0.0};
+  for (int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x; g < N;
+       g += (int64_t)gridDim.x * kThreads) {
+    const int t = (int)(g / n);
+    const int i = (int)(g - (int64_t)t * n);
+    const double uc = U[g];
+    const double ul = (i > 0) ? U[g - 1] : 0.0;
+    const double ur = (i + 1 < n) ? U[g + 1] : 0.0;
+    const double ku = (uc - ul) - (ur - uc);
+    acc[0] = fma(__ldg(&tauk[t]) * lam[g], ku, acc[0]);
+  }
+  block_store<1>(acc, partials);
+}
+
+cudaError_t launch_adjoint_grads(const Ctx &c, const double *lam, const double *U,
+                                 double *g_u0, double *partials, double *out, cudaStream_t s) {
+  const int n = (int)c.n;
+  k_grad_u0<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(lam, g_u0, n, c.h / 6.0); note_launch();
+  const int nb = red_blocks(c.N);
+  // beta_t = tau_t kappa / h, so tau_t lam^T K u = (beta_t / kappa) lam^T (h K) u / h ... use
+  // tau_t / h directly: the matvec's beta divided by kappa.
+  k_grad_kappa<<<nb, kThreads, 0, s>>>(lam, U, n, (int)c.ell, c.beta, partials); note_launch();
+  k_finish<<<1, 32, 0, s>>>(partials, nb, 1, out); note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace aao

@@ -1,0 +1,683 @@
+// C ABI of the all-at-once solver: context, per-frequency symbols, the
+// preconditioner applies, the matvec and the flexible GMRES driver.
+#include <complex>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "aao_internal.cuh"
+
+namespace aao {
+thread_local int64_t tl_launches = 0;
+}
+
+using aao::Ctx;
+using aao::cx;
+using cd = std::complex<double>;
+
+struct aao_ctx {
+  Ctx c;
+};
+
+namespace {
+
+constexpr int kMaxRestart = 128;
+constexpr int64_t kMaxEll = 4096;
+constexpr int64_t kMaxN = 16383;
+constexpr size_t kAlign = 256;
+constexpr int kPartials = 152 * 8 * 16;      // doubles for block partials
+constexpr int kSmall = 1024;                 // doubles for device-side small results
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// sin(pi a / b) with the argument reduced exactly, so that multiples of pi
+// give exactly 0 and odd multiples of pi/2 exactly +-1.
+double sinpi_q(int64_t a, int64_t b) {
+  const int64_t b2 = 2 * b;
+  a %= b2;
+  if (a < 0) a += b2;
+  double sg = 1.0;
+  if (a >= b) { a -= b; sg = -1.0; }
+  if (2 * a > b) a = b - a;
+  if (a == 0) return 0.0;
+  if (2 * a == b) return sg;
+  return sg * std::sin(M_PI * (double)a / (double)b);
+}
+
+// 1 - w_k with w_k = exp(-2 pi i k/ell): 2 sin^2(pi k/ell) + i sin(2 pi k/ell)
+cd one_minus_w(int64_t k, int64_t ell) {
+  const double s = sinpi_q(k, ell);
+  return cd(2.0 * s * s, sinpi_q(2 * k, ell));
+}
+
+// Frequency block A0 + w A1 (+ w^2 A2) = cM(k) M + cK K (Section 3).
+void block_symbol(const Ctx &c, int64_t k, cd &cM, double &cK) {
+  const cd om = one_minus_w(k, c.ell);
+  switch (c.equation) {
+    case AAO_WAVE_BD2:  // (M + tau^2 K) - 2 w M + w^2 M = (1 - w)^2 M + tau^2 K
+      cM = om * om;
+      cK = c.tau * c.tau;
+      break;
+    case AAO_HEAT_LITERAL:  // (K + tau M) - w M = (tau - 1 + (1 - w)) M + K
+      cM = om + cd(c.tau - 1.0, 0.0);
+      cK = 1.0;
+      break;
+    default:  // (M + tau kappa K) - w M = (1 - w) M + tau kappa K
+      cM = om;
+      cK = c.tau * c.kappa;
+      break;
+  }
+}
+
+// Row excess sigma = d + 2e and off-diagonal e of cM M + cK K (uniform P1:
+// M = (h/6) tridiag(1,4,1), K = (1/h) tridiag(-1,2,-1)).
+void excess_form(const Ctx &c, const cd &cM, double cK, cd &sig, cd &e) {
+  sig = cM * c.h;
+  e = cM * (c.h / 6.0) - cd(cK / c.h, 0.0);
+}
+
+template <typename R>
+cx<R> to_cx(const cd &z) { return aao::mk((R)z.real(), (R)z.imag()); }
+
+// Thomas solve on a chunk of `len` unknowns with the shared pivots.
+void chunk_solve(const std::vector<cd> &invp, const std::vector<cd> &bp, const cd &e,
+                 const std::vector<cd> &rhs, int len, std::vector<cd> &out) {
+  out.assign(len, cd(0, 0));
+  out[0] = rhs[0] * invp[0];
+  for (int i = 1; i < len; i++) out[i] = (rhs[i] - e * out[i - 1]) * invp[i];
+  for (int i = len - 2; i >= 0; i--) out[i] = out[i] - bp[i] * out[i + 1];
+}
+
+template <typename R, int CH>
+void build_tables(const Ctx &c, int64_t cl, std::vector<aao::TriTab<R, CH>> &tabs) {
+  tabs.assign((size_t)c.nk, aao::TriTab<R, CH>{});
+  const int cr = CH - 1;
+  for (int64_t k = 0; k < c.nk; k++) {
+    cd cM, sig, e;
+    double cK;
+    block_symbol(c, k, cM, cK);
+    excess_form(c, cM, cK, sig, e);
+    // pivots of the constant-coefficient LU in excess form:
+    // q_0 = sigma - e, q_i = sigma - e q_{i-1} / p_{i-1}, p_i = q_i - e
+    std::vector<cd> invp(CH), bp(CH);
+    cd q = sig - e, p = q - e;
+    for (int i = 0; i < CH; i++) {
+      if (i > 0) {
+        q = sig - e * q / p;
+        p = q - e;
+      }
+      invp[i] = 1.0 / p;
+      bp[i] = e / p;
+    }
+    std::vector<cd> unit_first(CH, cd(0, 0)), ones(CH, cd(1, 0));
+    unit_first[0] = 1.0;
+    std::vector<cd> gc, wc, gl, wl;
+    chunk_solve(invp, bp, e, unit_first, cr, gc);
+    chunk_solve(invp, bp, e, ones, cr, wc);
+    chunk_solve(invp, bp, e, unit_first, (int)cl, gl);
+    chunk_solve(invp, bp, e, ones, (int)cl, wl);
+    auto &T = tabs[(size_t)k];
+    for (int i = 0; i < CH; i++) {
+      T.invp[i] = to_cx<R>(invp[i]);
+      T.bp[i] = to_cx<R>(bp[i]);
+      T.fc[i] = to_cx<R>(i < cr ? -e * gc[i] : cd(0, 0));
+      T.fl[i] = to_cx<R>(i < cl ? -e * gl[i] : cd(0, 0));
+    }
+    T.e = to_cx<R>(e);
+    // separator rows: sigma' = sigma (1 - e (w_left[0] + w_right[0])),
+    // couplings -e^2 g[len-1] (identity 1 + e (g[0] + g[len-1]) = sigma w[0])
+    T.sig_reg = to_cx<R>(sig * (1.0 - 2.0 * e * wc[0]));
+    T.off_reg = to_cx<R>(-e * e * gc[cr - 1]);
+    T.sig_last = to_cx<R>(sig * (1.0 - e * (wc[0] + wl[0])));
+    T.off_last = to_cx<R>(-e * e * gl[cl - 1]);
+  }
+}
+
+// Chunks of a row of n unknowns with chunk length CH (CH-1 unknowns + one
+// separator); returns the chunk count P and the last chunk's size cl.
+void chunking(int64_t n, int CH, int &P, int64_t &cl) {
+  const int64_t M = (n >= CH + 1) ? ((n - 1 - CH) / CH + 1) : 0;
+  P = (int)(M + 1);
+  cl = n - M * CH;
+}
+
+template <typename T>
+cudaError_t upload(void **dst, const std::vector<T> &v) {
+  if (*dst) { cudaFree(*dst); *dst = nullptr; }
+  cudaError_t e = cudaMalloc(dst, v.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+int fail_cuda(Ctx &c, cudaError_t e, const char *where) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  c.last_error = buf;
+  return AAO_ECUDA;
+}
+
+#define AAO_CK(ctx, call)                                         \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return fail_cuda((ctx), e_, #call);    \
+  } while (0)
+
+cudaEvent_t take_event(Ctx &c) {
+  if (!c.event_pool.empty()) {
+    cudaEvent_t e = c.event_pool.back();
+    c.event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Run one launcher, attribute its kernels to class `cls`, and bracket them
+// with events when profiling is on.
+template <class F>
+cudaError_t run(Ctx &c, int cls, cudaStream_t s, F &&f) {
+  const int64_t before = aao::tl_launches;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (c.prof_on) {
+    a = take_event(c);
+    b = take_event(c);
+    if (a && b) cudaEventRecord(a, s);
+  }
+  const cudaError_t e = f();
+  if (c.prof_on && a && b) {
+    cudaEventRecord(b, s);
+    c.pending.push_back({cls, a, b});
+  }
+  c.launches[cls] += aao::tl_launches - before;
+  return e;
+}
+
+// Fold finished event pairs into the per-class totals.
+cudaError_t collect(Ctx &c) {
+  for (auto &p : c.pending) {
+    cudaError_t e = cudaEventSynchronize(p.b);
+    if (e != cudaSuccess) return e;
+    float ms = 0.0f;
+    e = cudaEventElapsedTime(&ms, p.a, p.b);
+    if (e != cudaSuccess) return e;
+    c.prof_ms[p.cls] += ms;
+    c.event_pool.push_back(p.a);
+    c.event_pool.push_back(p.b);
+  }
+  c.pending.clear();
+  return cudaSuccess;
+}
+
+// (Re)compute everything that depends on kappa, the steps or tau.
+int refresh_constants(Ctx &c) {
+  // per-frequency tridiagonal tables
+  {
+    int64_t cl;
+    chunking(c.n, c.ch32, c.P32, cl);
+    std::vector<aao::TriTab<float, 16>> t32;
+    build_tables<float, 16>(c, cl, t32);
+    AAO_CK(c, upload(&c.tab32, t32));
+    chunking(c.n, c.ch64, c.P64, cl);
+    if (c.ch64 == 8) {
+      std::vector<aao::TriTab<double, 8>> t64;
+      build_tables<double, 8>(c, cl, t64);
+      AAO_CK(c, upload(&c.tab64, t64));
+    } else {
+      std::vector<aao::TriTab<double, 16>> t64;
+      build_tables<double, 16>(c, cl, t64);
+      AAO_CK(c, upload(&c.tab64, t64));
+    }
+  }
+  // matvec K coefficients beta_t and Neumann coefficients (tau_t - tau) kappa / h
+  std::vector<double> beta((size_t)c.ell), sk((size_t)c.ell, 0.0);
+  std::vector<float> sk32((size_t)c.ell, 0.0f);
+  for (int64_t t = 0; t < c.ell; t++) {
+    const double tt = c.variable_steps ? c.taus[(size_t)t] : c.tau;
+    switch (c.equation) {
+      case AAO_WAVE_BD2: beta[(size_t)t] = c.tau * c.tau / c.h; break;
+      case AAO_HEAT_LITERAL: beta[(size_t)t] = 1.0 / c.h; break;
+      default: beta[(size_t)t] = tt * c.kappa / c.h; break;
+    }
+    if (c.variable_steps) {
+      sk[(size_t)t] = (tt - c.tau) * c.kappa / c.h;
+      sk32[(size_t)t] = (float)sk[(size_t)t];
+    }
+  }
+  AAO_CK(c, upload((void **)&c.beta, beta));
+  AAO_CK(c, upload((void **)&c.sigk, sk));
+  AAO_CK(c, upload((void **)&c.sigk32, sk32));
+  return AAO_OK;
+}
+
+bool overlap(const void *a, const void *b, size_t bytes) {
+  const char *pa = static_cast<const char *>(a), *pb = static_cast<const char *>(b);
+  return pa < pb + bytes && pb < pa + bytes;
+}
+
+cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+namespace aao {
+WsLayout ws_layout(const Ctx &c, int restart) {
+  WsLayout L;
+  L.spec = 0;
+  L.spec_bytes = round_up((size_t)c.nk * (size_t)c.n_pad * sizeof(cx<double>), kAlign);
+  L.red = L.spec + L.spec_bytes;
+  L.red_bytes = round_up((size_t)(kPartials + kSmall) * sizeof(double), kAlign);
+  L.vecs = L.red + L.red_bytes;
+  L.vec_bytes = round_up((size_t)c.N * sizeof(double), kAlign);
+  const int nvec = restart > 0 ? (restart + 1) + restart + 2 : 0;
+  L.total = L.vecs + (size_t)nvec * L.vec_bytes;
+  return L;
+}
+}  // namespace aao
+
+namespace {
+
+double *vec_at(Ctx &c, const aao::WsLayout &L, int j) {
+  return reinterpret_cast<double *>(c.ws + L.vecs + (size_t)j * L.vec_bytes);
+}
+
+int check_ws(const Ctx &c, int restart) {
+  if (!c.ws) return AAO_EINVAL;
+  if (c.ws_bytes < aao::ws_layout(c, restart).total) return AAO_EINVAL;
+  return AAO_OK;
+}
+
+cudaError_t precond_once(Ctx &c, const double *x, const double *yprev, double *y, int tr,
+                         cudaStream_t s) {
+  void *spec = c.ws + aao::ws_layout(c, 0).spec;
+  const bool f32 = c.prec == AAO_PREC_FP32;
+  cudaError_t e = run(c, AAO_K_FFT_FORWARD, s, [&] {
+    return f32 ? aao::fft_forward_f32(c, x, yprev, spec, s)
+               : aao::fft_forward_f64(c, x, yprev, spec, s);
+  });
+  if (e != cudaSuccess) return e;
+  e = run(c, AAO_K_TRIDIAG, s, [&] { return aao::launch_tridiag(c, spec, c.prec, tr, s); });
+  if (e != cudaSuccess) return e;
+  return run(c, AAO_K_FFT_INVERSE, s, [&] {
+    return f32 ? aao::fft_inverse_f32(c, spec, y, s) : aao::fft_inverse_f64(c, spec, y, s);
+  });
+}
+
+// Q_i^{-1} x (or Q_i^{-T} x) by y_0 = P^{-1} x, y_m = P^{-1}(x - E y_{m-1}).
+cudaError_t neumann(Ctx &c, int terms, const double *x, double *y, int tr, cudaStream_t s) {
+  cudaError_t e = precond_once(c, x, nullptr, y, tr, s);
+  if (e != cudaSuccess) return e;
+  if (!c.variable_steps) return cudaSuccess;   // E = 0: every further term is P^{-1} x
+  for (int m = 1; m < terms; m++)
+    if ((e = precond_once(c, x, y, y, tr, s)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+// Flexible GMRES(m), right preconditioning, CGS with one re-orthogonalisation.
+int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, int maxit,
+               int precond, aao_solve_info *info, cudaStream_t s) {
+  if (m < 1 || m > kMaxRestart || !(rtol > 0.0) || maxit < 0 || precond < 0) return AAO_EINVAL;
+  if (check_ws(c, m) != AAO_OK) return AAO_EINVAL;
+  const aao::WsLayout L = aao::ws_layout(c, m);
+  const int64_t N = c.N;
+  const size_t vb = (size_t)N * sizeof(double);
+  if (overlap(b, x, vb)) return AAO_EINVAL;
+  double *red = reinterpret_cast<double *>(c.ws + L.red);
+  double *small = red + kPartials;
+  double *d_h1 = small, *d_h2 = small + 160, *d_nr = small + 320, *d_y = small + 480;
+  double *hs = c.host_small;   // pinned: [0,160) h1, [160,320) h2, [320,480) norms, [480,...) y
+  std::vector<double *> V((size_t)m + 1), Z((size_t)m);
+  for (int j = 0; j <= m; j++) V[(size_t)j] = vec_at(c, L, j);
+  for (int j = 0; j < m; j++) Z[(size_t)j] = precond ? vec_at(c, L, m + 1 + j) : V[(size_t)j];
+  for (auto *v : V)
+    if (overlap(v, b, vb) || overlap(v, x, vb)) return AAO_EINVAL;
+
+  if (info) { info->iters = 0; info->restarts = 0; info->history_len = 0; }
+  auto norm2 = [&](const double *v, double *dst_dev, double *dst_host) -> cudaError_t {
+    cudaError_t e = run(c, AAO_K_DOTS, s, [&] {
+      return aao::launch_multidot(nullptr, 0, v, N, true, red, dst_dev, s);
+    });
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(dst_host, dst_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+  };
+  AAO_CK(c, norm2(b, d_nr, hs + 320));
+  const double bnorm = std::sqrt(hs[320]);
+  if (!std::isfinite(bnorm)) return AAO_ENUMERIC;
+  if (bnorm == 0.0) {
+    AAO_CK(c, cudaMemsetAsync(x, 0, vb, s));
+    AAO_CK(c, cudaStreamSynchronize(s));
+    if (info) { info->relres_true = 0.0; info->relres_est = 0.0; }
+    return AAO_OK;
+  }
+  std::vector<double> H((size_t)(m + 1) * m), cs((size_t)m), sn((size_t)m), g((size_t)m + 1);
+  auto Hij = [&](int i, int j) -> double & { return H[(size_t)i * m + j]; };
+  int iters = 0, restarts = 0, status = AAO_ENOCONV;
+  double relres_true = 1.0, est = 1.0;
+  for (;;) {
+    AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] { return aao::launch_matvec(c, x, V[0], tr, s); }));
+    AAO_CK(c, run(c, AAO_K_OTHER, s, [&] { return aao::launch_sub_from(b, V[0], N, s); }));
+    AAO_CK(c, norm2(V[0], d_nr, hs + 320));
+    const double beta = std::sqrt(hs[320]);
+    relres_true = beta / bnorm;
+    if (!std::isfinite(beta)) { status = AAO_ENUMERIC; break; }
+    if (relres_true <= rtol) { status = AAO_OK; break; }
+    if (iters >= maxit) { status = AAO_ENOCONV; break; }
+    AAO_CK(c, run(c, AAO_K_OTHER, s, [&] { return aao::launch_scale(V[0], V[0], d_nr, N, true, s); }));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jd = 0;
+    bool numeric_fail = false;
+    for (int j = 0; j < m; j++) {
+      if (precond == 1) AAO_CK(c, precond_once(c, V[(size_t)j], nullptr, Z[(size_t)j], tr, s));
+      else if (precond >= 2) AAO_CK(c, neumann(c, precond, V[(size_t)j], Z[(size_t)j], tr, s));
+      double *w = V[(size_t)j + 1];
+      AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] { return aao::launch_matvec(c, Z[(size_t)j], w, tr, s); }));
+      const int nv = j + 1;
+      AAO_CK(c, run(c, AAO_K_DOTS, s, [&] {
+        return aao::launch_multidot(V.data(), nv, w, N, false, red, d_h1, s);
+      }));
+      AAO_CK(c, run(c, AAO_K_UPDATE, s, [&] {
+        return aao::launch_update_dots(V.data(), nv, d_h1, w, N, true, red, d_h2, s);
+      }));
+      AAO_CK(c, run(c, AAO_K_UPDATE, s, [&] {
+        return aao::launch_update_dots(V.data(), nv, d_h2, w, N, false, red, d_nr, s);
+      }));
+      AAO_CK(c, cudaMemcpyAsync(hs, d_h1, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+      AAO_CK(c, cudaMemcpyAsync(hs + 160, d_h2, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+      AAO_CK(c, cudaMemcpyAsync(hs + 320 + nv, d_nr + nv, sizeof(double), cudaMemcpyDeviceToHost, s));
+      AAO_CK(c, cudaStreamSynchronize(s));
+      for (int i = 0; i < nv; i++) Hij(i, j) = hs[i] + hs[160 + i];
+      const double hn = std::sqrt(hs[320 + nv]);
+      Hij(j + 1, j) = hn;
+      if (!std::isfinite(hn)) { numeric_fail = true; break; }
+      const bool breakdown = !(hn > 1e-300);
+      if (!breakdown)
+        AAO_CK(c, run(c, AAO_K_OTHER, s, [&] { return aao::launch_scale(w, w, d_nr + nv, N, true, s); }));
+      for (int i = 0; i < j; i++) {
+        const double t = cs[(size_t)i] * Hij(i, j) + sn[(size_t)i] * Hij(i + 1, j);
+        Hij(i + 1, j) = -sn[(size_t)i] * Hij(i, j) + cs[(size_t)i] * Hij(i + 1, j);
+        Hij(i, j) = t;
+      }
+      const double a = Hij(j, j), bb = Hij(j + 1, j);
+      const double r = std::hypot(a, bb);
+      cs[(size_t)j] = (r == 0.0) ? 1.0 : a / r;
+      sn[(size_t)j] = (r == 0.0) ? 0.0 : bb / r;
+      Hij(j, j) = r;
+      Hij(j + 1, j) = 0.0;
+      g[(size_t)j + 1] = -sn[(size_t)j] * g[(size_t)j];
+      g[(size_t)j] = cs[(size_t)j] * g[(size_t)j];
+      iters++;
+      jd = j + 1;
+      est = std::fabs(g[(size_t)j + 1]) / bnorm;
+      if (info && info->history && info->history_len < info->history_cap)
+        info->history[info->history_len++] = est;
+      if (est <= rtol || iters >= maxit || breakdown) break;
+    }
+    if (numeric_fail) { status = AAO_ENUMERIC; break; }
+    // y = R^{-1} g, then x += Z y
+    std::vector<double> y((size_t)jd);
+    for (int i = jd - 1; i >= 0; i--) {
+      double acc = g[(size_t)i];
+      for (int l = i + 1; l < jd; l++) acc -= Hij(i, l) * y[(size_t)l];
+      y[(size_t)i] = acc / Hij(i, i);
+    }
+    for (int i = 0; i < jd; i++) hs[480 + i] = y[(size_t)i];
+    AAO_CK(c, cudaMemcpyAsync(d_y, hs + 480, jd * sizeof(double), cudaMemcpyHostToDevice, s));
+    AAO_CK(c, run(c, AAO_K_COMBINE, s, [&] { return aao::launch_combine(Z.data(), jd, d_y, x, N, s); }));
+    restarts++;
+  }
+  AAO_CK(c, cudaStreamSynchronize(s));
+  AAO_CK(c, collect(c));
+  if (info) {
+    info->iters = iters;
+    info->restarts = restarts;
+    info->relres_true = relres_true;
+    info->relres_est = est;
+  }
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *aao_strerror(int status) {
+  switch (status) {
+    case AAO_OK: return "ok";
+    case AAO_ENOCONV: return "not converged within maxit";
+    case AAO_EINVAL: return "invalid argument";
+    case AAO_ENOMEM: return "out of memory";
+    case AAO_ECUDA: return "CUDA error";
+    case AAO_ENUMERIC: return "non-finite value in the iteration";
+    case AAO_EUNSUPPORTED: return "unsupported shape";
+    default: return "unknown status";
+  }
+}
+
+const char *aao_last_error(const aao_ctx *ctx) {
+  return ctx ? ctx->c.last_error.c_str() : "";
+}
+
+int aao_create(int64_t n, int64_t ell, double tau, int equation, aao_ctx **out) {
+  if (!out) return AAO_EINVAL;
+  *out = nullptr;
+  if (n < 1 || !(tau > 0.0) || !std::isfinite(tau)) return AAO_EINVAL;
+  if (equation != AAO_HEAT && equation != AAO_WAVE_BD2 && equation != AAO_HEAT_LITERAL)
+    return AAO_EINVAL;
+  if (ell < 1 || ell > kMaxEll || (ell & (ell - 1)) != 0 || n > kMaxN) return AAO_EUNSUPPORTED;
+  aao_ctx *h = new (std::nothrow) aao_ctx();
+  if (!h) return AAO_ENOMEM;
+  Ctx &c = h->c;
+  c.n = n;
+  c.ell = ell;
+  c.N = n * ell;
+  c.tau = tau;
+  c.h = 1.0 / (double)(n + 1);
+  c.equation = equation;
+  c.nk = ell / 2 + 1;
+  c.n_pad = (int64_t)round_up((size_t)n, 16);
+  c.ch32 = 16;
+  c.ch64 = (n <= 8191) ? 8 : 16;
+  cudaGetDevice(&c.device);
+  int st = refresh_constants(c);
+  if (st == AAO_OK) {
+    std::vector<cx<float>> t32((size_t)ell);
+    std::vector<cx<double>> t64((size_t)ell);
+    for (int64_t m = 0; m < ell; m++) {
+      const double co = sinpi_q(4 * m + ell, 2 * ell);   // cos(2 pi m / ell)
+      const double si = sinpi_q(2 * m, ell);             // sin(2 pi m / ell)
+      t64[(size_t)m] = aao::mk(co, -si);
+      t32[(size_t)m] = aao::mk((float)co, (float)-si);
+    }
+    cudaError_t e = upload((void **)&c.tw32, t32);
+    if (e == cudaSuccess) e = upload((void **)&c.tw64, t64);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c.host_small, kSmall * sizeof(double));
+    if (e != cudaSuccess) st = fail_cuda(c, e, "create");
+  }
+  if (st != AAO_OK) {
+    aao_destroy(h);
+    return st == AAO_ECUDA ? AAO_ENOMEM : st;
+  }
+  *out = h;
+  return AAO_OK;
+}
+
+void aao_destroy(aao_ctx *ctx) {
+  if (!ctx) return;
+  Ctx &c = ctx->c;
+  void *ptrs[] = {c.tab32, c.tab64, c.tw32, c.tw64, c.beta, c.sigk, c.sigk32};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (c.host_small) cudaFreeHost(c.host_small);
+  for (auto &p : c.pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : c.event_pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+int aao_set_kappa(aao_ctx *ctx, double kappa) {
+  if (!ctx || !(kappa > 0.0) || !std::isfinite(kappa)) return AAO_EINVAL;
+  if (ctx->c.equation != AAO_HEAT) return AAO_EINVAL;
+  ctx->c.kappa = kappa;
+  return refresh_constants(ctx->c);
+}
+
+int aao_set_steps(aao_ctx *ctx, const double *tau_steps_host) {
+  if (!ctx) return AAO_EINVAL;
+  Ctx &c = ctx->c;
+  if (c.equation != AAO_HEAT) return AAO_EINVAL;
+  if (!tau_steps_host) {
+    c.variable_steps = false;
+    c.taus.clear();
+  } else {
+    for (int64_t t = 0; t < c.ell; t++)
+      if (!(tau_steps_host[t] > 0.0) || !std::isfinite(tau_steps_host[t])) return AAO_EINVAL;
+    c.taus.assign(tau_steps_host, tau_steps_host + c.ell);
+    c.variable_steps = true;
+  }
+  return refresh_constants(c);
+}
+
+int aao_set_precision(aao_ctx *ctx, int prec) {
+  if (!ctx || (prec != AAO_PREC_FP32 && prec != AAO_PREC_FP64)) return AAO_EINVAL;
+  ctx->c.prec = prec;
+  return AAO_OK;
+}
+
+size_t aao_workspace_bytes(const aao_ctx *ctx, int restart) {
+  if (!ctx || restart < 0 || restart > kMaxRestart) return 0;
+  return aao::ws_layout(ctx->c, restart).total;
+}
+
+int aao_set_workspace(aao_ctx *ctx, void *dev_ptr, size_t bytes) {
+  if (!ctx || !dev_ptr || (reinterpret_cast<uintptr_t>(dev_ptr) % kAlign) != 0) return AAO_EINVAL;
+  if (bytes < aao::ws_layout(ctx->c, 0).total) return AAO_EINVAL;
+  ctx->c.ws = static_cast<char *>(dev_ptr);
+  ctx->c.ws_bytes = bytes;
+  return AAO_OK;
+}
+
+int aao_precond_apply(aao_ctx *ctx, const double *x, double *y, int transpose, void *stream) {
+  if (!ctx || !x || !y) return AAO_EINVAL;
+  Ctx &c = ctx->c;
+  if (overlap(x, y, (size_t)c.N * sizeof(double)) || check_ws(c, 0) != AAO_OK) return AAO_EINVAL;
+  AAO_CK(c, precond_once(c, x, nullptr, y, transpose ? 1 : 0, as_stream(stream)));
+  return AAO_OK;
+}
+
+int aao_neumann_apply(aao_ctx *ctx, int terms, const double *x, double *y, int transpose,
+                      void *stream) {
+  if (!ctx || !x || !y || terms < 1) return AAO_EINVAL;
+  Ctx &c = ctx->c;
+  if (overlap(x, y, (size_t)c.N * sizeof(double)) || check_ws(c, 0) != AAO_OK) return AAO_EINVAL;
+  AAO_CK(c, neumann(c, terms, x, y, transpose ? 1 : 0, as_stream(stream)));
+  return AAO_OK;
+}
+
+int aao_matvec(aao_ctx *ctx, const double *x, double *y, int transpose, void *stream) {
+  if (!ctx || !x || !y) return AAO_EINVAL;
+  Ctx &c = ctx->c;
+  if (overlap(x, y, (size_t)c.N * sizeof(double))) return AAO_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] { return aao::launch_matvec(c, x, y, transpose ? 1 : 0, s); }));
+  return AAO_OK;
+}
+
+int aao_build_rhs(aao_ctx *ctx, const double *u0, const double *v0, double *b, void *stream) {
+  if (!ctx || !u0 || !b) return AAO_EINVAL;
+  Ctx &c = ctx->c;
+  const size_t nb = (size_t)c.n * sizeof(double), Nb = (size_t)c.N * sizeof(double);
+  if (overlap(u0, b, Nb > nb ? Nb : nb) || (v0 && overlap(v0, b, Nb))) return AAO_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  AAO_CK(c, run(c, AAO_K_OTHER, s, [&] { return aao::launch_rhs(c, u0, v0, b, s); }));
+  return AAO_OK;
+}
+
+int aao_gmres_solve(aao_ctx *ctx, const double *b, double *x, int restart, double rtol,
+                    int maxit, int precond, aao_solve_info *info, void *stream) {
+  if (!ctx || !b || !x) return AAO_EINVAL;
+  return solve_core(ctx->c, 0, b, x, restart, rtol, maxit, precond, info, as_stream(stream));
+}
+
+int aao_adjoint_solve(aao_ctx *ctx, const double *g, double *lambda, int restart, double rtol,
+                      int maxit, int precond, aao_solve_info *info, void *stream) {
+  if (!ctx || !g || !lambda) return AAO_EINVAL;
+  return solve_core(ctx->c, 1, g, lambda, restart, rtol, maxit, precond, info,
+                    as_stream(stream));
+}
+
+int aao_adjoint_grads(aao_ctx *ctx, const double *lambda, const double *U, double *g_u0,
+                      double *g_kappa, void *stream) {
+  if (!ctx || !lambda || !U || !g_u0 || !g_kappa) return AAO_EINVAL;
+  Ctx &c = ctx->c;
+  if (c.equation != AAO_HEAT || check_ws(c, 0) != AAO_OK) return AAO_EINVAL;
+  const aao::WsLayout L = aao::ws_layout(c, 0);
+  double *red = reinterpret_cast<double *>(c.ws + L.red);
+  double *out = red + kPartials + 960;
+  cudaStream_t s = as_stream(stream);
+  AAO_CK(c, run(c, AAO_K_OTHER, s, [&] { return aao::launch_adjoint_grads(c, lambda, U, g_u0, red, out, s); }));
+  AAO_CK(c, cudaMemcpyAsync(c.host_small + 960, out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  AAO_CK(c, cudaStreamSynchronize(s));
+  // the reduction used beta_t = tau_t kappa / h: it holds kappa sum_t tau_t lam_t^T K u_t
+  *g_kappa = -c.host_small[960] / c.kappa;
+  return AAO_OK;
+}
+
+int aao_profile_enable(aao_ctx *ctx, int on) {
+  if (!ctx) return AAO_EINVAL;
+  ctx->c.prof_on = on != 0;
+  return AAO_OK;
+}
+
+int aao_profile_read(aao_ctx *ctx, double *ms, int64_t *launches, int reset) {
+  if (!ctx) return AAO_EINVAL;
+  Ctx &c = ctx->c;
+  AAO_CK(c, collect(c));
+  for (int k = 0; k < AAO_K_COUNT; k++) {
+    if (ms) ms[k] = c.prof_ms[k];
+    if (launches) launches[k] = c.launches[k];
+    if (reset) {
+      c.prof_ms[k] = 0.0;
+      c.launches[k] = 0;
+    }
+  }
+  return AAO_OK;
+}
+
+int64_t aao_kernel_launches(const aao_ctx *ctx) {
+  if (!ctx) return 0;
+  int64_t total = 0;
+  for (int k = 0; k < AAO_K_COUNT; k++) total += ctx->c.launches[k];
+  return total;
+}
+
+int aao_solve_host(aao_ctx *ctx, const double *u0_host, const double *v0_host, double *U_host,
+                   int restart, double rtol, int maxit, int precond, aao_solve_info *info,
+                   void *stream) {
+  if (!ctx || !u0_host || !U_host) return AAO_EINVAL;
+  Ctx &c = ctx->c;
+  if (restart < 1 || restart > kMaxRestart || check_ws(c, restart) != AAO_OK) return AAO_EINVAL;
+  const aao::WsLayout L = aao::ws_layout(c, restart);
+  cudaStream_t s = as_stream(stream);
+  double *db = vec_at(c, L, 2 * restart + 1);
+  double *dx = vec_at(c, L, 2 * restart + 2);
+  // u0 and v0 go to the x buffer (n and 2n doubles) before x is zeroed
+  const size_t nb = (size_t)c.n * sizeof(double);
+  if ((size_t)c.N < 2 * (size_t)c.n && v0_host) return AAO_EUNSUPPORTED;
+  AAO_CK(c, cudaMemcpyAsync(dx, u0_host, nb, cudaMemcpyHostToDevice, s));
+  if (v0_host) AAO_CK(c, cudaMemcpyAsync(dx + c.n, v0_host, nb, cudaMemcpyHostToDevice, s));
+  AAO_CK(c, run(c, AAO_K_OTHER, s, [&] { return aao::launch_rhs(c, dx, v0_host ? dx + c.n : nullptr, db, s); }));
+  AAO_CK(c, cudaMemsetAsync(dx, 0, (size_t)c.N * sizeof(double), s));
+  const int st = solve_core(c, 0, db, dx, restart, rtol, maxit, precond, info, s);
+  if (st < 0) return st;
+  AAO_CK(c, cudaMemcpyAsync(U_host, dx, (size_t)c.N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  AAO_CK(c, cudaStreamSynchronize(s));
+  return st;
+}
+
+}  // extern "C"

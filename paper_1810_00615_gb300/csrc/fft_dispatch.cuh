@@ -1,0 +1,70 @@
+// Instantiation and dispatch of the time-axis FFT kernels for one real type.
+#pragma once
+#include "fft_time.cuh"
+
+namespace aao {
+namespace fft {
+
+template <typename R, int L>
+static cudaError_t run_forward(int64_t n, int64_t n_pad, const double *x, const double *y,
+                               const R *sigk, cx<R> *spec, const cx<R> *tw, cudaStream_t s) {
+  using S = Shape<R, L>;
+  const int W = 2 * S::C;
+  const unsigned grid = (unsigned)((n + W - 1) / W);
+  cudaError_t e;
+  if (y) {
+    e = cudaFuncSetAttribute(k_fft_forward<R, L, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    if (e != cudaSuccess) return e;
+    k_fft_forward<R, L, true><<<grid, S::T, S::SMEM, s>>>(x, y, sigk, spec, (int)n, n_pad, tw); note_launch();
+  } else {
+    e = cudaFuncSetAttribute(k_fft_forward<R, L, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    if (e != cudaSuccess) return e;
+    k_fft_forward<R, L, false><<<grid, S::T, S::SMEM, s>>>(x, nullptr, nullptr, spec, (int)n,
+                                                           n_pad, tw); note_launch();
+  }
+  return cudaGetLastError();
+}
+
+template <typename R, int L>
+static cudaError_t run_inverse(int64_t n, int64_t n_pad, const cx<R> *spec, double *y,
+                               const cx<R> *tw, cudaStream_t s) {
+  using S = Shape<R, L>;
+  const int W = 2 * S::C;
+  const unsigned grid = (unsigned)((n + W - 1) / W);
+  cudaError_t e = cudaFuncSetAttribute(k_fft_inverse<R, L>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)S::SMEM);
+  if (e != cudaSuccess) return e;
+  k_fft_inverse<R, L><<<grid, S::T, S::SMEM, s>>>(spec, y, (int)n, n_pad, tw); note_launch();
+  return cudaGetLastError();
+}
+
+#define AAO_FFT_CASES(X) \
+  X(1) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
+
+template <typename R>
+cudaError_t forward_any(int64_t ell, int64_t n, int64_t n_pad, const double *x, const double *y,
+                        const R *sigk, cx<R> *spec, const cx<R> *tw, cudaStream_t s) {
+  switch (ell) {
+#define AAO_F(L) case L: return run_forward<R, L>(n, n_pad, x, y, sigk, spec, tw, s);
+    AAO_FFT_CASES(AAO_F)
+#undef AAO_F
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename R>
+cudaError_t inverse_any(int64_t ell, int64_t n, int64_t n_pad, const cx<R> *spec, double *y,
+                        const cx<R> *tw, cudaStream_t s) {
+  switch (ell) {
+#define AAO_I(L) case L: return run_inverse<R, L>(n, n_pad, spec, y, tw, s);
+    AAO_FFT_CASES(AAO_I)
+#undef AAO_I
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace fft
+}  // namespace aao

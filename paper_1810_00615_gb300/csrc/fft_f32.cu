@@ -1,0 +1,14 @@
+// FP32 instantiation of the time-axis FFTs (the mixed-precision preconditioner).
+#include "fft_dispatch.cuh"
+
+namespace aao {
+cudaError_t fft_forward_f32(const Ctx &c, const double *x, const double *y, void *spec,
+                            cudaStream_t s) {
+  return fft::forward_any<float>(c.ell, c.n, c.n_pad, x, y, c.sigk32,
+                                 static_cast<cx<float> *>(spec), c.tw32, s);
+}
+cudaError_t fft_inverse_f32(const Ctx &c, const void *spec, double *y, cudaStream_t s) {
+  return fft::inverse_any<float>(c.ell, c.n, c.n_pad, static_cast<const cx<float> *>(spec), y,
+                                 c.tw32, s);
+}
+}  // namespace aao

@@ -1,0 +1,307 @@
+// Batched real FFT along the time axis of an ell x n block vector (Section 3,
+// the FFT route to (U* (x) I_n) z: a "vector transpose" so that each spatial
+// index i owns a length-ell time series, then one FFT per series).
+//
+// GB300 design.  One CTA owns a panel of 2C consecutive spatial columns and
+// all ell time samples, so the transpose never leaves the SM: the panel is
+// read row by row (2C contiguous doubles per time step, coalesced across the
+// warp), packed two real columns per complex column, transformed in shared
+// memory by self-sorting (Stockham) radix-16/8/4/2 passes with every thread
+// holding E = 16 points in registers between two barriers, and written out as
+// the half spectrum k = 0..ell/2, row k contiguous in the spatial index (the
+// layout the per-frequency tridiagonal solves read).  The inverse kernel runs
+// the same passes backwards from the half spectrum.
+#pragma once
+#include "aao_internal.cuh"
+
+namespace aao {
+namespace fft {
+
+// Shared-memory index of time sample e, complex column c: one padding row per
+// 16 time samples keeps the strided writes of the first pass spread over the
+// banks.
+template <int C>
+__device__ __forceinline__ int phys(int e, int c) { return (e + (e >> 4)) * C + c; }
+
+template <int L> struct Plan {
+  static constexpr int LOG2 = (L <= 1) ? 0 : 1 + Plan<(L >> 1)>::LOG2;
+};
+template <> struct Plan<1> { static constexpr int LOG2 = 0; };
+
+// Twiddle multiply by exp(DIR * 2 pi i m / L) with the table tw[m] =
+// exp(-2 pi i m / L): forward (DIR = -1) uses tw, inverse its conjugate.
+template <typename R, int DIR>
+__device__ __forceinline__ cx<R> twiddle(cx<R> v, cx<R> w) {
+  if (DIR > 0) w.im = -w.im;
+  return v * w;
+}
+
+// multiply by DIR*i : forward (DIR = -1) -i, inverse +i
+template <typename R, int DIR>
+__device__ __forceinline__ cx<R> rot90(cx<R> a) {
+  return (DIR < 0) ? mk(a.im, -a.re) : mk(-a.im, a.re);
+}
+
+template <typename R, int DIR>
+__device__ __forceinline__ void dft2(cx<R> &a, cx<R> &b) {
+  cx<R> t = a - b;
+  a = a + b;
+  b = t;
+}
+
+// In-place 4-point DFT, natural order in and out.
+template <typename R, int DIR>
+__device__ __forceinline__ void dft4(cx<R> &a0, cx<R> &a1, cx<R> &a2, cx<R> &a3) {
+  cx<R> t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3, t3 = rot90<R, DIR>(a1 - a3);
+  a0 = t0 + t2;
+  a2 = t0 - t2;
+  a1 = t1 + t3;
+  a3 = t1 - t3;
+}
+
+// constants cos(pi/4), cos(pi/8), sin(pi/8)
+#define AAO_C4 0.70710678118654752440
+#define AAO_C8 0.92387953251128675613
+#define AAO_S8 0.38268343236508977173
+
+// Multiply by w_R^(q k) = exp(DIR 2 pi i q k / R) for R = 8 or 16, q k < R*R/4.
+template <typename R, int DIR>
+__device__ __forceinline__ cx<R> rot_by(cx<R> a, int m, int Rn) {
+  // m in units of 2 pi / Rn, reduced mod Rn
+  m &= (Rn - 1);
+  // express angle as multiple of 2 pi / 16
+  int m16 = m * (16 / Rn);
+  R c, s;
+  switch (m16) {
+    case 0: return a;
+    case 1: c = (R)AAO_C8; s = (R)AAO_S8; break;
+    case 2: c = (R)AAO_C4; s = (R)AAO_C4; break;
+    case 3: c = (R)AAO_S8; s = (R)AAO_C8; break;
+    case 4: return rot90<R, DIR>(a);
+    case 5: c = -(R)AAO_S8; s = (R)AAO_C8; break;
+    case 6: c = -(R)AAO_C4; s = (R)AAO_C4; break;
+    case 7: c = -(R)AAO_C8; s = (R)AAO_S8; break;
+    case 8: return mk(-a.re, -a.im);
+    case 9: c = -(R)AAO_C8; s = -(R)AAO_S8; break;
+    case 10: c = -(R)AAO_C4; s = -(R)AAO_C4; break;
+    case 11: c = -(R)AAO_S8; s = -(R)AAO_C8; break;
+    case 12: return rot90<R, -DIR>(a);
+    case 13: c = (R)AAO_S8; s = -(R)AAO_C8; break;
+    case 14: c = (R)AAO_C4; s = -(R)AAO_C4; break;
+    default: c = (R)AAO_C8; s = -(R)AAO_S8; break;
+  }
+  // exp(DIR i theta) with theta = m16 * 2pi/16: (c, DIR*s)
+  const R sd = (DIR < 0) ? -s : s;
+  return mk(a.re * c - a.im * sd, a.re * sd + a.im * c);
+}
+
+// In-place RAD-point DFT of v[0..RAD), natural order in and out.
+template <typename R, int DIR, int RAD>
+__device__ __forceinline__ void dft(cx<R> *v) {
+  if constexpr (RAD == 1) {
+    return;
+  } else if constexpr (RAD == 2) {
+    dft2<R, DIR>(v[0], v[1]);
+  } else if constexpr (RAD == 4) {
+    dft4<R, DIR>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (RAD == 8) {
+    // n = q + 2m (q < 2, m < 4), k = k1 + 4 k2
+    cx<R> b[2][4];
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+      b[q][0] = v[q]; b[q][1] = v[q + 2]; b[q][2] = v[q + 4]; b[q][3] = v[q + 6];
+      dft4<R, DIR>(b[q][0], b[q][1], b[q][2], b[q][3]);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; k1++) {
+      cx<R> x0 = b[0][k1], x1 = rot_by<R, DIR>(b[1][k1], k1, 8);
+      v[k1] = x0 + x1;
+      v[k1 + 4] = x0 - x1;
+    }
+  } else {
+    static_assert(RAD == 16, "radix");
+    // n = q + 4m, k = k1 + 4 k2
+    cx<R> b[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      b[q][0] = v[q]; b[q][1] = v[q + 4]; b[q][2] = v[q + 8]; b[q][3] = v[q + 12];
+      dft4<R, DIR>(b[q][0], b[q][1], b[q][2], b[q][3]);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; k1++) {
+      cx<R> x0 = b[0][k1];
+      cx<R> x1 = rot_by<R, DIR>(b[1][k1], k1, 16);
+      cx<R> x2 = rot_by<R, DIR>(b[2][k1], 2 * k1, 16);
+      cx<R> x3 = rot_by<R, DIR>(b[3][k1], 3 * k1, 16);
+      dft4<R, DIR>(x0, x1, x2, x3);
+      v[k1] = x0; v[k1 + 4] = x1; v[k1 + 8] = x2; v[k1 + 12] = x3;
+    }
+  }
+}
+
+// One Stockham pass of radix RAD over C columns of length L held in shared
+// memory (Govindaraju et al. 2008 formulation): butterfly j reads
+// x[j + r L/RAD], multiplies by exp(DIR 2 pi i (j mod Ns) r / (Ns RAD)),
+// transforms, and writes x'[(j/Ns) Ns RAD + (j mod Ns) + r Ns].
+template <typename R, int L, int C, int RAD, int DIR, int T>
+__device__ __forceinline__ void pass(cx<R> *sm, int Ns, const cx<R> *__restrict__ tw) {
+  constexpr int E = (L < 16) ? L : 16;
+  constexpr int NB = E / RAD;
+  cx<R> v[NB][RAD];
+  int jj[NB], cc[NB];
+#pragma unroll
+  for (int q = 0; q < NB; q++) {
+    const int b = threadIdx.x + q * T;
+    cc[q] = b % C;
+    jj[q] = b / C;
+#pragma unroll
+    for (int r = 0; r < RAD; r++) v[q][r] = sm[phys<C>(jj[q] + r * (L / RAD), cc[q])];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NB; q++) {
+    const int j = jj[q];
+    const int jm = j % Ns;
+    if (Ns > 1) {
+      const int step = jm * (L / (Ns * RAD));
+#pragma unroll
+      for (int r = 1; r < RAD; r++) v[q][r] = twiddle<R, DIR>(v[q][r], tw[step * r]);
+    }
+    dft<R, DIR, RAD>(v[q]);
+    const int base = (j / Ns) * Ns * RAD + jm;
+#pragma unroll
+    for (int r = 0; r < RAD; r++) sm[phys<C>(base + r * Ns, cc[q])] = v[q][r];
+  }
+  __syncthreads();
+}
+
+// Full length-L transform of the C columns in shared memory.
+template <typename R, int L, int C, int DIR, int T>
+__device__ __forceinline__ void transform(cx<R> *sm, const cx<R> *__restrict__ tw) {
+  constexpr int LOG2 = Plan<L>::LOG2;
+  if constexpr (L == 1) {
+    return;
+  } else if constexpr (L <= 16) {
+    pass<R, L, C, L, DIR, T>(sm, 1, tw);
+  } else {
+    constexpr int NP = (LOG2 + 3) / 4;               // number of passes
+    constexpr int R1 = 1 << (LOG2 - 4 * (NP - 1));   // first radix
+    pass<R, L, C, R1, DIR, T>(sm, 1, tw);
+    int Ns = R1;
+#pragma unroll
+    for (int p = 1; p < NP; p++) {
+      pass<R, L, C, 16, DIR, T>(sm, Ns, tw);
+      Ns *= 16;
+    }
+  }
+}
+
+template <typename R> struct Cap;   // complex points of shared memory per CTA
+template <> struct Cap<float> { static constexpr int V = 16384; };
+template <> struct Cap<double> { static constexpr int V = 8192; };
+
+template <typename R, int L> struct Shape {
+  static constexpr int C0 = Cap<R>::V / L;
+  static constexpr int C = C0 > 16 ? 16 : (C0 < 1 ? 1 : C0);   // complex columns
+  static constexpr int E = (L < 16) ? L : 16;                   // points per thread
+  static constexpr int T = L * C / E;                           // threads
+  static constexpr size_t SMEM = (size_t)(L + (L >> 4) + 1) * C * sizeof(cx<R>);
+};
+
+// Forward: x (FP64, ell x n) -> half spectrum (R complex, nk x n_pad).
+// NEUMANN: the input is x - E y with (E y)_t = sigk_t (2 y_i - y_{i-1} - y_{i+1}),
+// sigk_t = (tau_t - tau) kappa / h (Section 2, E = sigma (x) kappa K).
+template <typename R, int L, bool NEUMANN>
+__global__ void __launch_bounds__(Shape<R, L>::T)
+k_fft_forward(const double *__restrict__ x, const double *__restrict__ y,
+              const R *__restrict__ sigk, cx<R> *__restrict__ spec, int n, int64_t n_pad,
+              const cx<R> *__restrict__ tw) {
+  using S = Shape<R, L>;
+  constexpr int C = S::C, T = S::T, W = 2 * C;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
+  R *smr = reinterpret_cast<R *>(smraw);
+  const int i0 = blockIdx.x * W;
+
+  // load the panel: time row t, column w -> real (w even) / imaginary part
+  // of complex column w/2
+#pragma unroll 8
+  for (int idx = threadIdx.x; idx < L * W; idx += T) {
+    const int t = idx / W, w = idx - t * W, i = i0 + w;
+    R v = (R)0;
+    if (i < n) {
+      const size_t o = (size_t)t * n + i;
+      if constexpr (NEUMANN) {
+        const R yc = from_f64<R>(__ldg(&y[o]));
+        const R yl = (i > 0) ? from_f64<R>(__ldg(&y[o - 1])) : (R)0;
+        const R yr = (i + 1 < n) ? from_f64<R>(__ldg(&y[o + 1])) : (R)0;
+        const R ky = (yc + yc) - yl - yr;
+        v = from_f64<R>(__ldg(&x[o])) - __ldg(&sigk[t]) * ky;
+      } else {
+        v = from_f64<R>(__ldg(&x[o]));
+      }
+    }
+    smr[2 * phys<C>(t, w >> 1) + (w & 1)] = v;
+  }
+  __syncthreads();
+
+  transform<R, L, C, -1, T>(sm, tw);
+
+  // unpack the two real columns of each complex column and write k = 0..L/2
+  constexpr int NK = L / 2 + 1;
+  for (int idx = threadIdx.x; idx < NK * C; idx += T) {
+    const int k = idx / C, c = idx - k * C;
+    const cx<R> zk = sm[phys<C>(k, c)];
+    const cx<R> zm = sm[phys<C>((L - k) & (L - 1), c)];
+    const R hf = (R)0.5;
+    const cx<R> X = mk(hf * (zk.re + zm.re), hf * (zk.im - zm.im));
+    const cx<R> Y = mk(hf * (zk.im + zm.im), hf * (zm.re - zk.re));
+    const int i = i0 + 2 * c;
+    cx<R> *dst = spec + (size_t)k * n_pad + i;
+    if (i + 1 < n) {
+      dst[0] = X;
+      dst[1] = Y;
+    } else if (i < n) {
+      dst[0] = X;
+    }
+  }
+}
+
+// Inverse: half spectrum -> y (FP64), scaled by 1/L.
+template <typename R, int L>
+__global__ void __launch_bounds__(Shape<R, L>::T)
+k_fft_inverse(const cx<R> *__restrict__ spec, double *__restrict__ y, int n, int64_t n_pad,
+              const cx<R> *__restrict__ tw) {
+  using S = Shape<R, L>;
+  constexpr int C = S::C, T = S::T, W = 2 * C;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
+  const int i0 = blockIdx.x * W;
+  constexpr int NK = L / 2 + 1;
+  for (int idx = threadIdx.x; idx < NK * C; idx += T) {
+    const int k = idx / C, c = idx - k * C;
+    const int i = i0 + 2 * c;
+    const cx<R> *src = spec + (size_t)k * n_pad + i;
+    cx<R> A = mk((R)0, (R)0), B = mk((R)0, (R)0);
+    if (i < n) A = src[0];
+    if (i + 1 < n) B = src[1];
+    if (k == 0 || 2 * k == L) { A.im = (R)0; B.im = (R)0; }
+    // Z = A + i B for the pair of real outputs; Hermitian extension for L-k
+    sm[phys<C>(k, c)] = mk(A.re - B.im, A.im + B.re);
+    if (k > 0 && 2 * k < L) sm[phys<C>(L - k, c)] = mk(A.re + B.im, B.re - A.im);
+  }
+  __syncthreads();
+
+  transform<R, L, C, +1, T>(sm, tw);
+
+  const R scale = (R)1 / (R)L;
+  const R *smr = reinterpret_cast<const R *>(smraw);
+#pragma unroll 8
+  for (int idx = threadIdx.x; idx < L * W; idx += T) {
+    const int t = idx / W, w = idx - t * W, i = i0 + w;
+    if (i < n) y[(size_t)t * n + i] = to_double<R>(scale * smr[2 * phys<C>(t, w >> 1) + (w & 1)]);
+  }
+}
+
+}  // namespace fft
+}  // namespace aao

@@ -1,0 +1,166 @@
+// Per-frequency complex tridiagonal solves (Section 3: after the Fourier
+// diagonalisation, I (x) A0 + Lambda (x) A1 is block diagonal and each block
+// A0 + w_k A1 (+ w_k^2 A2) is tridiagonal; the paper assigns one block per
+// process and applies the Thomas algorithm).
+//
+// GB300 design: one CTA per frequency k, one thread per chunk of CH-1
+// unknowns plus the separator unknown that follows it.  Every thread loads
+// its CH contiguous spectrum values straight into registers (128 bytes), so
+// the row is read and written exactly once.
+//   1. Local Dirichlet solve of each chunk with the chunk LU, whose pivots are
+//      shared by all chunks of a row (constant coefficients) and precomputed.
+//   2. The separators satisfy a tridiagonal Schur-complement system (one row
+//      per separator) whose coefficients follow from the chunk Green's
+//      functions (precomputed); it is solved by parallel cyclic reduction in
+//      shared memory, written in "row excess" form: each row keeps
+//      sigma = a + b + c instead of its diagonal b, which is how the smooth,
+//      nearly singular low frequencies (k = 0 is tau*kappa*K, the Laplacian)
+//      keep their accuracy in FP32.
+//   3. Each chunk is corrected with the two separator values around it.
+#include "aao_internal.cuh"
+
+namespace aao {
+
+template <typename R>
+__device__ __forceinline__ cx<R> cdiv(cx<R> a, cx<R> b) {
+  const R d = (R)1 / (b.re * b.re + b.im * b.im);
+  return mk((a.re * b.re + a.im * b.im) * d, (a.im * b.re - a.re * b.im) * d);
+}
+
+template <typename R>
+__device__ __forceinline__ cx<R> ld_tab(const cx<R> &v, int conj) {
+  cx<R> z = v;
+  if (conj) z.im = -z.im;
+  return z;
+}
+
+template <typename R, int CH>
+__global__ void __launch_bounds__(1024)
+k_tridiag(cx<R> *__restrict__ spec, int n, int64_t n_pad, const TriTab<R, CH> *__restrict__ tabs,
+          int conj_sym) {
+  const int k = blockIdx.x;
+  const int p = threadIdx.x;        // chunk index
+  const int P = blockDim.x;         // chunks in the row
+  const int M = P - 1;              // separators
+  __shared__ cx<R> s_invp[CH], s_bp[CH], s_fc[CH], s_fl[CH], s_sc[5];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cx<R> *buf = reinterpret_cast<cx<R> *>(smraw);   // [2][4][M] PCR rows
+  cx<R> *s_first = buf + 8 * M;                     // [P] first local value of each chunk
+  cx<R> *s_sep = s_first + P;                       // [M] separator solution
+
+  const TriTab<R, CH> *tb = tabs + k;
+  for (int i = p; i < CH; i += P) {
+    s_invp[i] = ld_tab(tb->invp[i], conj_sym);
+    s_bp[i] = ld_tab(tb->bp[i], conj_sym);
+    s_fc[i] = ld_tab(tb->fc[i], conj_sym);
+    s_fl[i] = ld_tab(tb->fl[i], conj_sym);
+  }
+  if (p == 0) {
+    s_sc[0] = ld_tab(tb->e, conj_sym);
+    s_sc[1] = ld_tab(tb->sig_reg, conj_sym);
+    s_sc[2] = ld_tab(tb->off_reg, conj_sym);
+    s_sc[3] = ld_tab(tb->sig_last, conj_sym);
+    s_sc[4] = ld_tab(tb->off_last, conj_sym);
+  }
+
+  cx<R> *row = spec + (size_t)k * n_pad;
+  const int base = p * CH;
+  const int len = (p == M) ? (n - base) : (CH - 1);   // unknowns of this chunk
+  cx<R> v[CH];
+#pragma unroll
+  for (int i = 0; i < CH; i++) v[i] = (base + i < n) ? row[base + i] : mk((R)0, (R)0);
+  __syncthreads();
+
+  const cx<R> e = s_sc[0];
+  const cx<R> sep_rhs = v[CH - 1];
+  // 1. local solve: forward elimination then back substitution
+  v[0] = v[0] * s_invp[0];
+#pragma unroll
+  for (int i = 1; i < CH; i++)
+    if (i < len) v[i] = cfnms(v[i], e, v[i - 1]) * s_invp[i];
+#pragma unroll
+  for (int i = CH - 2; i >= 0; i--)
+    if (i < len - 1) v[i] = cfnms(v[i], s_bp[i], v[i + 1]);
+
+  if (M > 0) {
+    // 2. separator (Schur complement) system
+    s_first[p] = v[0];
+    __syncthreads();
+    if (p < M) {
+      const cx<R> r = cfnms(sep_rhs, e, v[CH - 2] + s_first[p + 1]);
+      const bool last = (p == M - 1);
+      buf[0 * M + p] = s_sc[2];                          // a: left coupling
+      buf[1 * M + p] = last ? s_sc[3] : s_sc[1];         // sigma: row excess
+      buf[2 * M + p] = last ? s_sc[4] : s_sc[2];         // c: right coupling
+      buf[3 * M + p] = r;
+    }
+    __syncthreads();
+    int cur = 0;
+    for (int s = 1; s < M; s <<= 1) {
+      if (p < M) {
+        const cx<R> *B = buf + cur * 4 * M;
+        cx<R> *O = buf + (1 - cur) * 4 * M;
+        const cx<R> a = B[p], sg = B[M + p], c = B[2 * M + p], r = B[3 * M + p];
+        cx<R> aL = mk((R)0, (R)0), sL = mk((R)1, (R)0), cL = aL, rL = aL;
+        cx<R> aR = aL, sR = sL, cR = aL, rR = aL;
+        if (p - s >= 0) { aL = B[p - s]; sL = B[M + p - s]; cL = B[2 * M + p - s]; rL = B[3 * M + p - s]; }
+        if (p + s < M) { aR = B[p + s]; sR = B[M + p + s]; cR = B[2 * M + p + s]; rR = B[3 * M + p + s]; }
+        const cx<R> bL = sL - aL - cL, bR = sR - aR - cR;
+        const cx<R> al = cdiv(a, bL), ga = cdiv(c, bR);
+        O[p] = mk((R)0, (R)0) - al * aL;
+        O[2 * M + p] = mk((R)0, (R)0) - ga * cR;
+        O[M + p] = cfnms(cfnms(sg, al, sL), ga, sR);
+        O[3 * M + p] = cfnms(cfnms(r, al, rL), ga, rR);
+      }
+      __syncthreads();
+      cur ^= 1;
+    }
+    if (p < M) {
+      const cx<R> *B = buf + cur * 4 * M;
+      const cx<R> b = B[M + p] - B[p] - B[2 * M + p];
+      s_sep[p] = cdiv(B[3 * M + p], b);
+    }
+    __syncthreads();
+    // 3. correction with the separator values on both sides
+    const cx<R> sl = (p > 0) ? s_sep[p - 1] : mk((R)0, (R)0);
+    if (p < M) {
+      const cx<R> sr = s_sep[p];
+#pragma unroll
+      for (int i = 0; i < CH - 1; i++) v[i] = cfma(cfma(v[i], sl, s_fc[i]), sr, s_fc[CH - 2 - i]);
+      v[CH - 1] = sr;
+    } else {
+#pragma unroll
+      for (int i = 0; i < CH; i++)
+        if (i < len) v[i] = cfma(v[i], sl, s_fl[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < CH; i++)
+    if (base + i < n) row[base + i] = v[i];
+}
+
+template <typename R, int CH>
+static cudaError_t run_tridiag(const Ctx &c, void *spec, const void *tab, int P, int conj,
+                               cudaStream_t s) {
+  const int M = P - 1;
+  const size_t smem = (size_t)(8 * M + P + M) * sizeof(cx<R>);
+  cudaError_t e = cudaFuncSetAttribute(k_tridiag<R, CH>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_tridiag<R, CH><<<(unsigned)c.nk, P, smem, s>>>(
+      static_cast<cx<R> *>(spec), (int)c.n, c.n_pad,
+      static_cast<const TriTab<R, CH> *>(tab), conj); note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tridiag(const Ctx &c, void *spec, int prec, int transpose, cudaStream_t s) {
+  if (prec == AAO_PREC_FP32) {
+    if (c.ch32 == 16) return run_tridiag<float, 16>(c, spec, c.tab32, c.P32, transpose, s);
+    return cudaErrorInvalidValue;
+  }
+  if (c.ch64 == 8) return run_tridiag<double, 8>(c, spec, c.tab64, c.P64, transpose, s);
+  if (c.ch64 == 16) return run_tridiag<double, 16>(c, spec, c.tab64, c.P64, transpose, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace aao

@@ -1,0 +1,75 @@
+"""Parity of the FP64 all-at-once matvec and right-hand side (Section 2) with
+the oracle.  Both sides are FP64 sums of a handful of products; the GPU
+evaluates the same operator in a different order (differences of
+neighbours), so the agreement is a few ulps of the largest term: the
+tolerance 1e-13 relative to max|y| allows ~500 ulps."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import system
+from tests._helpers import need_gpu, oracle_system, rand_block, rel_max, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n,ell", [(1, 1), (2, 3), (5, 7), (33, 16), (255, 64), (1000, 9)])
+@pytest.mark.parametrize("kind", ["heat", "wave_bd2", "heat_literal", "steps"])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_matvec_matches_oracle(n, ell, kind, transpose):
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    if (ell & (ell - 1)) != 0:
+        pytest.skip("contexts need a power-of-two ell")
+    taus = syn.time_steps(ell, 0.6, syn.rng(ell)) if kind == "steps" else None
+    S = oracle_system("heat" if kind == "steps" else kind, n, ell, kappa=1.0, taus=taus)
+    X = rand_block(n, ell, 3 + n)
+    want = system.matvec_T(S, X) if transpose else system.matvec(S, X)
+    a = AllAtOnce(n, ell, 1.0 / ell, equation="heat" if kind == "steps" else kind, restart=1)
+    if taus is not None:
+        a.set_steps(taus)
+    got = to_host(a.matvec(to_dev(torch, X), transpose=transpose))
+    assert rel_max(got, want) <= 1e-13
+
+
+@pytest.mark.parametrize("ell", [1, 2, 8, 64])
+def test_matvec_kappa(ell):
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    n = 40
+    S = oracle_system("heat", n, ell, kappa=2.5)
+    X = rand_block(n, ell, 4)
+    a = AllAtOnce(n, ell, 1.0 / ell, kappa=2.5, restart=1)
+    assert rel_max(to_host(a.matvec(to_dev(torch, X))), system.matvec(S, X)) <= 1e-13
+
+
+def test_matvec_full_size():
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    n, ell = 4095, 4096
+    S = oracle_system("heat", n, ell)
+    X = rand_block(n, ell, 5)
+    a = AllAtOnce(n, ell, 1.0 / ell, restart=1)
+    got = to_host(a.matvec(to_dev(torch, X)))
+    assert rel_max(got, system.matvec(S, X)) <= 1e-13
+    got = to_host(a.matvec(to_dev(torch, X), transpose=True))
+    assert rel_max(got, system.matvec_T(S, X)) <= 1e-13
+
+
+@pytest.mark.parametrize("kind", ["heat", "wave_bd2", "heat_literal"])
+@pytest.mark.parametrize("with_v0", [False, True])
+def test_rhs_matches_oracle(kind, with_v0):
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    if with_v0 and kind != "wave_bd2":
+        pytest.skip("initial velocity is a wave input")
+    n, ell = 63, 16
+    S = oracle_system(kind, n, ell)
+    u0, v0 = syn.wave_initial(n, modes=16)
+    a = AllAtOnce(n, ell, 1.0 / ell, equation=kind, restart=1)
+    if kind == "wave_bd2":
+        want = system.rhs_bd2(S, u0, v0 if with_v0 else None)
+    else:
+        want = system.rhs_heat(S, u0)
+    got = to_host(a.build_rhs(to_dev(torch, u0), to_dev(torch, v0) if with_v0 else None))
+    assert rel_max(got, want) <= 1e-13

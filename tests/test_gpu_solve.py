@@ -1,0 +1,205 @@
+"""Flexible-GMRES solves on the GPU against the oracle's exact all-at-once
+solution (forward substitution, i.e. time stepping itself), at the workload
+sizes.  Acceptance (both precisions of the preconditioner): true relative
+residual ||b - A x|| / ||b|| <= 1e-10, re-computed here by the oracle's
+matvec, and relative solution error <= 1e-8 in the max norm.
+"""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import adjoint, fem, system
+from tests._helpers import need_gpu, oracle_system, rel_max, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(S, B, X, rtol=1e-10, errtol=1e-8):
+    U = system.forward_substitution(S, B)
+    R = B - system.matvec(S, X)
+    relres = np.linalg.norm(R) / np.linalg.norm(B)
+    assert relres <= rtol, relres
+    assert rel_max(X, U) <= errtol, rel_max(X, U)
+    return U
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_heat_n63_ell64_single_mode(prec):
+    """n = 63, ell = 64, u0 = L2 projection of sin(pi x), GMRES(30), 1e-10."""
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    n, ell = 63, 64
+    S = oracle_system("heat", n, ell)
+    u0 = fem.l2_projection(lambda x: np.sin(np.pi * x), n)
+    a = AllAtOnce(n, ell, 1.0 / ell, precision=prec, restart=30)
+    b = a.build_rhs(to_dev(torch, u0))
+    x, info = a.solve(b, restart=30, rtol=1e-10)
+    assert info["converged"]
+    X = to_host(x)
+    _check(S, system.rhs_heat(S, u0), X)
+    # b and A P^{-1} b are parallel for one sine mode: one iteration with the
+    # exact circulant (FP64); the FP32 circulant needs a couple more
+    assert info["iters"] <= (2 if prec == "fp64" else 4)
+    # the closed form u_t = rho^t u0
+    h = 1.0 / (n + 1)
+    th = np.pi * h
+    m = (h / 6) * (4 + 2 * np.cos(th))
+    k = (2 / h) * (1 - np.cos(th))
+    rho = m / (m + k / ell)
+    expect = np.array([rho ** (t + 1) * u0 for t in range(ell)])
+    assert rel_max(X, expect) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_heat_n4095_ell4096(prec):
+    """The benchmark workload: 8 seeded sine modes, FGMRES(30), 1e-10."""
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    n, ell = 4095, 4096
+    S = oracle_system("heat", n, ell)
+    u0 = syn.heat_initial(n, modes=8)
+    a = AllAtOnce(n, ell, 1.0 / ell, precision=prec, restart=30)
+    x, info = a.solve(a.build_rhs(to_dev(torch, u0)), restart=30, rtol=1e-10)
+    assert info["converged"], info
+    _check(S, system.rhs_heat(S, u0), to_host(x))
+
+
+def test_wave_bd2_n8191_ell2048():
+    """BD2 with 16-mode displacement and velocity, FP32 preconditioner,
+    FGMRES(40), 1e-10."""
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    n, ell = 8191, 2048
+    S = oracle_system("wave_bd2", n, ell)
+    u0, v0 = syn.wave_initial(n, modes=16)
+    a = AllAtOnce(n, ell, 1.0 / ell, equation="wave_bd2", precision="fp32", restart=40)
+    x, info = a.solve(a.build_rhs(to_dev(torch, u0), to_dev(torch, v0)), restart=40, rtol=1e-10)
+    assert info["converged"], info
+    _check(S, system.rhs_bd2(S, u0, v0), to_host(x))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_neumann_variable_steps(prec):
+    """System B with the perturbed grid (delta = 0.5): every preconditioner
+    (P, Q_2, Q_3) reaches the oracle's solution; iteration counts do not
+    increase with the number of Neumann terms (Table 2 trend)."""
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    n, ell = 255, 256
+    taus = syn.time_steps(ell, 0.5, syn.rng(17))
+    S = oracle_system("heat", n, ell, taus=taus)
+    u0 = syn.heat_initial(n)
+    a = AllAtOnce(n, ell, 1.0 / ell, precision=prec, restart=30)
+    a.set_steps(taus)
+    b = a.build_rhs(to_dev(torch, u0))
+    B = system.rhs_heat(S, u0)
+    its = []
+    for pc in (1, 2, 3):
+        x, info = a.solve(b, restart=30, rtol=1e-10, precond=pc)
+        assert info["converged"], (pc, info)
+        _check(S, B, to_host(x))
+        its.append(info["iters"])
+    assert its[0] >= its[1] >= its[2]
+
+
+def test_unpreconditioned_and_restarted():
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    n, ell = 15, 16
+    S = oracle_system("heat", n, ell)
+    u0 = syn.heat_initial(n)
+    a = AllAtOnce(n, ell, 1.0 / ell, restart=8)
+    b = a.build_rhs(to_dev(torch, u0))
+    x, info = a.solve(b, restart=8, rtol=1e-10, maxit=2000, precond=0)
+    assert info["converged"] and info["restarts"] > 1
+    _check(S, system.rhs_heat(S, u0), to_host(x))
+
+
+def test_maxit_returns_noconv_with_iterate():
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce, AAO_ENOCONV
+    n, ell = 63, 64
+    a = AllAtOnce(n, ell, 1.0 / ell, restart=30)
+    b = a.build_rhs(to_dev(torch, syn.heat_initial(n)))
+    x, info = a.solve(b, restart=30, rtol=1e-14, maxit=1, precond=0)
+    assert info["status"] == AAO_ENOCONV and info["iters"] == 1
+    assert torch.isfinite(x).all() and x.abs().max() > 0
+
+
+def test_zero_rhs_gives_zero():
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    a = AllAtOnce(7, 8, 1 / 8, restart=4)
+    b = torch.zeros(8, 7, dtype=torch.float64, device="cuda")
+    x, info = a.solve(b, x0=torch.ones(8, 7, dtype=torch.float64, device="cuda"))
+    assert info["converged"] and torch.count_nonzero(x) == 0
+
+
+def test_solve_host_matches_device_solve():
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    n, ell = 255, 256
+    u0 = syn.heat_initial(n)
+    a = AllAtOnce(n, ell, 1.0 / ell, restart=30)
+    x, _ = a.solve(a.build_rhs(to_dev(torch, u0)), restart=30, rtol=1e-10)
+    U, info = a.solve_host(torch.from_numpy(u0), restart=30, rtol=1e-10)
+    assert info["status"] == 0
+    assert torch.equal(U, x.cpu())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_adjoint_n16383_ell1024(prec):
+    """Adjoint workload: loss 1/2 ||U - U_obs||^2, U_obs from a seeded
+    8-mode u0_true plus N(0, 1e-3^2) noise; the adjoint solve matches the
+    oracle's backward substitution and the gradients match the oracle's
+    adjoint gradients to 1e-6 relative."""
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    n, ell = 16383, 1024
+    tau = 1.0 / ell
+    g = syn.rng(2024)
+    u0_true = syn.sine_l2_projection(syn.sine_coefficients(8, g), n)
+    S = oracle_system("heat", n, ell)
+    U_obs = system.forward_substitution(S, system.rhs_heat(S, u0_true))
+    U_obs = U_obs + 1e-3 * g.standard_normal(U_obs.shape)
+    u0 = syn.sine_l2_projection(syn.sine_coefficients(8, g), n)
+    L, gu_want, gk_want, U_want, lam_want = adjoint.gradients(n, ell, tau, 1.0, u0, U_obs)
+    a = AllAtOnce(n, ell, tau, precision=prec, restart=30)
+    x, info = a.solve(a.build_rhs(to_dev(torch, u0)), restart=30, rtol=1e-12)
+    assert info["converged"], info
+    G = x - to_dev(torch, U_obs)
+    lam, info = a.adjoint_solve(G, restart=30, rtol=1e-12)
+    assert info["converged"], info
+    assert rel_max(to_host(lam), lam_want) <= 1e-8
+    gu, gk = a.adjoint_grads(lam, x)
+    assert rel_max(to_host(gu), gu_want) <= 1e-6
+    assert abs(gk - gk_want) <= 1e-6 * abs(gk_want)
+
+
+def test_autograd_function_matches_oracle_and_finite_differences():
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce, AAOSolve
+    n, ell = 63, 64
+    tau = 1.0 / ell
+    g = syn.rng(99)
+    u0 = syn.sine_l2_projection(syn.sine_coefficients(4, g), n)
+    U_obs = g.standard_normal((ell, n)) * 0.01
+    solver = AllAtOnce(n, ell, tau, precision="fp64", restart=30)
+    u0_t = to_dev(torch, u0).requires_grad_(True)
+    k_t = torch.tensor(0.8, dtype=torch.float64, requires_grad=True)
+    U = AAOSolve.apply(u0_t, k_t, solver, 1e-13, 30)
+    loss = 0.5 * ((U - to_dev(torch, U_obs)) ** 2).sum()
+    loss.backward()
+    L, gu, gk, _, _ = adjoint.gradients(n, ell, tau, 0.8, u0, U_obs)
+    assert abs(loss.item() - L) <= 1e-10 * abs(L)
+    assert rel_max(to_host(u0_t.grad), gu) <= 1e-8
+    assert abs(k_t.grad.item() - gk) <= 1e-8 * abs(gk)
+    # central differences in kappa through the GPU solve (h = 1e-6)
+    hs = 1e-6
+    def f(k):
+        with torch.no_grad():
+            Uk = AAOSolve.apply(to_dev(torch, u0), torch.tensor(k, dtype=torch.float64), solver,
+                                1e-13, 30)
+            return 0.5 * float(((Uk - to_dev(torch, U_obs)) ** 2).sum())
+    fd = (f(0.8 + hs) - f(0.8 - hs)) / (2 * hs)
+    assert abs(fd - k_t.grad.item()) <= 1e-6 * abs(k_t.grad.item())

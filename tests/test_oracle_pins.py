@@ -193,6 +193,18 @@ def test_circulant_inverse_matches_dense_lu(kind, ell):
                                np.linalg.solve(C.T, X.ravel()), atol=1e-12)
 
 
+@pytest.mark.parametrize("kind", ["heat", "bd2"])
+def test_circulant_matvec_matches_dense(kind):
+    n, ell = 4, 6
+    S = system.heat(n, ell, 1.0 / ell) if kind == "heat" else system.bd2(n, ell, 1.0 / ell)
+    C = system.dense_circulant(S)
+    X = syn.block_vector(n, ell, syn.rng(3))
+    np.testing.assert_allclose(precond.circulant_matvec(S, X).ravel(), C @ X.ravel(),
+                               atol=1e-13)
+    np.testing.assert_allclose(precond.circulant_matvec(S, X, transpose=True).ravel(),
+                               C.T @ X.ravel(), atol=1e-13)
+
+
 def test_dense_circulant_corner_blocks():
     """P has A1 in the top-right block; R_BD2 has A2, A1 in the top-right and
     A2 in the second row's last block (Section 2 displays)."""
