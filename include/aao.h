@@ -152,8 +152,11 @@ int aao_build_rhs(aao_ctx *ctx, const double *u0, const double *v0, double *b,
  * Arnoldi with classical Gram-Schmidt and re-orthogonalisation, Givens
  * rotations on the host, the true residual recomputed in FP64 at every
  * restart.  precond: 0 none, 1 the circulant P (R_BD2), i >= 2 the Neumann
- * series Q_i^{-1}.  Stops when ||b - A x|| <= rtol ||b|| (true residual) or
- * after maxit Arnoldi steps (AAO_ENOCONV, x holds the last iterate).  x is
+ * series Q_i^{-1}.  Stops when ||b - A x|| <= rtol ||b|| (true residual), or
+ * with AAO_ENOCONV (x holds the last iterate) after maxit Arnoldi steps or
+ * when three restart cycles in a row lower the true residual by less than
+ * 10% (the
+ * FP64 attainable accuracy of x is reached; see aao_solve_info).  x is
  * the initial guess on entry.  info may be NULL.  Needs
  * aao_workspace_bytes(ctx, restart) of workspace.  Synchronises `stream`. */
 int aao_gmres_solve(aao_ctx *ctx, const double *b, double *x, int restart,

@@ -129,7 +129,10 @@ struct Ctx {
   void *tab64 = nullptr;   // TriTab<double, ch64>[nk]
   cx<float> *tw32 = nullptr;      // exp(-2 pi i m/ell), m < ell
   cx<double> *tw64 = nullptr;
-  double *beta = nullptr;         // per-step K coefficient of the matvec (ell)
+  double *beta = nullptr;         // per-step K coefficient tau_t kappa / h (ell)
+  double *mv_d0 = nullptr;        // per-step diagonal of A0^t (ell)
+  double *mv_o0 = nullptr;        // per-step off-diagonal of A0^t (ell)
+  double mv_d1 = 0, mv_o1 = 0, mv_d2 = 0, mv_o2 = 0;   // A1, A2 (diag, off)
   double *sigk = nullptr;         // per-step Neumann coefficient (tau_t - tau) kappa / h
   float *sigk32 = nullptr;
   double *host_small = nullptr;   // pinned host scratch for small results (1024 doubles)
@@ -171,8 +174,9 @@ cudaError_t fft_forward_f64(const Ctx &c, const double *x, const double *yprev, 
 cudaError_t fft_inverse_f64(const Ctx &c, const void *spec, double *y, cudaStream_t s);
 cudaError_t launch_tridiag(const Ctx &c, void *spec, int prec, int transpose,
                            cudaStream_t s);
+// y = A x (or A^T x); with `sub`, y = A x - sub (fused, for the shifted Arnoldi).
 cudaError_t launch_matvec(const Ctx &c, const double *x, double *y, int transpose,
-                          cudaStream_t s);
+                          cudaStream_t s, const double *sub = nullptr);
 cudaError_t launch_rhs(const Ctx &c, const double *u0, const double *v0, double *b,
                        cudaStream_t s);
 

@@ -64,66 +64,83 @@ int red_blocks(int64_t N) {
 }
 
 // ------------------------------------------------------------------ matvec
-// y_t = M d_t + beta_t (K x_t) with d_t = sum_j alpha_j x_{t -+ j}; the K
-// term is evaluated as differences of neighbours, (x_i - x_{i-1}) -
-// (x_{i+1} - x_i), which keeps the rounding relative to the (small)
-// second difference of a smooth field instead of to the field itself.
-template <int NB, bool TR>
-__global__ void __launch_bounds__(kThreads)
+// (A x)_t = A0^t x_t + A1 x_{t-1} (+ A2 x_{t-2}), every block a symmetric
+// tridiagonal tridiag(off, diag, off) (Section 2).  The transpose runs the
+// same recurrence backwards in t.  FP64 issues at 2 operations per clock per
+// SM here, so the kernel is written for the fewest FP64 operations: a thread
+// walks down a column i over TCH consecutive time steps, keeps the centre
+// value and the neighbour sum s = x_{i-1} + x_{i+1} of the previous one or
+// two steps in registers, and spends 1 add + 1 mul + 3 fma per output for the
+// heat equation (2 more fma for BD2); the two neighbour loads hit L1.
+constexpr int kMvCols = 128;   // columns per CTA
+constexpr int kMvRows = 32;    // time steps per thread
+
+template <int NB, bool TR, bool SUB>
+__global__ void __launch_bounds__(kMvCols)
 k_matvec(const double *__restrict__ x, double *__restrict__ y, int n, int ell,
-         double a0, double a1, double a2, double mh, const double *__restrict__ beta) {
-  const int64_t N = (int64_t)n * ell;
-  for (int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x; g < N;
-       g += (int64_t)gridDim.x * kThreads) {
-    const int t = (int)(g / n);
-    const int i = (int)(g - (int64_t)t * n);
-    const double *xt = x + (int64_t)t * n;
-    const double xc = xt[i];
-    const double xl = (i > 0) ? xt[i - 1] : 0.0;
-    const double xr = (i + 1 < n) ? xt[i + 1] : 0.0;
-    double dc = a0 * xc, dl = a0 * xl, dr = a0 * xr;
-    const int t1 = TR ? t + 1 : t - 1;
-    if (t1 >= 0 && t1 < ell) {
-      const double *xs = x + (int64_t)t1 * n;
-      dc = fma(a1, xs[i], dc);
-      if (i > 0) dl = fma(a1, xs[i - 1], dl);
-      if (i + 1 < n) dr = fma(a1, xs[i + 1], dr);
-    }
+         const double *__restrict__ d0, const double *__restrict__ o0,
+         double d1, double o1, double d2, double o2, const double *__restrict__ sub) {
+  const int i = blockIdx.x * kMvCols + threadIdx.x;
+  if (i >= n) return;
+  const int c0 = blockIdx.y * kMvRows;
+  const int c1 = min(ell, c0 + kMvRows);
+  auto row_vals = [&](int t, double &xc, double &sn) {
+    const double *xr = x + (int64_t)t * n;
+    xc = xr[i];
+    const double l = (i > 0) ? xr[i - 1] : 0.0;
+    const double r = (i + 1 < n) ? xr[i + 1] : 0.0;
+    sn = l + r;
+  };
+  // registers: previous (p1) and second previous (p2) step in walk order
+  double xp1 = 0.0, sp1 = 0.0, xp2 = 0.0, sp2 = 0.0;
+  const int first = TR ? c1 - 1 : c0;
+  const int step = TR ? -1 : 1;
+  const int tp1 = first - step, tp2 = first - 2 * step;
+  if (tp1 >= 0 && tp1 < ell) row_vals(tp1, xp1, sp1);
+  if (NB > 2 && tp2 >= 0 && tp2 < ell) row_vals(tp2, xp2, sp2);
+  for (int k = 0; k < c1 - c0; k++) {
+    const int t = first + k * step;
+    double xc, sn;
+    row_vals(t, xc, sn);
+    double acc = d1 * xp1;
+    acc = fma(o1, sp1, acc);
     if (NB > 2) {
-      const int t2 = TR ? t + 2 : t - 2;
-      if (t2 >= 0 && t2 < ell) {
-        const double *xs = x + (int64_t)t2 * n;
-        dc = fma(a2, xs[i], dc);
-        if (i > 0) dl = fma(a2, xs[i - 1], dl);
-        if (i + 1 < n) dr = fma(a2, xs[i + 1], dr);
-      }
+      acc = fma(d2, xp2, acc);
+      acc = fma(o2, sp2, acc);
+      xp2 = xp1;
+      sp2 = sp1;
     }
-    const double kx = (xc - xl) - (xr - xc);
-    const double md = fma(4.0, dc, dl + dr);
-    y[g] = fma(mh, md, __ldg(&beta[t]) * kx);
+    acc = fma(__ldg(&d0[t]), xc, acc);
+    acc = fma(__ldg(&o0[t]), sn, acc);
+    if (SUB) acc -= __ldg(&sub[(int64_t)t * n + i]);
+    y[(int64_t)t * n + i] = acc;
+    xp1 = xc;
+    sp1 = sn;
   }
 }
 
-cudaError_t launch_matvec(const Ctx &c, const double *x, double *y, int transpose,
-                          cudaStream_t s) {
-  const int64_t N = c.N;
-  int64_t blocks = (N + kThreads - 1) / kThreads;
-  if (blocks > 152 * 32) blocks = 152 * 32;
-  const double mh = c.h / 6.0;
-  double a0 = 1.0, a1 = -1.0, a2 = 0.0;
-  if (c.equation == AAO_HEAT_LITERAL) a0 = c.tau;
-  if (c.equation == AAO_WAVE_BD2) { a1 = -2.0; a2 = 1.0; }
-  const bool bd2 = c.equation == AAO_WAVE_BD2;
-  const unsigned g = (unsigned)blocks;
+template <int NB, bool TR>
+static void mv_sub(const Ctx &c, dim3 grid, const double *x, double *y, const double *sub,
+                   cudaStream_t s) {
   const int n = (int)c.n, ell = (int)c.ell;
-  if (bd2 && transpose)
-    k_matvec<3, true><<<g, kThreads, 0, s>>>(x, y, n, ell, a0, a1, a2, mh, c.beta);
-  else if (bd2)
-    k_matvec<3, false><<<g, kThreads, 0, s>>>(x, y, n, ell, a0, a1, a2, mh, c.beta);
-  else if (transpose)
-    k_matvec<2, true><<<g, kThreads, 0, s>>>(x, y, n, ell, a0, a1, a2, mh, c.beta);
+  if (sub)
+    k_matvec<NB, TR, true><<<grid, kMvCols, 0, s>>>(x, y, n, ell, c.mv_d0, c.mv_o0, c.mv_d1,
+                                                    c.mv_o1, c.mv_d2, c.mv_o2, sub);
   else
-    k_matvec<2, false><<<g, kThreads, 0, s>>>(x, y, n, ell, a0, a1, a2, mh, c.beta);
+    k_matvec<NB, TR, false><<<grid, kMvCols, 0, s>>>(x, y, n, ell, c.mv_d0, c.mv_o0, c.mv_d1,
+                                                     c.mv_o1, c.mv_d2, c.mv_o2, nullptr);
+}
+
+cudaError_t launch_matvec(const Ctx &c, const double *x, double *y, int transpose,
+                          cudaStream_t s, const double *sub) {
+  const int n = (int)c.n, ell = (int)c.ell;
+  const dim3 grid((unsigned)((n + kMvCols - 1) / kMvCols),
+                  (unsigned)((ell + kMvRows - 1) / kMvRows));
+  const bool bd2 = c.equation == AAO_WAVE_BD2;
+  if (bd2 && transpose) mv_sub<3, true>(c, grid, x, y, sub, s);
+  else if (bd2) mv_sub<3, false>(c, grid, x, y, sub, s);
+  else if (transpose) mv_sub<2, true>(c, grid, x, y, sub, s);
+  else mv_sub<2, false>(c, grid, x, y, sub, s);
   note_launch();
   return cudaGetLastError();
 }

@@ -233,6 +233,8 @@ int refresh_constants(Ctx &c) {
   }
   // matvec K coefficients beta_t and Neumann coefficients (tau_t - tau) kappa / h
   std::vector<double> beta((size_t)c.ell), sk((size_t)c.ell, 0.0);
+  std::vector<double> d0((size_t)c.ell), o0((size_t)c.ell);
+  const double mh = c.h / 6.0, kh = 1.0 / c.h;   // M = mh tridiag(1,4,1), K = kh tridiag(-1,2,-1)
   std::vector<float> sk32((size_t)c.ell, 0.0f);
   for (int64_t t = 0; t < c.ell; t++) {
     const double tt = c.variable_steps ? c.taus[(size_t)t] : c.tau;
@@ -241,21 +243,51 @@ int refresh_constants(Ctx &c) {
       case AAO_HEAT_LITERAL: beta[(size_t)t] = 1.0 / c.h; break;
       default: beta[(size_t)t] = tt * c.kappa / c.h; break;
     }
+    // A0^t as diag / off-diagonal
+    switch (c.equation) {
+      case AAO_WAVE_BD2: {
+        const double q = c.tau * c.tau;
+        d0[(size_t)t] = 4 * mh + 2 * q * kh;
+        o0[(size_t)t] = mh - q * kh;
+        break;
+      }
+      case AAO_HEAT_LITERAL:
+        d0[(size_t)t] = 2 * kh + c.tau * 4 * mh;
+        o0[(size_t)t] = -kh + c.tau * mh;
+        break;
+      default: {
+        const double q = tt * c.kappa;
+        d0[(size_t)t] = 4 * mh + 2 * q * kh;
+        o0[(size_t)t] = mh - q * kh;
+        break;
+      }
+    }
     if (c.variable_steps) {
       sk[(size_t)t] = (tt - c.tau) * c.kappa / c.h;
       sk32[(size_t)t] = (float)sk[(size_t)t];
     }
   }
   AAO_CK(c, upload((void **)&c.beta, beta));
+  AAO_CK(c, upload((void **)&c.mv_d0, d0));
+  AAO_CK(c, upload((void **)&c.mv_o0, o0));
+  // A1 = -M (heat) or -2M (BD2), A2 = M (BD2)
+  const double a1 = (c.equation == AAO_WAVE_BD2) ? -2.0 : -1.0;
+  c.mv_d1 = a1 * 4 * mh;
+  c.mv_o1 = a1 * mh;
+  c.mv_d2 = (c.equation == AAO_WAVE_BD2) ? 4 * mh : 0.0;
+  c.mv_o2 = (c.equation == AAO_WAVE_BD2) ? mh : 0.0;
   AAO_CK(c, upload((void **)&c.sigk, sk));
   AAO_CK(c, upload((void **)&c.sigk32, sk32));
   return AAO_OK;
 }
 
-bool overlap(const void *a, const void *b, size_t bytes) {
+// Do [a, a + na) and [b, b + nb) intersect?
+bool overlap2(const void *a, size_t na, const void *b, size_t nb) {
   const char *pa = static_cast<const char *>(a), *pb = static_cast<const char *>(b);
-  return pa < pb + bytes && pb < pa + bytes;
+  return pa < pb + nb && pb < pa + na;
 }
+
+bool overlap(const void *a, const void *b, size_t bytes) { return overlap2(a, bytes, b, bytes); }
 
 cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
 
@@ -314,7 +346,15 @@ cudaError_t neumann(Ctx &c, int terms, const double *x, double *y, int tr, cudaS
   return cudaSuccess;
 }
 
-// Flexible GMRES(m), right preconditioning, CGS with one re-orthogonalisation.
+// Flexible GMRES(m), right preconditioning, FP64 Arnoldi.
+//
+// Shifted Arnoldi: with a good circulant, A P^{-1} is close to the identity,
+// so w = A z_j is almost parallel to v_j and Gram-Schmidt on w cancels
+// catastrophically.  The basis is built instead from w~ = A z_j - v_j (the
+// subtraction is fused into the matvec), which spans the same Krylov space;
+// the Hessenberg matrix of A P^{-1} is that of w~ plus the identity.  One
+// classical Gram-Schmidt pass is followed by a second one only when the
+// norm drops below 1/sqrt(2) of its value (the DGKS criterion).
 int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, int maxit,
                int precond, aao_solve_info *info, cudaStream_t s) {
   if (m < 1 || m > kMaxRestart || !(rtol > 0.0) || maxit < 0 || precond < 0) return AAO_EINVAL;
@@ -326,7 +366,7 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
   double *red = reinterpret_cast<double *>(c.ws + L.red);
   double *small = red + kPartials;
   double *d_h1 = small, *d_h2 = small + 160, *d_nr = small + 320, *d_y = small + 480;
-  double *hs = c.host_small;   // pinned: [0,160) h1, [160,320) h2, [320,480) norms, [480,...) y
+  double *hs = c.host_small;   // pinned mirror of the same offsets
   std::vector<double *> V((size_t)m + 1), Z((size_t)m);
   for (int j = 0; j <= m; j++) V[(size_t)j] = vec_at(c, L, j);
   for (int j = 0; j < m; j++) Z[(size_t)j] = precond ? vec_at(c, L, m + 1 + j) : V[(size_t)j];
@@ -334,16 +374,19 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
     if (overlap(v, b, vb) || overlap(v, x, vb)) return AAO_EINVAL;
 
   if (info) { info->iters = 0; info->restarts = 0; info->history_len = 0; }
-  auto norm2 = [&](const double *v, double *dst_dev, double *dst_host) -> cudaError_t {
+  auto fetch = [&](double *dev, int count) -> cudaError_t {
+    return cudaMemcpyAsync(hs + (dev - small), dev, count * sizeof(double),
+                           cudaMemcpyDeviceToHost, s);
+  };
+  auto norm2 = [&](const double *v) -> cudaError_t {
     cudaError_t e = run(c, AAO_K_DOTS, s, [&] {
-      return aao::launch_multidot(nullptr, 0, v, N, true, red, dst_dev, s);
+      return aao::launch_multidot(nullptr, 0, v, N, true, red, d_nr, s);
     });
     if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(dst_host, dst_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return e;
+    if ((e = fetch(d_nr, 1)) != cudaSuccess) return e;
     return cudaStreamSynchronize(s);
   };
-  AAO_CK(c, norm2(b, d_nr, hs + 320));
+  AAO_CK(c, norm2(b));
   const double bnorm = std::sqrt(hs[320]);
   if (!std::isfinite(bnorm)) return AAO_ENUMERIC;
   if (bnorm == 0.0) {
@@ -354,17 +397,26 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
   }
   std::vector<double> H((size_t)(m + 1) * m), cs((size_t)m), sn((size_t)m), g((size_t)m + 1);
   auto Hij = [&](int i, int j) -> double & { return H[(size_t)i * m + j]; };
-  int iters = 0, restarts = 0, status = AAO_ENOCONV;
-  double relres_true = 1.0, est = 1.0;
+  int iters = 0, restarts = 0, status = AAO_ENOCONV, stalled = 0;
+  double relres_true = 1.0, est = 1.0, best = INFINITY;
   for (;;) {
     AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] { return aao::launch_matvec(c, x, V[0], tr, s); }));
     AAO_CK(c, run(c, AAO_K_OTHER, s, [&] { return aao::launch_sub_from(b, V[0], N, s); }));
-    AAO_CK(c, norm2(V[0], d_nr, hs + 320));
+    AAO_CK(c, norm2(V[0]));
     const double beta = std::sqrt(hs[320]);
     relres_true = beta / bnorm;
     if (!std::isfinite(beta)) { status = AAO_ENUMERIC; break; }
     if (relres_true <= rtol) { status = AAO_OK; break; }
     if (iters >= maxit) { status = AAO_ENOCONV; break; }
+    // Restart cycles that no longer lower the true residual by 10% mean the
+    // FP64 attainable accuracy (the rounding of x itself times |A|) is
+    // reached; after three such cycles in a row stop.
+    if (relres_true > 0.9 * best) {
+      if (++stalled >= 3) { status = AAO_ENOCONV; break; }
+    } else {
+      stalled = 0;
+    }
+    if (relres_true < best) best = relres_true;
     AAO_CK(c, run(c, AAO_K_OTHER, s, [&] { return aao::launch_scale(V[0], V[0], d_nr, N, true, s); }));
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
@@ -374,25 +426,42 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
       if (precond == 1) AAO_CK(c, precond_once(c, V[(size_t)j], nullptr, Z[(size_t)j], tr, s));
       else if (precond >= 2) AAO_CK(c, neumann(c, precond, V[(size_t)j], Z[(size_t)j], tr, s));
       double *w = V[(size_t)j + 1];
-      AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] { return aao::launch_matvec(c, Z[(size_t)j], w, tr, s); }));
+      // w~ = A z_j - v_j
+      AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] {
+        return aao::launch_matvec(c, Z[(size_t)j], w, tr, s, V[(size_t)j]);
+      }));
       const int nv = j + 1;
+      // pass 1: h = V^T w~ and ||w~||^2;  pass 2: w~ -= V h and its new norm
       AAO_CK(c, run(c, AAO_K_DOTS, s, [&] {
-        return aao::launch_multidot(V.data(), nv, w, N, false, red, d_h1, s);
+        return aao::launch_multidot(V.data(), nv, w, N, true, red, d_h1, s);
       }));
       AAO_CK(c, run(c, AAO_K_UPDATE, s, [&] {
-        return aao::launch_update_dots(V.data(), nv, d_h1, w, N, true, red, d_h2, s);
+        return aao::launch_update_dots(V.data(), nv, d_h1, w, N, false, red, d_nr, s);
       }));
-      AAO_CK(c, run(c, AAO_K_UPDATE, s, [&] {
-        return aao::launch_update_dots(V.data(), nv, d_h2, w, N, false, red, d_nr, s);
-      }));
-      AAO_CK(c, cudaMemcpyAsync(hs, d_h1, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
-      AAO_CK(c, cudaMemcpyAsync(hs + 160, d_h2, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
-      AAO_CK(c, cudaMemcpyAsync(hs + 320 + nv, d_nr + nv, sizeof(double), cudaMemcpyDeviceToHost, s));
+      AAO_CK(c, fetch(d_h1, nv + 1));
+      AAO_CK(c, fetch(d_nr + nv, 1));
       AAO_CK(c, cudaStreamSynchronize(s));
-      for (int i = 0; i < nv; i++) Hij(i, j) = hs[i] + hs[160 + i];
-      const double hn = std::sqrt(hs[320 + nv]);
+      const double before = hs[nv];          // ||w~||^2 before the projection
+      double after = hs[320 + nv];           // after
+      for (int i = 0; i < nv; i++) Hij(i, j) = hs[i];
+      if (after < 0.5 * before) {
+        // DGKS: lost more than half the norm, orthogonalise once more
+        AAO_CK(c, run(c, AAO_K_DOTS, s, [&] {
+          return aao::launch_multidot(V.data(), nv, w, N, false, red, d_h2, s);
+        }));
+        AAO_CK(c, run(c, AAO_K_UPDATE, s, [&] {
+          return aao::launch_update_dots(V.data(), nv, d_h2, w, N, false, red, d_nr, s);
+        }));
+        AAO_CK(c, fetch(d_h2, nv));
+        AAO_CK(c, fetch(d_nr + nv, 1));
+        AAO_CK(c, cudaStreamSynchronize(s));
+        for (int i = 0; i < nv; i++) Hij(i, j) += hs[160 + i];
+        after = hs[320 + nv];
+      }
+      Hij(j, j) += 1.0;                      // undo the shift: A P^{-1} = (A P^{-1} - I) + I
+      const double hn = std::sqrt(after);
       Hij(j + 1, j) = hn;
-      if (!std::isfinite(hn)) { numeric_fail = true; break; }
+      if (!std::isfinite(hn) || !std::isfinite(before)) { numeric_fail = true; break; }
       const bool breakdown = !(hn > 1e-300);
       if (!breakdown)
         AAO_CK(c, run(c, AAO_K_OTHER, s, [&] { return aao::launch_scale(w, w, d_nr + nv, N, true, s); }));
@@ -508,7 +577,7 @@ int aao_create(int64_t n, int64_t ell, double tau, int equation, aao_ctx **out) 
 void aao_destroy(aao_ctx *ctx) {
   if (!ctx) return;
   Ctx &c = ctx->c;
-  void *ptrs[] = {c.tab32, c.tab64, c.tw32, c.tw64, c.beta, c.sigk, c.sigk32};
+  void *ptrs[] = {c.tab32, c.tab64, c.tw32, c.tw64, c.beta, c.mv_d0, c.mv_o0, c.sigk, c.sigk32};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c.host_small) cudaFreeHost(c.host_small);
@@ -592,7 +661,7 @@ int aao_build_rhs(aao_ctx *ctx, const double *u0, const double *v0, double *b, v
   if (!ctx || !u0 || !b) return AAO_EINVAL;
   Ctx &c = ctx->c;
   const size_t nb = (size_t)c.n * sizeof(double), Nb = (size_t)c.N * sizeof(double);
-  if (overlap(u0, b, Nb > nb ? Nb : nb) || (v0 && overlap(v0, b, Nb))) return AAO_EINVAL;
+  if (overlap2(u0, nb, b, Nb) || (v0 && overlap2(v0, nb, b, Nb))) return AAO_EINVAL;
   cudaStream_t s = as_stream(stream);
   AAO_CK(c, run(c, AAO_K_OTHER, s, [&] { return aao::launch_rhs(c, u0, v0, b, s); }));
   return AAO_OK;

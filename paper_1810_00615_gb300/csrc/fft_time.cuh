@@ -175,6 +175,12 @@ __device__ __forceinline__ void pass(cx<R> *sm, int Ns, const cx<R> *__restrict_
   __syncthreads();
 }
 
+template <int L> struct Passes {
+  static constexpr int LOG2 = Plan<L>::LOG2;
+  static constexpr int NP = (L <= 1) ? 0 : (L <= 16 ? 1 : (LOG2 + 3) / 4);   // passes
+  static constexpr int R1 = (L <= 16) ? L : (1 << (LOG2 - 4 * (NP - 1)));   // first radix
+};
+
 // Full length-L transform of the C columns in shared memory.
 template <typename R, int L, int C, int DIR, int T>
 __device__ __forceinline__ void transform(cx<R> *sm, const cx<R> *__restrict__ tw) {
@@ -196,9 +202,18 @@ __device__ __forceinline__ void transform(cx<R> *sm, const cx<R> *__restrict__ t
   }
 }
 
-template <typename R> struct Cap;   // complex points of shared memory per CTA
-template <> struct Cap<float> { static constexpr int V = 16384; };
-template <> struct Cap<double> { static constexpr int V = 8192; };
+// Complex points of shared memory per CTA.  8192 points (64 KB in FP32)
+// leave room for three CTAs per SM so that one CTA's loads overlap another's
+// passes.
+#ifndef AAO_FFT_CAP32
+#define AAO_FFT_CAP32 8192
+#endif
+#ifndef AAO_FFT_CAP64
+#define AAO_FFT_CAP64 8192
+#endif
+template <typename R> struct Cap;
+template <> struct Cap<float> { static constexpr int V = AAO_FFT_CAP32; };
+template <> struct Cap<double> { static constexpr int V = AAO_FFT_CAP64; };
 
 template <typename R, int L> struct Shape {
   static constexpr int C0 = Cap<R>::V / L;
@@ -211,41 +226,70 @@ template <typename R, int L> struct Shape {
 // Forward: x (FP64, ell x n) -> half spectrum (R complex, nk x n_pad).
 // NEUMANN: the input is x - E y with (E y)_t = sigk_t (2 y_i - y_{i-1} - y_{i+1}),
 // sigk_t = (tau_t - tau) kappa / h (Section 2, E = sigma (x) kappa K).
+// The first Stockham pass (radix R1, no twiddles) reads its 2*R1 real inputs
+// per butterfly straight from global memory into registers, so a thread has
+// all of its loads in flight at once; later passes go through shared memory.
+template <typename R, int L, bool NEUMANN>
+__device__ __forceinline__ R load_real(const double *__restrict__ x, const double *__restrict__ y,
+                                       const R *__restrict__ sigk, int n, int t, int i) {
+  if (i >= n) return (R)0;
+  const size_t o = (size_t)t * n + i;
+  if constexpr (NEUMANN) {
+    const R yc = from_f64<R>(__ldg(&y[o]));
+    const R yl = (i > 0) ? from_f64<R>(__ldg(&y[o - 1])) : (R)0;
+    const R yr = (i + 1 < n) ? from_f64<R>(__ldg(&y[o + 1])) : (R)0;
+    return from_f64<R>(__ldg(&x[o])) - __ldg(&sigk[t]) * ((yc + yc) - yl - yr);
+  } else {
+    return from_f64<R>(__ldg(&x[o]));
+  }
+}
+
 template <typename R, int L, bool NEUMANN>
 __global__ void __launch_bounds__(Shape<R, L>::T)
 k_fft_forward(const double *__restrict__ x, const double *__restrict__ y,
               const R *__restrict__ sigk, cx<R> *__restrict__ spec, int n, int64_t n_pad,
               const cx<R> *__restrict__ tw) {
   using S = Shape<R, L>;
-  constexpr int C = S::C, T = S::T, W = 2 * C;
+  using PL = Passes<L>;
+  constexpr int C = S::C, T = S::T, E = S::E;
+  constexpr int R1 = PL::R1 < 1 ? 1 : PL::R1;
+  constexpr int NB = E / R1;
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
-  R *smr = reinterpret_cast<R *>(smraw);
-  const int i0 = blockIdx.x * W;
+  const int i0 = blockIdx.x * (2 * C);
 
-  // load the panel: time row t, column w -> real (w even) / imaginary part
-  // of complex column w/2
-#pragma unroll 8
-  for (int idx = threadIdx.x; idx < L * W; idx += T) {
-    const int t = idx / W, w = idx - t * W, i = i0 + w;
-    R v = (R)0;
-    if (i < n) {
-      const size_t o = (size_t)t * n + i;
-      if constexpr (NEUMANN) {
-        const R yc = from_f64<R>(__ldg(&y[o]));
-        const R yl = (i > 0) ? from_f64<R>(__ldg(&y[o - 1])) : (R)0;
-        const R yr = (i + 1 < n) ? from_f64<R>(__ldg(&y[o + 1])) : (R)0;
-        const R ky = (yc + yc) - yl - yr;
-        v = from_f64<R>(__ldg(&x[o])) - __ldg(&sigk[t]) * ky;
-      } else {
-        v = from_f64<R>(__ldg(&x[o]));
+  {
+    cx<R> v[NB][R1];
+#pragma unroll
+    for (int q = 0; q < NB; q++) {
+      const int b = threadIdx.x + q * T;
+      const int c = b % C, j = b / C;
+      const int i = i0 + 2 * c;
+#pragma unroll
+      for (int r = 0; r < R1; r++) {
+        const int t = j + r * (L / R1);
+        v[q][r] = mk(load_real<R, L, NEUMANN>(x, y, sigk, n, t, i),
+                     load_real<R, L, NEUMANN>(x, y, sigk, n, t, i + 1));
       }
     }
-    smr[2 * phys<C>(t, w >> 1) + (w & 1)] = v;
+#pragma unroll
+    for (int q = 0; q < NB; q++) {
+      const int b = threadIdx.x + q * T;
+      const int c = b % C, j = b / C;
+      dft<R, -1, R1>(v[q]);
+#pragma unroll
+      for (int r = 0; r < R1; r++) sm[phys<C>(j * R1 + r, c)] = v[q][r];
+    }
   }
   __syncthreads();
-
-  transform<R, L, C, -1, T>(sm, tw);
+  if constexpr (PL::NP > 1) {
+    int Ns = R1;
+#pragma unroll
+    for (int p = 1; p < PL::NP; p++) {
+      pass<R, L, C, 16, -1, T>(sm, Ns, tw);
+      Ns *= 16;
+    }
+  }
 
   // unpack the two real columns of each complex column and write k = 0..L/2
   constexpr int NK = L / 2 + 1;
@@ -267,16 +311,19 @@ k_fft_forward(const double *__restrict__ x, const double *__restrict__ y,
   }
 }
 
-// Inverse: half spectrum -> y (FP64), scaled by 1/L.
+// Inverse: half spectrum -> y (FP64), scaled by 1/L.  The last Stockham pass
+// (where j < Ns, so output index j + r Ns is time step t) writes straight to
+// global memory.
 template <typename R, int L>
 __global__ void __launch_bounds__(Shape<R, L>::T)
 k_fft_inverse(const cx<R> *__restrict__ spec, double *__restrict__ y, int n, int64_t n_pad,
               const cx<R> *__restrict__ tw) {
   using S = Shape<R, L>;
-  constexpr int C = S::C, T = S::T, W = 2 * C;
+  using PL = Passes<L>;
+  constexpr int C = S::C, T = S::T, E = S::E;
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
-  const int i0 = blockIdx.x * W;
+  const int i0 = blockIdx.x * (2 * C);
   constexpr int NK = L / 2 + 1;
   for (int idx = threadIdx.x; idx < NK * C; idx += T) {
     const int k = idx / C, c = idx - k * C;
@@ -292,14 +339,39 @@ k_fft_inverse(const cx<R> *__restrict__ spec, double *__restrict__ y, int n, int
   }
   __syncthreads();
 
-  transform<R, L, C, +1, T>(sm, tw);
-
+  constexpr int RL = (PL::NP <= 1) ? (L < 1 ? 1 : L) : 16;   // radix of the last pass
+  int Ns = 1;
+  if constexpr (PL::NP > 1) {
+    pass<R, L, C, PL::R1, +1, T>(sm, 1, tw);
+    Ns = PL::R1;
+#pragma unroll
+    for (int p = 1; p < PL::NP - 1; p++) {
+      pass<R, L, C, 16, +1, T>(sm, Ns, tw);
+      Ns *= 16;
+    }
+  }
+  constexpr int NB = E / RL;
   const R scale = (R)1 / (R)L;
-  const R *smr = reinterpret_cast<const R *>(smraw);
-#pragma unroll 8
-  for (int idx = threadIdx.x; idx < L * W; idx += T) {
-    const int t = idx / W, w = idx - t * W, i = i0 + w;
-    if (i < n) y[(size_t)t * n + i] = to_double<R>(scale * smr[2 * phys<C>(t, w >> 1) + (w & 1)]);
+#pragma unroll
+  for (int q = 0; q < NB; q++) {
+    const int b = threadIdx.x + q * T;
+    const int c = b % C, j = b / C;   // j < L / RL = Ns
+    cx<R> v[RL];
+#pragma unroll
+    for (int r = 0; r < RL; r++) v[r] = sm[phys<C>(j + r * (L / RL), c)];
+    if (Ns > 1) {
+      const int step = j * (L / (Ns * RL));
+#pragma unroll
+      for (int r = 1; r < RL; r++) v[r] = twiddle<R, +1>(v[r], tw[step * r]);
+    }
+    dft<R, +1, RL>(v);
+    const int i = i0 + 2 * c;
+#pragma unroll
+    for (int r = 0; r < RL; r++) {
+      const size_t o = (size_t)(j + r * Ns) * n + i;
+      if (i < n) y[o] = to_double<R>(scale * v[r].re);
+      if (i + 1 < n) y[o + 1] = to_double<R>(scale * v[r].im);
+    }
   }
 }
 

@@ -34,7 +34,13 @@ __device__ __forceinline__ cx<R> ld_tab(const cx<R> &v, int conj) {
   return z;
 }
 
-template <typename R, int CH>
+// Row staging: the row is moved between global and shared memory in 16-byte
+// chunks by consecutive threads (coalesced), and stored with the 16-byte
+// chunk index XOR-ed with (line & 7) inside each 128-byte line, so that the
+// per-thread reads of one whole line (thread p owns line p) hit all 32 banks.
+__device__ __forceinline__ int swz(int chunk) { return chunk ^ ((chunk >> 3) & 7); }
+
+template <typename R, int CH, bool STAGE>
 __global__ void __launch_bounds__(1024)
 k_tridiag(cx<R> *__restrict__ spec, int n, int64_t n_pad, const TriTab<R, CH> *__restrict__ tabs,
           int conj_sym) {
@@ -47,6 +53,10 @@ k_tridiag(cx<R> *__restrict__ spec, int n, int64_t n_pad, const TriTab<R, CH> *_
   cx<R> *buf = reinterpret_cast<cx<R> *>(smraw);   // [2][4][M] PCR rows
   cx<R> *s_first = buf + 8 * M;                     // [P] first local value of each chunk
   cx<R> *s_sep = s_first + P;                       // [M] separator solution
+  // [P * CH] staged row, 16-byte aligned (offset rounded up to 2 complex)
+  float4 *s_row = reinterpret_cast<float4 *>(smraw + (((size_t)(10 * M + P) * sizeof(cx<R>) + 15) & ~(size_t)15));
+  constexpr int EPC = 16 / sizeof(cx<R>);           // complex values per 16-byte chunk
+  const int nchunks = (P * CH) / EPC;
 
   const TriTab<R, CH> *tb = tabs + k;
   for (int i = p; i < CH; i += P) {
@@ -67,8 +77,21 @@ k_tridiag(cx<R> *__restrict__ spec, int n, int64_t n_pad, const TriTab<R, CH> *_
   const int base = p * CH;
   const int len = (p == M) ? (n - base) : (CH - 1);   // unknowns of this chunk
   cx<R> v[CH];
+  if constexpr (STAGE) {
+    const float4 *g = reinterpret_cast<const float4 *>(row);
+    for (int q = p; q < nchunks; q += P) s_row[swz(q)] = g[q];
+    __syncthreads();
 #pragma unroll
-  for (int i = 0; i < CH; i++) v[i] = (base + i < n) ? row[base + i] : mk((R)0, (R)0);
+    for (int j = 0; j < CH / EPC; j++) {
+      const float4 f = s_row[swz(p * (CH / EPC) + j)];
+      const cx<R> *z = reinterpret_cast<const cx<R> *>(&f);
+#pragma unroll
+      for (int u = 0; u < EPC; u++) v[j * EPC + u] = (base + j * EPC + u < n) ? z[u] : mk((R)0, (R)0);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < CH; i++) v[i] = (base + i < n) ? row[base + i] : mk((R)0, (R)0);
+  }
   __syncthreads();
 
   const cx<R> e = s_sc[0];
@@ -134,22 +157,50 @@ k_tridiag(cx<R> *__restrict__ spec, int n, int64_t n_pad, const TriTab<R, CH> *_
         if (i < len) v[i] = cfma(v[i], sl, s_fl[i]);
     }
   }
+  if constexpr (STAGE) {
 #pragma unroll
-  for (int i = 0; i < CH; i++)
-    if (base + i < n) row[base + i] = v[i];
+    for (int j = 0; j < CH / EPC; j++) {
+      float4 f;
+      cx<R> *z = reinterpret_cast<cx<R> *>(&f);
+#pragma unroll
+      for (int u = 0; u < EPC; u++) z[u] = v[j * EPC + u];
+      s_row[swz(p * (CH / EPC) + j)] = f;
+    }
+    __syncthreads();
+    // chunks past n hold zeros or padding; only whole chunks below n_pad exist
+    float4 *g = reinterpret_cast<float4 *>(row);
+    const int nlive = (n + EPC - 1) / EPC;
+    for (int q = p; q < nlive; q += P) {
+      if ((q + 1) * EPC <= n) {
+        g[q] = s_row[swz(q)];
+      } else {
+        const float4 f = s_row[swz(q)];
+        const cx<R> *z = reinterpret_cast<const cx<R> *>(&f);
+        for (int u = 0; q * EPC + u < n; u++) row[q * EPC + u] = z[u];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < CH; i++)
+      if (base + i < n) row[base + i] = v[i];
+  }
 }
 
 template <typename R, int CH>
 static cudaError_t run_tridiag(const Ctx &c, void *spec, const void *tab, int P, int conj,
                                cudaStream_t s) {
   const int M = P - 1;
-  const size_t smem = (size_t)(8 * M + P + M) * sizeof(cx<R>);
-  cudaError_t e = cudaFuncSetAttribute(k_tridiag<R, CH>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t base_smem = (size_t)(10 * M + P) * sizeof(cx<R>);
+  const size_t stage_smem = ((base_smem + 15) & ~(size_t)15) + (size_t)P * CH * sizeof(cx<R>);
+  const bool stage = stage_smem <= 200 * 1024;
+  const size_t smem = stage ? stage_smem : base_smem;
+  auto kern = stage ? k_tridiag<R, CH, true> : k_tridiag<R, CH, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
-  k_tridiag<R, CH><<<(unsigned)c.nk, P, smem, s>>>(
-      static_cast<cx<R> *>(spec), (int)c.n, c.n_pad,
-      static_cast<const TriTab<R, CH> *>(tab), conj); note_launch();
+  kern<<<(unsigned)c.nk, P, smem, s>>>(static_cast<cx<R> *>(spec), (int)c.n, c.n_pad,
+                                       static_cast<const TriTab<R, CH> *>(tab), conj);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -1,0 +1,76 @@
+"""Run one kernel family of the solver repeatedly on synthetic inputs, for
+profilers (ncu) and quick timing.
+
+    python -m paper_1810_00615_gb300.profile_case --op precond --n 4095 --ell 4096 \\
+        --prec fp32 --reps 3
+
+--op precond | neumann | matvec | solve.  Prints one line with the mean CUDA-
+event time per call.  Inputs are seeded standard-normal block vectors (or the
+8-mode heat initial data for `solve`).
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", default="precond", choices=["precond", "neumann", "matvec", "solve"])
+    ap.add_argument("--n", type=int, default=4095)
+    ap.add_argument("--ell", type=int, default=4096)
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--equation", default="heat")
+    ap.add_argument("--terms", type=int, default=2)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=1)
+    a = ap.parse_args(argv)
+
+    import numpy as np
+    import synthetic as syn
+    from paper_1810_00615_gb300 import AllAtOnce
+
+    s = AllAtOnce(a.n, a.ell, 1.0 / a.ell, equation=a.equation, precision=a.prec,
+                  restart=30 if a.op == "solve" else 1)
+    if a.op == "neumann":
+        s.set_steps(syn.time_steps(a.ell, 0.5, syn.rng(3)))
+    g = torch.Generator(device="cuda").manual_seed(1)
+    x = torch.randn(a.ell, a.n, dtype=torch.float64, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    if a.op == "solve":
+        b = s.build_rhs(torch.from_numpy(syn.heat_initial(a.n)).cuda())
+
+    def once():
+        if a.op == "precond":
+            s.precond_apply(x, out=y)
+        elif a.op == "neumann":
+            s.neumann_apply(x, a.terms, out=y)
+        elif a.op == "matvec":
+            s.matvec(x, out=y)
+        else:
+            s.solve(b, restart=30, rtol=1e-10)
+
+    for _ in range(a.warmup):
+        once()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.reps
+    print(f"op={a.op} n={a.n} ell={a.ell} prec={a.prec} ms_per_call={ms:.4f} "
+          f"launches={s.kernel_launches()}")
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -205,6 +205,22 @@ def test_circulant_matvec_matches_dense(kind):
                                C.T @ X.ravel(), atol=1e-13)
 
 
+@pytest.mark.parametrize("kind,n,ell", [("heat", 9, 8), ("bd2", 9, 8), ("heat", 31, 64),
+                                        ("bd2", 5, 2), ("heat", 1, 1)])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_spectral_inverse_matches_dft_route(kind, n, ell, transpose):
+    """The DST (x) FFT route agrees with the dense-DFT + banded-LU route and
+    with the dense LU of the circulant."""
+    S = system.heat(n, ell, 1.0 / ell, 0.7) if kind == "heat" else system.bd2(n, ell, 1.0 / ell)
+    X = syn.block_vector(n, ell, syn.rng(6))
+    a = precond.circulant_inverse_spectral(S, X, transpose)
+    b = precond.circulant_inverse(S, X, transpose)
+    np.testing.assert_allclose(a, b, atol=1e-11 * np.abs(b).max())
+    C = system.dense_circulant(S)
+    c = np.linalg.solve(C.T if transpose else C, X.ravel()).reshape(ell, n)
+    np.testing.assert_allclose(a, c, atol=1e-11 * np.abs(c).max())
+
+
 def test_dense_circulant_corner_blocks():
     """P has A1 in the top-right block; R_BD2 has A2, A1 in the top-right and
     A2 in the second row's last block (Section 2 displays)."""
