@@ -187,17 +187,18 @@ cudaError_t launch_rhs(const Ctx &c, const double *u0, const double *v0, double 
 int  red_blocks(int64_t N);
 cudaError_t launch_multidot(const double *const *V, int nv, const double *w, int64_t N,
                             bool with_norm, double *partials, double *out, cudaStream_t s);
-// w -= sum_j h[j] V_j (h on device); optionally fused: dots of the updated w
-// with V_j (out2[j]) and its squared norm (out2[nv]).
+// w -= sum_j hf[j] h[j] V_j (h on device, hf host factors, NULL = 1);
+// optionally fused: dots of the updated w with V_j (out2[j]); always its
+// squared norm (out2[nv]).
 cudaError_t launch_update_dots(const double *const *V, int nv, const double *h,
                                double *w, int64_t N, bool want_dots, double *partials,
-                               double *out2, cudaStream_t s);
+                               double *out2, cudaStream_t s, const double *hf = nullptr);
 // x += sum_j y[j] Z_j (y on device)
 cudaError_t launch_combine(const double *const *Z, int nv, const double *y, double *x,
                            int64_t N, cudaStream_t s);
 // y = a*x (a on device, *a_scale of index)
 cudaError_t launch_scale(const double *x, double *y, const double *a, int64_t N,
-                         bool invert, cudaStream_t s);
+                         bool invert, cudaStream_t s, bool negate = false);
 // r = b - r (in place on r)
 cudaError_t launch_sub_from(const double *b, double *r, int64_t N, cudaStream_t s);
 cudaError_t launch_adjoint_grads(const Ctx &c, const double *lam, const double *U,

@@ -54,6 +54,9 @@ __global__ void k_finish(const double *__restrict__ partials, int nb, int nv,
 struct Ptrs8 {
   const double *p[8];
 };
+struct Coef8 {
+  double c[8];
+};
 }  // namespace
 
 int red_blocks(int64_t N) {
@@ -248,12 +251,12 @@ cudaError_t launch_multidot(const double *const *V, int nv, const double *w, int
 // acc_nv += w_new . w_new.
 template <int NV, bool DOTS>
 __global__ void __launch_bounds__(kThreads)
-k_update(Ptrs8 V, const double *__restrict__ h, double *__restrict__ w, int64_t N,
+k_update(Ptrs8 V, const double *__restrict__ h, Coef8 f, double *__restrict__ w, int64_t N,
          double *__restrict__ partials) {
   constexpr int NO = (DOTS ? NV : 0) + 1;
   double hv[NV];
 #pragma unroll
-  for (int j = 0; j < NV; j++) hv[j] = h[j];
+  for (int j = 0; j < NV; j++) hv[j] = h[j] * f.c[j];
   double acc[NO];
 #pragma unroll
   for (int j = 0; j < NO; j++) acc[j] = 0.0;
@@ -278,18 +281,24 @@ k_update(Ptrs8 V, const double *__restrict__ h, double *__restrict__ w, int64_t 
 
 cudaError_t launch_update_dots(const double *const *V, int nv, const double *h, double *w,
                                int64_t N, bool want_dots, double *partials, double *out2,
-                               cudaStream_t s) {
+                               cudaStream_t s, const double *hf) {
   // Groups of 8 vectors: every group but the last only updates; the dots of
   // the final w with all vectors are then taken by a multi-dot pass when
   // nv > 8 (the fused path covers nv <= 8, the common case).
   const int nb = red_blocks(N);
+  auto coef = [&](int first, int g) {
+    Coef8 f{};
+    for (int j = 0; j < g; j++) f.c[j] = hf ? hf[first + j] : 1.0;
+    return f;
+  };
   if (nv <= 8) {
     Ptrs8 P{};
     for (int j = 0; j < nv; j++) P.p[j] = V[j];
+    const Coef8 F = coef(0, nv);
 #define AAO_UP(G)                                                                          \
   case G:                                                                                  \
-    if (want_dots) k_update<G, true><<<nb, kThreads, 0, s>>>(P, h, w, N, partials);        \
-    else k_update<G, false><<<nb, kThreads, 0, s>>>(P, h, w, N, partials);                 \
+    if (want_dots) k_update<G, true><<<nb, kThreads, 0, s>>>(P, h, F, w, N, partials);     \
+    else k_update<G, false><<<nb, kThreads, 0, s>>>(P, h, F, w, N, partials);              \
     note_launch();                                                                         \
     break;
     switch (nv) {
@@ -309,8 +318,9 @@ cudaError_t launch_update_dots(const double *const *V, int nv, const double *h, 
     const int g = (nv - done) > 8 ? 8 : (nv - done);
     Ptrs8 P{};
     for (int j = 0; j < g; j++) P.p[j] = V[done + j];
+    const Coef8 F = coef(done, g);
     switch (g) {
-#define AAO_UP2(G) case G: k_update<G, false><<<nb, kThreads, 0, s>>>(P, h + done, w, N, partials); note_launch(); break;
+#define AAO_UP2(G) case G: k_update<G, false><<<nb, kThreads, 0, s>>>(P, h + done, F, w, N, partials); note_launch(); break;
       AAO_UP2(1) AAO_UP2(2) AAO_UP2(3) AAO_UP2(4) AAO_UP2(5) AAO_UP2(6) AAO_UP2(7) AAO_UP2(8)
 #undef AAO_UP2
     }
@@ -357,21 +367,24 @@ cudaError_t launch_combine(const double *const *Z, int nv, const double *y, doub
 }
 
 // ------------------------------------------------------------ misc
-// y = a * x with a = *ap (or 1/sqrt(*ap) when invert: a norm^2 on device)
+// y = a * x with a = *ap (or 1/sqrt(*ap) when invert: a norm^2 on device),
+// negated when negate != 0
 __global__ void k_scale(const double *__restrict__ x, double *__restrict__ y,
-                        const double *__restrict__ ap, int64_t N, int invert) {
+                        const double *__restrict__ ap, int64_t N, int invert, int negate) {
   double a = *ap;
   if (invert) a = 1.0 / sqrt(a);
+  if (negate) a = -a;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N;
        g += (int64_t)gridDim.x * blockDim.x)
     y[g] = a * x[g];
 }
 
 cudaError_t launch_scale(const double *x, double *y, const double *a, int64_t N, bool invert,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool negate) {
   int64_t blocks = (N + kThreads - 1) / kThreads;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_scale<<<(unsigned)blocks, kThreads, 0, s>>>(x, y, a, N, invert ? 1 : 0); note_launch();
+  k_scale<<<(unsigned)blocks, kThreads, 0, s>>>(x, y, a, N, invert ? 1 : 0, negate ? 1 : 0);
+  note_launch();
   return cudaGetLastError();
 }
 

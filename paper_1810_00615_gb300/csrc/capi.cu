@@ -355,6 +355,10 @@ cudaError_t neumann(Ctx &c, int terms, const double *x, double *y, int tr, cudaS
 // the Hessenberg matrix of A P^{-1} is that of w~ plus the identity.  One
 // classical Gram-Schmidt pass is followed by a second one only when the
 // norm drops below 1/sqrt(2) of its value (the DGKS criterion).
+//
+// Lazy normalisation: basis vectors are stored unscaled, v_j = sc[j] * V_j,
+// and the scales are folded into the coefficients the kernels receive (the
+// preconditioner and A are linear), which saves a full pass per step.
 int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, int maxit,
                int precond, aao_solve_info *info, cudaStream_t s) {
   if (m < 1 || m > kMaxRestart || !(rtol > 0.0) || maxit < 0 || precond < 0) return AAO_EINVAL;
@@ -396,12 +400,13 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
     return AAO_OK;
   }
   std::vector<double> H((size_t)(m + 1) * m), cs((size_t)m), sn((size_t)m), g((size_t)m + 1);
+  std::vector<double> sc((size_t)m + 1), sc2((size_t)m + 1);
   auto Hij = [&](int i, int j) -> double & { return H[(size_t)i * m + j]; };
   int iters = 0, restarts = 0, status = AAO_ENOCONV, stalled = 0;
   double relres_true = 1.0, est = 1.0, best = INFINITY;
   for (;;) {
-    AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] { return aao::launch_matvec(c, x, V[0], tr, s); }));
-    AAO_CK(c, run(c, AAO_K_OTHER, s, [&] { return aao::launch_sub_from(b, V[0], N, s); }));
+    // V_0 = A x - b = -r (one fused pass); v_0 = -V_0 / beta
+    AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] { return aao::launch_matvec(c, x, V[0], tr, s, b); }));
     AAO_CK(c, norm2(V[0]));
     const double beta = std::sqrt(hs[320]);
     relres_true = beta / bnorm;
@@ -417,7 +422,7 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
       stalled = 0;
     }
     if (relres_true < best) best = relres_true;
-    AAO_CK(c, run(c, AAO_K_OTHER, s, [&] { return aao::launch_scale(V[0], V[0], d_nr, N, true, s); }));
+    sc[0] = -1.0 / beta;
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int jd = 0;
@@ -426,45 +431,46 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
       if (precond == 1) AAO_CK(c, precond_once(c, V[(size_t)j], nullptr, Z[(size_t)j], tr, s));
       else if (precond >= 2) AAO_CK(c, neumann(c, precond, V[(size_t)j], Z[(size_t)j], tr, s));
       double *w = V[(size_t)j + 1];
-      // w~ = A z_j - v_j
+      // w~ = A z_j - V_j (unscaled; the true vector is sc[j] times it)
       AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] {
         return aao::launch_matvec(c, Z[(size_t)j], w, tr, s, V[(size_t)j]);
       }));
       const int nv = j + 1;
-      // pass 1: h = V^T w~ and ||w~||^2;  pass 2: w~ -= V h and its new norm
+      for (int i = 0; i < nv; i++) sc2[(size_t)i] = sc[(size_t)i] * sc[(size_t)i];
+      // pass 1: d = V^T w~ and ||w~||^2;  pass 2: w~ -= sum sc_i^2 d_i V_i and its norm
       AAO_CK(c, run(c, AAO_K_DOTS, s, [&] {
         return aao::launch_multidot(V.data(), nv, w, N, true, red, d_h1, s);
       }));
       AAO_CK(c, run(c, AAO_K_UPDATE, s, [&] {
-        return aao::launch_update_dots(V.data(), nv, d_h1, w, N, false, red, d_nr, s);
+        return aao::launch_update_dots(V.data(), nv, d_h1, w, N, false, red, d_nr, s, sc2.data());
       }));
       AAO_CK(c, fetch(d_h1, nv + 1));
       AAO_CK(c, fetch(d_nr + nv, 1));
       AAO_CK(c, cudaStreamSynchronize(s));
-      const double before = hs[nv];          // ||w~||^2 before the projection
+      const double before = hs[nv];          // ||w~||^2 before the projection (unscaled)
       double after = hs[320 + nv];           // after
-      for (int i = 0; i < nv; i++) Hij(i, j) = hs[i];
+      for (int i = 0; i < nv; i++) Hij(i, j) = sc[(size_t)i] * sc[(size_t)j] * hs[i];
       if (after < 0.5 * before) {
         // DGKS: lost more than half the norm, orthogonalise once more
         AAO_CK(c, run(c, AAO_K_DOTS, s, [&] {
           return aao::launch_multidot(V.data(), nv, w, N, false, red, d_h2, s);
         }));
         AAO_CK(c, run(c, AAO_K_UPDATE, s, [&] {
-          return aao::launch_update_dots(V.data(), nv, d_h2, w, N, false, red, d_nr, s);
+          return aao::launch_update_dots(V.data(), nv, d_h2, w, N, false, red, d_nr, s, sc2.data());
         }));
         AAO_CK(c, fetch(d_h2, nv));
         AAO_CK(c, fetch(d_nr + nv, 1));
         AAO_CK(c, cudaStreamSynchronize(s));
-        for (int i = 0; i < nv; i++) Hij(i, j) += hs[160 + i];
+        for (int i = 0; i < nv; i++) Hij(i, j) += sc[(size_t)i] * sc[(size_t)j] * hs[160 + i];
         after = hs[320 + nv];
       }
       Hij(j, j) += 1.0;                      // undo the shift: A P^{-1} = (A P^{-1} - I) + I
-      const double hn = std::sqrt(after);
+      const double hn = std::fabs(sc[(size_t)j]) * std::sqrt(after);
       Hij(j + 1, j) = hn;
       if (!std::isfinite(hn) || !std::isfinite(before)) { numeric_fail = true; break; }
       const bool breakdown = !(hn > 1e-300);
-      if (!breakdown)
-        AAO_CK(c, run(c, AAO_K_OTHER, s, [&] { return aao::launch_scale(w, w, d_nr + nv, N, true, s); }));
+      // v_{j+1} = w~ / hn = (sc_j / hn) W~
+      sc[(size_t)j + 1] = breakdown ? 0.0 : sc[(size_t)j] / hn;
       for (int i = 0; i < j; i++) {
         const double t = cs[(size_t)i] * Hij(i, j) + sn[(size_t)i] * Hij(i + 1, j);
         Hij(i + 1, j) = -sn[(size_t)i] * Hij(i, j) + cs[(size_t)i] * Hij(i + 1, j);
@@ -493,7 +499,7 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
       for (int l = i + 1; l < jd; l++) acc -= Hij(i, l) * y[(size_t)l];
       y[(size_t)i] = acc / Hij(i, i);
     }
-    for (int i = 0; i < jd; i++) hs[480 + i] = y[(size_t)i];
+    for (int i = 0; i < jd; i++) hs[480 + i] = y[(size_t)i] * sc[(size_t)i];   // z_i = sc_i Z_i
     AAO_CK(c, cudaMemcpyAsync(d_y, hs + 480, jd * sizeof(double), cudaMemcpyHostToDevice, s));
     AAO_CK(c, run(c, AAO_K_COMBINE, s, [&] { return aao::launch_combine(Z.data(), jd, d_y, x, N, s); }));
     restarts++;

@@ -5,9 +5,39 @@
 namespace aao {
 namespace fft {
 
+// Persistent grid: as many CTAs as fit on the device at once, capped by the
+// panel count.
+template <class K>
+static int persistent_grid(K kern, int threads, size_t smem, int npanels) {
+  int dev = 0, sms = 1, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess ||
+      per < 1)
+    per = 1;
+  const int g = sms * per;
+  return g < npanels ? g : npanels;
+}
+
+#ifndef AAO_FFT_PIPE
+#define AAO_FFT_PIPE 0
+#endif
+
 template <typename R, int L>
 static cudaError_t run_forward(int64_t n, int64_t n_pad, const double *x, const double *y,
                                const R *sigk, cx<R> *spec, const cx<R> *tw, cudaStream_t s) {
+  if (!y && AAO_FFT_PIPE) {
+    using P = PShape<R, L>;
+    const int np = (int)((n + 2 * P::C - 1) / (2 * P::C));
+    auto kern = k_fft_forward_pipe<R, L>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)P::SMEM_F);
+    if (e != cudaSuccess) return e;
+    const int g = persistent_grid(kern, P::T, P::SMEM_F, np);
+    kern<<<g, P::T, P::SMEM_F, s>>>(x, spec, (int)n, n_pad, tw, np);
+    note_launch();
+    return cudaGetLastError();
+  }
   using S = Shape<R, L>;
   const int W = 2 * S::C;
   const unsigned grid = (unsigned)((n + W - 1) / W);
@@ -30,14 +60,27 @@ static cudaError_t run_forward(int64_t n, int64_t n_pad, const double *x, const 
 template <typename R, int L>
 static cudaError_t run_inverse(int64_t n, int64_t n_pad, const cx<R> *spec, double *y,
                                const cx<R> *tw, cudaStream_t s) {
-  using S = Shape<R, L>;
-  const int W = 2 * S::C;
-  const unsigned grid = (unsigned)((n + W - 1) / W);
-  cudaError_t e = cudaFuncSetAttribute(k_fft_inverse<R, L>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)S::SMEM);
+  if (!AAO_FFT_PIPE) {
+    using S = Shape<R, L>;
+    const int W = 2 * S::C;
+    const unsigned grid = (unsigned)((n + W - 1) / W);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_inverse<R, L>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)S::SMEM);
+    if (e != cudaSuccess) return e;
+    k_fft_inverse<R, L><<<grid, S::T, S::SMEM, s>>>(spec, y, (int)n, n_pad, tw);
+    note_launch();
+    return cudaGetLastError();
+  }
+  using P = PShape<R, L>;
+  const int np = (int)((n + 2 * P::C - 1) / (2 * P::C));
+  auto kern = k_fft_inverse_pipe<R, L>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)P::SMEM_I);
   if (e != cudaSuccess) return e;
-  k_fft_inverse<R, L><<<grid, S::T, S::SMEM, s>>>(spec, y, (int)n, n_pad, tw); note_launch();
+  const int g = persistent_grid(kern, P::T, P::SMEM_I, np);
+  kern<<<g, P::T, P::SMEM_I, s>>>(spec, y, (int)n, n_pad, tw, np);
+  note_launch();
   return cudaGetLastError();
 }
 

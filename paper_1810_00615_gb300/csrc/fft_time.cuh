@@ -181,6 +181,12 @@ template <int L> struct Passes {
   static constexpr int R1 = (L <= 16) ? L : (1 << (LOG2 - 4 * (NP - 1)));   // first radix
 };
 
+// Copy the twiddle table (L entries) into shared memory.
+template <typename R, int L, int T>
+__device__ __forceinline__ void load_twiddles(cx<R> *stw, const cx<R> *__restrict__ tw) {
+  for (int m = threadIdx.x; m < L; m += T) stw[m] = tw[m];
+}
+
 // Full length-L transform of the C columns in shared memory.
 template <typename R, int L, int C, int DIR, int T>
 __device__ __forceinline__ void transform(cx<R> *sm, const cx<R> *__restrict__ tw) {
@@ -206,7 +212,7 @@ __device__ __forceinline__ void transform(cx<R> *sm, const cx<R> *__restrict__ t
 // leave room for three CTAs per SM so that one CTA's loads overlap another's
 // passes.
 #ifndef AAO_FFT_CAP32
-#define AAO_FFT_CAP32 8192
+#define AAO_FFT_CAP32 16384
 #endif
 #ifndef AAO_FFT_CAP64
 #define AAO_FFT_CAP64 8192
@@ -215,12 +221,17 @@ template <typename R> struct Cap;
 template <> struct Cap<float> { static constexpr int V = AAO_FFT_CAP32; };
 template <> struct Cap<double> { static constexpr int V = AAO_FFT_CAP64; };
 
+#ifndef AAO_FFT_STW
+#define AAO_FFT_STW 0
+#endif
 template <typename R, int L> struct Shape {
   static constexpr int C0 = Cap<R>::V / L;
   static constexpr int C = C0 > 16 ? 16 : (C0 < 1 ? 1 : C0);   // complex columns
   static constexpr int E = (L < 16) ? L : 16;                   // points per thread
   static constexpr int T = L * C / E;                           // threads
-  static constexpr size_t SMEM = (size_t)(L + (L >> 4) + 1) * C * sizeof(cx<R>);
+  static constexpr size_t WORK = ((size_t)(L + (L >> 4) + 1) * C * sizeof(cx<R>) + 15) & ~(size_t)15;
+  static constexpr size_t TWB = AAO_FFT_STW ? (size_t)L * sizeof(cx<R>) : 0;   // twiddle copy
+  static constexpr size_t SMEM = WORK + TWB;
 };
 
 // Forward: x (FP64, ell x n) -> half spectrum (R complex, nk x n_pad).
@@ -256,6 +267,12 @@ k_fft_forward(const double *__restrict__ x, const double *__restrict__ y,
   constexpr int NB = E / R1;
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
+  const cx<R> *twp = tw;
+  if constexpr (AAO_FFT_STW) {
+    cx<R> *stw = reinterpret_cast<cx<R> *>(smraw + S::WORK);
+    load_twiddles<R, L, T>(stw, tw);
+    twp = stw;
+  }
   const int i0 = blockIdx.x * (2 * C);
 
   {
@@ -286,7 +303,7 @@ k_fft_forward(const double *__restrict__ x, const double *__restrict__ y,
     int Ns = R1;
 #pragma unroll
     for (int p = 1; p < PL::NP; p++) {
-      pass<R, L, C, 16, -1, T>(sm, Ns, tw);
+      pass<R, L, C, 16, -1, T>(sm, Ns, twp);
       Ns *= 16;
     }
   }
@@ -311,19 +328,29 @@ k_fft_forward(const double *__restrict__ x, const double *__restrict__ y,
   }
 }
 
-// Inverse: half spectrum -> y (FP64), scaled by 1/L.  The last Stockham pass
-// (where j < Ns, so output index j + r Ns is time step t) writes straight to
-// global memory.
+// Inverse: half spectrum -> y (FP64), scaled by 1/L.  With AAO_FFT_DIRECT_OUT
+// the last Stockham pass (where j < Ns, so output index j + r Ns is time step
+// t) writes straight to global memory; otherwise the result goes through
+// shared memory and is written row by row (2C contiguous doubles per step).
+#ifndef AAO_FFT_DIRECT_OUT
+#define AAO_FFT_DIRECT_OUT 0
+#endif
 template <typename R, int L>
 __global__ void __launch_bounds__(Shape<R, L>::T)
 k_fft_inverse(const cx<R> *__restrict__ spec, double *__restrict__ y, int n, int64_t n_pad,
               const cx<R> *__restrict__ tw) {
   using S = Shape<R, L>;
   using PL = Passes<L>;
-  constexpr int C = S::C, T = S::T, E = S::E;
+  constexpr int C = S::C, T = S::T, E = S::E, W = 2 * C;
   extern __shared__ __align__(16) unsigned char smraw[];
   cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
-  const int i0 = blockIdx.x * (2 * C);
+  const cx<R> *twp = tw;
+  if constexpr (AAO_FFT_STW) {
+    cx<R> *stw = reinterpret_cast<cx<R> *>(smraw + S::WORK);
+    load_twiddles<R, L, T>(stw, tw);
+    twp = stw;
+  }
+  const int i0 = blockIdx.x * W;
   constexpr int NK = L / 2 + 1;
   for (int idx = threadIdx.x; idx < NK * C; idx += T) {
     const int k = idx / C, c = idx - k * C;
@@ -338,20 +365,31 @@ k_fft_inverse(const cx<R> *__restrict__ spec, double *__restrict__ y, int n, int
     if (k > 0 && 2 * k < L) sm[phys<C>(L - k, c)] = mk(A.re + B.im, B.re - A.im);
   }
   __syncthreads();
+  const R scale = (R)1 / (R)L;
+
+  if constexpr (!AAO_FFT_DIRECT_OUT) {
+    transform<R, L, C, +1, T>(sm, twp);
+    const R *smr = reinterpret_cast<const R *>(smraw);
+#pragma unroll 8
+    for (int idx = threadIdx.x; idx < L * W; idx += T) {
+      const int t = idx / W, w = idx - t * W, i = i0 + w;
+      if (i < n) y[(size_t)t * n + i] = to_double<R>(scale * smr[2 * phys<C>(t, w >> 1) + (w & 1)]);
+    }
+    return;
+  }
 
   constexpr int RL = (PL::NP <= 1) ? (L < 1 ? 1 : L) : 16;   // radix of the last pass
   int Ns = 1;
   if constexpr (PL::NP > 1) {
-    pass<R, L, C, PL::R1, +1, T>(sm, 1, tw);
+    pass<R, L, C, PL::R1, +1, T>(sm, 1, twp);
     Ns = PL::R1;
 #pragma unroll
     for (int p = 1; p < PL::NP - 1; p++) {
-      pass<R, L, C, 16, +1, T>(sm, Ns, tw);
+      pass<R, L, C, 16, +1, T>(sm, Ns, twp);
       Ns *= 16;
     }
   }
   constexpr int NB = E / RL;
-  const R scale = (R)1 / (R)L;
 #pragma unroll
   for (int q = 0; q < NB; q++) {
     const int b = threadIdx.x + q * T;
@@ -362,7 +400,7 @@ k_fft_inverse(const cx<R> *__restrict__ spec, double *__restrict__ y, int n, int
     if (Ns > 1) {
       const int step = j * (L / (Ns * RL));
 #pragma unroll
-      for (int r = 1; r < RL; r++) v[r] = twiddle<R, +1>(v[r], tw[step * r]);
+      for (int r = 1; r < RL; r++) v[r] = twiddle<R, +1>(v[r], twp[step * r]);
     }
     dft<R, +1, RL>(v);
     const int i = i0 + 2 * c;
@@ -372,6 +410,218 @@ k_fft_inverse(const cx<R> *__restrict__ spec, double *__restrict__ y, int n, int
       if (i < n) y[o] = to_double<R>(scale * v[r].re);
       if (i + 1 < n) y[o + 1] = to_double<R>(scale * v[r].im);
     }
+  }
+}
+
+// ------------------------------------------------ pipelined persistent FFTs
+// The kernels above move their panel in one burst and then compute, so with
+// one or two CTAs per SM the DRAM is idle during the passes.  The persistent
+// variants below keep a second shared buffer: while a CTA transforms panel
+// p, cp.async (asynchronous global -> shared copies) bring in panel p + grid
+// so that the loads overlap the passes.
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+#ifndef AAO_FFT_PCAP32
+#define AAO_FFT_PCAP32 8192
+#endif
+#ifndef AAO_FFT_PCAP64
+#define AAO_FFT_PCAP64 4096
+#endif
+template <typename R> struct PCap;   // complex points of the work buffer
+template <> struct PCap<float> { static constexpr int V = AAO_FFT_PCAP32; };
+template <> struct PCap<double> { static constexpr int V = AAO_FFT_PCAP64; };
+
+template <typename R, int L> struct PShape {
+  static constexpr int C0 = PCap<R>::V / L;
+  static constexpr int C = C0 > 16 ? 16 : (C0 < 1 ? 1 : C0);
+  static constexpr int E = (L < 16) ? L : 16;
+  static constexpr int T = L * C / E;
+  static constexpr size_t WORK = ((size_t)(L + (L >> 4) + 1) * C * sizeof(cx<R>) + 15) & ~(size_t)15;
+  static constexpr size_t STAGE_F = (size_t)L * 2 * C * sizeof(double);          // raw FP64 rows
+  static constexpr size_t STAGE_I = (size_t)(L / 2 + 1) * 2 * C * sizeof(cx<R>);  // half spectrum
+  static constexpr size_t SMEM_F = WORK + STAGE_F;
+  static constexpr size_t SMEM_I = WORK + STAGE_I;
+};
+
+template <typename R, int L>
+__device__ __forceinline__ void stage_rows(double *stage, const double *__restrict__ x, int n,
+                                           int i0) {
+  using S = PShape<R, L>;
+  constexpr int W = 2 * S::C;
+  for (int q = threadIdx.x; q < L * W; q += S::T) {
+    const int t = q / W, w = q - t * W, i = i0 + w;
+    const bool ok = i < n;
+    cp_async8(&stage[q], ok ? &x[(size_t)t * n + i] : x, ok);
+  }
+  cp_commit();
+}
+
+template <typename R, int L>
+__global__ void __launch_bounds__(PShape<R, L>::T)
+k_fft_forward_pipe(const double *__restrict__ x, cx<R> *__restrict__ spec, int n, int64_t n_pad,
+                   const cx<R> *__restrict__ tw, int npanels) {
+  using S = PShape<R, L>;
+  using PL = Passes<L>;
+  constexpr int C = S::C, T = S::T, E = S::E, W = 2 * C;
+  constexpr int R1 = PL::R1 < 1 ? 1 : PL::R1;
+  constexpr int NB = E / R1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
+  double *stage = reinterpret_cast<double *>(smraw + S::WORK);
+
+  int panel = blockIdx.x;
+  if (panel < npanels) stage_rows<R, L>(stage, x, n, panel * W);
+  for (; panel < npanels; panel += gridDim.x) {
+    const int i0 = panel * W;
+    cp_wait_all();
+    __syncthreads();
+    cx<R> v[NB][R1];
+#pragma unroll
+    for (int q = 0; q < NB; q++) {
+      const int b = threadIdx.x + q * T;
+      const int c = b % C, j = b / C;
+#pragma unroll
+      for (int r = 0; r < R1; r++) {
+        const int t = j + r * (L / R1);
+        const double2 d = *reinterpret_cast<const double2 *>(&stage[t * W + 2 * c]);
+        v[q][r] = mk(from_f64<R>(d.x), from_f64<R>(d.y));
+      }
+    }
+    __syncthreads();                       // stage free: prefetch the next panel
+    if (panel + (int)gridDim.x < npanels) stage_rows<R, L>(stage, x, n, (panel + gridDim.x) * W);
+#pragma unroll
+    for (int q = 0; q < NB; q++) {
+      const int b = threadIdx.x + q * T;
+      const int c = b % C, j = b / C;
+      dft<R, -1, R1>(v[q]);
+#pragma unroll
+      for (int r = 0; r < R1; r++) sm[phys<C>(j * R1 + r, c)] = v[q][r];
+    }
+    __syncthreads();
+    if constexpr (PL::NP > 1) {
+      int Ns = R1;
+#pragma unroll
+      for (int p = 1; p < PL::NP; p++) {
+        pass<R, L, C, 16, -1, T>(sm, Ns, tw);
+        Ns *= 16;
+      }
+    }
+    constexpr int NK = L / 2 + 1;
+    for (int idx = threadIdx.x; idx < NK * C; idx += T) {
+      const int k = idx / C, c = idx - k * C;
+      const cx<R> zk = sm[phys<C>(k, c)];
+      const cx<R> zm = sm[phys<C>((L - k) & (L - 1), c)];
+      const R hf = (R)0.5;
+      const cx<R> X = mk(hf * (zk.re + zm.re), hf * (zk.im - zm.im));
+      const cx<R> Y = mk(hf * (zk.im + zm.im), hf * (zm.re - zk.re));
+      const int i = i0 + 2 * c;
+      cx<R> *dst = spec + (size_t)k * n_pad + i;
+      if (i + 1 < n) {
+        dst[0] = X;
+        dst[1] = Y;
+      } else if (i < n) {
+        dst[0] = X;
+      }
+    }
+    __syncthreads();                       // work buffer reused by the next panel
+  }
+}
+
+template <typename R, int L>
+__device__ __forceinline__ void stage_spec(cx<R> *stage, const cx<R> *__restrict__ spec, int n,
+                                           int64_t n_pad, int i0) {
+  using S = PShape<R, L>;
+  constexpr int W = 2 * S::C;
+  constexpr int EPC = 16 / sizeof(cx<R>);   // complex per 16-byte copy
+  constexpr int CPR = W / EPC;               // copies per row
+  constexpr int NK = L / 2 + 1;
+  for (int q = threadIdx.x; q < NK * CPR; q += S::T) {
+    const int k = q / CPR, u = q - k * CPR, i = i0 + u * EPC;
+    const bool ok = i < n;                   // i < n <= n_pad: the 16 bytes lie in the row
+    cp_async16(&stage[k * W + u * EPC], ok ? &spec[(size_t)k * n_pad + i] : spec, ok);
+  }
+  cp_commit();
+}
+
+template <typename R, int L>
+__global__ void __launch_bounds__(PShape<R, L>::T)
+k_fft_inverse_pipe(const cx<R> *__restrict__ spec, double *__restrict__ y, int n, int64_t n_pad,
+                   const cx<R> *__restrict__ tw, int npanels) {
+  using S = PShape<R, L>;
+  using PL = Passes<L>;
+  constexpr int C = S::C, T = S::T, E = S::E, W = 2 * C;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
+  cx<R> *stage = reinterpret_cast<cx<R> *>(smraw + S::WORK);
+  constexpr int NK = L / 2 + 1;
+  constexpr int RL = (PL::NP <= 1) ? (L < 1 ? 1 : L) : 16;
+  constexpr int NB = E / RL;
+  const R scale = (R)1 / (R)L;
+
+  int panel = blockIdx.x;
+  if (panel < npanels) stage_spec<R, L>(stage, spec, n, n_pad, panel * W);
+  for (; panel < npanels; panel += gridDim.x) {
+    const int i0 = panel * W;
+    cp_wait_all();
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NK * C; idx += T) {
+      const int k = idx / C, c = idx - k * C;
+      const int i = i0 + 2 * c;
+      cx<R> A = (i < n) ? stage[k * W + 2 * c] : mk((R)0, (R)0);
+      cx<R> B = (i + 1 < n) ? stage[k * W + 2 * c + 1] : mk((R)0, (R)0);
+      if (k == 0 || 2 * k == L) { A.im = (R)0; B.im = (R)0; }
+      sm[phys<C>(k, c)] = mk(A.re - B.im, A.im + B.re);
+      if (k > 0 && 2 * k < L) sm[phys<C>(L - k, c)] = mk(A.re + B.im, B.re - A.im);
+    }
+    __syncthreads();                       // stage free: prefetch the next panel
+    if (panel + (int)gridDim.x < npanels)
+      stage_spec<R, L>(stage, spec, n, n_pad, (panel + gridDim.x) * W);
+    int Ns = 1;
+    if constexpr (PL::NP > 1) {
+      pass<R, L, C, PL::R1, +1, T>(sm, 1, tw);
+      Ns = PL::R1;
+#pragma unroll
+      for (int p = 1; p < PL::NP - 1; p++) {
+        pass<R, L, C, 16, +1, T>(sm, Ns, tw);
+        Ns *= 16;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NB; q++) {
+      const int b = threadIdx.x + q * T;
+      const int c = b % C, j = b / C;
+      cx<R> v[RL];
+#pragma unroll
+      for (int r = 0; r < RL; r++) v[r] = sm[phys<C>(j + r * (L / RL), c)];
+      if (Ns > 1) {
+        const int step = j * (L / (Ns * RL));
+#pragma unroll
+        for (int r = 1; r < RL; r++) v[r] = twiddle<R, +1>(v[r], tw[step * r]);
+      }
+      dft<R, +1, RL>(v);
+      const int i = i0 + 2 * c;
+#pragma unroll
+      for (int r = 0; r < RL; r++) {
+        const size_t o = (size_t)(j + r * Ns) * n + i;
+        if (i < n) y[o] = to_double<R>(scale * v[r].re);
+        if (i + 1 < n) y[o + 1] = to_double<R>(scale * v[r].im);
+      }
+    }
+    __syncthreads();                       // work buffer reused by the next panel
   }
 }
 
