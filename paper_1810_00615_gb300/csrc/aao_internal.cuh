@@ -108,6 +108,21 @@ struct TriTab {
   cx<R> sig_last, off_last;  // last separator row (regular | last chunk)
 };
 
+// Recursive form for rows whose separator systems are again regular
+// (n + 1 a power of CH times a chunk count at every level, e.g. n = 2^p - 1):
+// level l is the constant-coefficient system (sigma_l, e_l) of the level-(l-1)
+// separators, cut again into chunks of CH-1 unknowns plus a separator, down
+// to a last level of at most CH-1 unknowns solved by one Thomas sweep.  Per
+// level: chunk pivots, Green's function and off-diagonal.
+constexpr int kRecLevels = 6;
+template <typename R, int CH>
+struct RecTab {
+  cx<R> invp[kRecLevels][CH];
+  cx<R> bp[kRecLevels][CH];
+  cx<R> fc[kRecLevels][CH];
+  cx<R> e[kRecLevels];
+};
+
 // ------------------------------------------------------------ context
 struct Ctx {
   int64_t n = 0, ell = 0, N = 0;
@@ -127,6 +142,10 @@ struct Ctx {
   // device-side constants (owned)
   void *tab32 = nullptr;   // TriTab<float, ch32>[nk]; the transposed symbols are their conjugates
   void *tab64 = nullptr;   // TriTab<double, ch64>[nk]
+  void *rec32 = nullptr;   // RecTab<float, ch32>[nk] when the recursive form applies
+  void *rec64 = nullptr;   // RecTab<double, ch64>[nk]
+  int lev32 = 0, lev64 = 0;             // levels of the recursive form (0: not applicable)
+  int lsz32[kRecLevels] = {0}, lsz64[kRecLevels] = {0};   // unknowns per level
   cx<float> *tw32 = nullptr;      // exp(-2 pi i m/ell), m < ell
   cx<double> *tw64 = nullptr;
   double *beta = nullptr;         // per-step K coefficient tau_t kappa / h (ell)
@@ -151,6 +170,15 @@ struct Ctx {
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
 };
+
+}  // namespace aao
+
+// The opaque handle of the C ABI.
+struct aao_ctx {
+  aao::Ctx c;
+};
+
+namespace aao {
 
 // Workspace layout (offsets in bytes from ws, each 256-byte aligned).
 struct WsLayout {

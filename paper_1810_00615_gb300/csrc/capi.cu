@@ -17,10 +17,6 @@ using aao::Ctx;
 using aao::cx;
 using cd = std::complex<double>;
 
-struct aao_ctx {
-  Ctx c;
-};
-
 namespace {
 
 constexpr int kMaxRestart = 128;
@@ -135,6 +131,71 @@ void build_tables(const Ctx &c, int64_t cl, std::vector<aao::TriTab<R, CH>> &tab
   }
 }
 
+// Tables of the recursive form: level l is (sigma_l, e_l); its chunks of
+// CH-1 unknowns have pivots invp/bp and Green's function g; the separators
+// form level l+1 with sigma_{l+1} = sigma_l (1 - 2 e_l w_l[0]) and
+// e_{l+1} = -e_l^2 g_l[CH-2] (w_l = T^{-1} 1), all in FP64.
+template <typename R, int CH>
+void build_rec_tables(const Ctx &c, int levels, std::vector<aao::RecTab<R, CH>> &tabs) {
+  tabs.assign((size_t)c.nk, aao::RecTab<R, CH>{});
+  const int cr = CH - 1;
+  for (int64_t k = 0; k < c.nk; k++) {
+    cd cM, sig, e;
+    double cK;
+    block_symbol(c, k, cM, cK);
+    excess_form(c, cM, cK, sig, e);
+    auto &T = tabs[(size_t)k];
+    for (int l = 0; l < levels; l++) {
+      std::vector<cd> invp(CH), bp(CH);
+      cd q = sig - e, pv = q - e;
+      for (int i = 0; i < CH; i++) {
+        if (i > 0) {
+          q = sig - e * q / pv;
+          pv = q - e;
+        }
+        invp[i] = 1.0 / pv;
+        bp[i] = e / pv;
+      }
+      std::vector<cd> unit_first(CH, cd(0, 0)), ones(CH, cd(1, 0)), g, w;
+      unit_first[0] = 1.0;
+      chunk_solve(invp, bp, e, unit_first, cr, g);
+      chunk_solve(invp, bp, e, ones, cr, w);
+      for (int i = 0; i < CH; i++) {
+        T.invp[l][i] = to_cx<R>(invp[i]);
+        T.bp[l][i] = to_cx<R>(bp[i]);
+        T.fc[l][i] = to_cx<R>(i < cr ? -e * g[i] : cd(0, 0));
+      }
+      T.e[l] = to_cx<R>(e);
+      const cd sig_next = sig * (1.0 - 2.0 * e * w[0]);
+      const cd e_next = -e * e * g[cr - 1];
+      sig = sig_next;
+      e = e_next;
+    }
+  }
+}
+
+// Level sizes of the recursive form, or 0 levels if some chunked level is
+// not an exact multiple of CH (then the cyclic-reduction kernel is used).
+int rec_levels(int64_t n, int CH, int *lsz) {
+  int levels = 0;
+  int64_t m = n;
+  while (true) {
+    if (levels >= aao::kRecLevels) return 0;
+    lsz[levels++] = (int)m;
+    if (m <= CH - 1) break;
+    if ((m + 1) % CH != 0) return 0;
+    m = (m + 1) / CH - 1;
+  }
+  if (levels < 2) return 0;   // a single chunk: the plain kernel is as good
+  if ((n + 1) / CH > 1024) return 0;
+  return levels;
+}
+
+// The recursive kernel stages the whole row in shared memory.
+bool rec_fits(int64_t n, int CH, size_t elem) {
+  return (size_t)((n + 1) / CH) * CH * elem <= 160 * 1024;
+}
+
 // Chunks of a row of n unknowns with chunk length CH (CH-1 unknowns + one
 // separator); returns the chunk count P and the last chunk's size cl.
 void chunking(int64_t n, int CH, int &P, int64_t &cl) {
@@ -229,6 +290,25 @@ int refresh_constants(Ctx &c) {
       std::vector<aao::TriTab<double, 16>> t64;
       build_tables<double, 16>(c, cl, t64);
       AAO_CK(c, upload(&c.tab64, t64));
+    }
+  }
+  // recursive tables where the row structure allows them
+  c.lev32 = rec_fits(c.n, c.ch32, sizeof(cx<float>)) ? rec_levels(c.n, c.ch32, c.lsz32) : 0;
+  if (c.lev32 > 0) {
+    std::vector<aao::RecTab<float, 16>> r32;
+    build_rec_tables<float, 16>(c, c.lev32, r32);
+    AAO_CK(c, upload(&c.rec32, r32));
+  }
+  c.lev64 = rec_fits(c.n, c.ch64, sizeof(cx<double>)) ? rec_levels(c.n, c.ch64, c.lsz64) : 0;
+  if (c.lev64 > 0) {
+    if (c.ch64 == 8) {
+      std::vector<aao::RecTab<double, 8>> r64;
+      build_rec_tables<double, 8>(c, c.lev64, r64);
+      AAO_CK(c, upload(&c.rec64, r64));
+    } else {
+      std::vector<aao::RecTab<double, 16>> r64;
+      build_rec_tables<double, 16>(c, c.lev64, r64);
+      AAO_CK(c, upload(&c.rec64, r64));
     }
   }
   // matvec K coefficients beta_t and Neumann coefficients (tau_t - tau) kappa / h
@@ -583,7 +663,8 @@ int aao_create(int64_t n, int64_t ell, double tau, int equation, aao_ctx **out) 
 void aao_destroy(aao_ctx *ctx) {
   if (!ctx) return;
   Ctx &c = ctx->c;
-  void *ptrs[] = {c.tab32, c.tab64, c.tw32, c.tw64, c.beta, c.mv_d0, c.mv_o0, c.sigk, c.sigk32};
+  void *ptrs[] = {c.tab32, c.tab64, c.rec32, c.rec64, c.tw32, c.tw64, c.beta, c.mv_d0, c.mv_o0,
+                  c.sigk, c.sigk32};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c.host_small) cudaFreeHost(c.host_small);

@@ -32,7 +32,7 @@ static cudaError_t run_forward(int64_t n, int64_t n_pad, const double *x, const 
     auto kern = k_fft_forward_pipe<R, L>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)P::SMEM_F);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) { cudaGetLastError(); return e; }
     const int g = persistent_grid(kern, P::T, P::SMEM_F, np);
     kern<<<g, P::T, P::SMEM_F, s>>>(x, spec, (int)n, n_pad, tw, np);
     note_launch();
@@ -40,20 +40,22 @@ static cudaError_t run_forward(int64_t n, int64_t n_pad, const double *x, const 
   }
   using S = Shape<R, L>;
   const int W = 2 * S::C;
-  const unsigned grid = (unsigned)((n + W - 1) / W);
+  const int np = (int)((n + W - 1) / W);
   cudaError_t e;
   if (y) {
-    e = cudaFuncSetAttribute(k_fft_forward<R, L, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
-    if (e != cudaSuccess) return e;
-    k_fft_forward<R, L, true><<<grid, S::T, S::SMEM, s>>>(x, y, sigk, spec, (int)n, n_pad, tw); note_launch();
+    auto kern = k_fft_forward<R, L, true>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    if (e != cudaSuccess) { cudaGetLastError(); return e; }
+    const int g = persistent_grid(kern, S::T, S::SMEM, np);
+    kern<<<g, S::T, S::SMEM, s>>>(x, y, sigk, spec, (int)n, n_pad, tw, np);
   } else {
-    e = cudaFuncSetAttribute(k_fft_forward<R, L, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
-    if (e != cudaSuccess) return e;
-    k_fft_forward<R, L, false><<<grid, S::T, S::SMEM, s>>>(x, nullptr, nullptr, spec, (int)n,
-                                                           n_pad, tw); note_launch();
+    auto kern = k_fft_forward<R, L, false>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    if (e != cudaSuccess) { cudaGetLastError(); return e; }
+    const int g = persistent_grid(kern, S::T, S::SMEM, np);
+    kern<<<g, S::T, S::SMEM, s>>>(x, nullptr, nullptr, spec, (int)n, n_pad, tw, np);
   }
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -63,12 +65,13 @@ static cudaError_t run_inverse(int64_t n, int64_t n_pad, const cx<R> *spec, doub
   if (!AAO_FFT_PIPE) {
     using S = Shape<R, L>;
     const int W = 2 * S::C;
-    const unsigned grid = (unsigned)((n + W - 1) / W);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_inverse<R, L>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const int np = (int)((n + W - 1) / W);
+    auto kern = k_fft_inverse<R, L>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::SMEM);
-    if (e != cudaSuccess) return e;
-    k_fft_inverse<R, L><<<grid, S::T, S::SMEM, s>>>(spec, y, (int)n, n_pad, tw);
+    if (e != cudaSuccess) { cudaGetLastError(); return e; }
+    const int g = persistent_grid(kern, S::T, S::SMEM, np);
+    kern<<<g, S::T, S::SMEM, s>>>(spec, y, (int)n, n_pad, tw, np);
     note_launch();
     return cudaGetLastError();
   }
@@ -77,7 +80,7 @@ static cudaError_t run_inverse(int64_t n, int64_t n_pad, const cx<R> *spec, doub
   auto kern = k_fft_inverse_pipe<R, L>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)P::SMEM_I);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) { cudaGetLastError(); return e; }
   const int g = persistent_grid(kern, P::T, P::SMEM_I, np);
   kern<<<g, P::T, P::SMEM_I, s>>>(spec, y, (int)n, n_pad, tw, np);
   note_launch();

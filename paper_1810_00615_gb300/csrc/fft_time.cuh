@@ -255,14 +255,36 @@ __device__ __forceinline__ R load_real(const double *__restrict__ x, const doubl
   }
 }
 
+// L2 prefetch of a panel's rows (2C doubles of each of the L time steps),
+// one request per touched 128-byte line: the loads of the next panel then
+// hit L2, which keeps the latency-bound load phase short.
+#ifndef AAO_FFT_PREFETCH
+#define AAO_FFT_PREFETCH 1
+#endif
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+template <int L, int W, int T>
+__device__ __forceinline__ void prefetch_rows(const double *__restrict__ x, int n, int i0) {
+  if (i0 >= n) return;
+  const int last = min(i0 + W, n) - 1;
+  for (int t = threadIdx.x; t < L; t += T) {
+    const double *a = x + (size_t)t * n + i0;
+    const double *b = x + (size_t)t * n + last;
+    prefetch_l2(a);
+    if (((uintptr_t)a >> 7) != ((uintptr_t)b >> 7)) prefetch_l2(b);
+  }
+}
+
 template <typename R, int L, bool NEUMANN>
 __global__ void __launch_bounds__(Shape<R, L>::T)
 k_fft_forward(const double *__restrict__ x, const double *__restrict__ y,
               const R *__restrict__ sigk, cx<R> *__restrict__ spec, int n, int64_t n_pad,
-              const cx<R> *__restrict__ tw) {
+              const cx<R> *__restrict__ tw, int npanels) {
   using S = Shape<R, L>;
   using PL = Passes<L>;
-  constexpr int C = S::C, T = S::T, E = S::E;
+  constexpr int C = S::C, T = S::T, E = S::E, W = 2 * C;
   constexpr int R1 = PL::R1 < 1 ? 1 : PL::R1;
   constexpr int NB = E / R1;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -273,58 +295,61 @@ k_fft_forward(const double *__restrict__ x, const double *__restrict__ y,
     load_twiddles<R, L, T>(stw, tw);
     twp = stw;
   }
-  const int i0 = blockIdx.x * (2 * C);
-
-  {
-    cx<R> v[NB][R1];
+  for (int panel = blockIdx.x; panel < npanels; panel += gridDim.x) {
+    const int i0 = panel * W;
+    if (AAO_FFT_PREFETCH && !NEUMANN) prefetch_rows<L, W, T>(x, n, (panel + gridDim.x) * W);
+    {
+      cx<R> v[NB][R1];
 #pragma unroll
-    for (int q = 0; q < NB; q++) {
-      const int b = threadIdx.x + q * T;
-      const int c = b % C, j = b / C;
-      const int i = i0 + 2 * c;
+      for (int q = 0; q < NB; q++) {
+        const int b = threadIdx.x + q * T;
+        const int c = b % C, j = b / C;
+        const int i = i0 + 2 * c;
 #pragma unroll
-      for (int r = 0; r < R1; r++) {
-        const int t = j + r * (L / R1);
-        v[q][r] = mk(load_real<R, L, NEUMANN>(x, y, sigk, n, t, i),
-                     load_real<R, L, NEUMANN>(x, y, sigk, n, t, i + 1));
+        for (int r = 0; r < R1; r++) {
+          const int t = j + r * (L / R1);
+          v[q][r] = mk(load_real<R, L, NEUMANN>(x, y, sigk, n, t, i),
+                       load_real<R, L, NEUMANN>(x, y, sigk, n, t, i + 1));
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NB; q++) {
+        const int b = threadIdx.x + q * T;
+        const int c = b % C, j = b / C;
+        dft<R, -1, R1>(v[q]);
+#pragma unroll
+        for (int r = 0; r < R1; r++) sm[phys<C>(j * R1 + r, c)] = v[q][r];
       }
     }
+    __syncthreads();
+    if constexpr (PL::NP > 1) {
+      int Ns = R1;
 #pragma unroll
-    for (int q = 0; q < NB; q++) {
-      const int b = threadIdx.x + q * T;
-      const int c = b % C, j = b / C;
-      dft<R, -1, R1>(v[q]);
-#pragma unroll
-      for (int r = 0; r < R1; r++) sm[phys<C>(j * R1 + r, c)] = v[q][r];
+      for (int p = 1; p < PL::NP; p++) {
+        pass<R, L, C, 16, -1, T>(sm, Ns, twp);
+        Ns *= 16;
+      }
     }
-  }
-  __syncthreads();
-  if constexpr (PL::NP > 1) {
-    int Ns = R1;
-#pragma unroll
-    for (int p = 1; p < PL::NP; p++) {
-      pass<R, L, C, 16, -1, T>(sm, Ns, twp);
-      Ns *= 16;
-    }
-  }
 
-  // unpack the two real columns of each complex column and write k = 0..L/2
-  constexpr int NK = L / 2 + 1;
-  for (int idx = threadIdx.x; idx < NK * C; idx += T) {
-    const int k = idx / C, c = idx - k * C;
-    const cx<R> zk = sm[phys<C>(k, c)];
-    const cx<R> zm = sm[phys<C>((L - k) & (L - 1), c)];
-    const R hf = (R)0.5;
-    const cx<R> X = mk(hf * (zk.re + zm.re), hf * (zk.im - zm.im));
-    const cx<R> Y = mk(hf * (zk.im + zm.im), hf * (zm.re - zk.re));
-    const int i = i0 + 2 * c;
-    cx<R> *dst = spec + (size_t)k * n_pad + i;
-    if (i + 1 < n) {
-      dst[0] = X;
-      dst[1] = Y;
-    } else if (i < n) {
-      dst[0] = X;
+    // unpack the two real columns of each complex column and write k = 0..L/2
+    constexpr int NK = L / 2 + 1;
+    for (int idx = threadIdx.x; idx < NK * C; idx += T) {
+      const int k = idx / C, c = idx - k * C;
+      const cx<R> zk = sm[phys<C>(k, c)];
+      const cx<R> zm = sm[phys<C>((L - k) & (L - 1), c)];
+      const R hf = (R)0.5;
+      const cx<R> X = mk(hf * (zk.re + zm.re), hf * (zk.im - zm.im));
+      const cx<R> Y = mk(hf * (zk.im + zm.im), hf * (zm.re - zk.re));
+      const int i = i0 + 2 * c;
+      cx<R> *dst = spec + (size_t)k * n_pad + i;
+      if (i + 1 < n) {
+        dst[0] = X;
+        dst[1] = Y;
+      } else if (i < n) {
+        dst[0] = X;
+      }
     }
+    __syncthreads();   // the work buffer is reused by the next panel
   }
 }
 
@@ -335,10 +360,23 @@ k_fft_forward(const double *__restrict__ x, const double *__restrict__ y,
 #ifndef AAO_FFT_DIRECT_OUT
 #define AAO_FFT_DIRECT_OUT 0
 #endif
+template <int NK, int W, int T, typename CXT>
+__device__ __forceinline__ void prefetch_spec(const CXT *__restrict__ spec, int n, int64_t n_pad,
+                                              int i0) {
+  if (i0 >= n) return;
+  const int last = min(i0 + W, n) - 1;
+  for (int k = threadIdx.x; k < NK; k += T) {
+    const CXT *a = spec + (size_t)k * n_pad + i0;
+    const CXT *b = spec + (size_t)k * n_pad + last;
+    prefetch_l2(a);
+    if (((uintptr_t)a >> 7) != ((uintptr_t)b >> 7)) prefetch_l2(b);
+  }
+}
+
 template <typename R, int L>
 __global__ void __launch_bounds__(Shape<R, L>::T)
 k_fft_inverse(const cx<R> *__restrict__ spec, double *__restrict__ y, int n, int64_t n_pad,
-              const cx<R> *__restrict__ tw) {
+              const cx<R> *__restrict__ tw, int npanels) {
   using S = Shape<R, L>;
   using PL = Passes<L>;
   constexpr int C = S::C, T = S::T, E = S::E, W = 2 * C;
@@ -350,24 +388,24 @@ k_fft_inverse(const cx<R> *__restrict__ spec, double *__restrict__ y, int n, int
     load_twiddles<R, L, T>(stw, tw);
     twp = stw;
   }
-  const int i0 = blockIdx.x * W;
   constexpr int NK = L / 2 + 1;
-  for (int idx = threadIdx.x; idx < NK * C; idx += T) {
-    const int k = idx / C, c = idx - k * C;
-    const int i = i0 + 2 * c;
-    const cx<R> *src = spec + (size_t)k * n_pad + i;
-    cx<R> A = mk((R)0, (R)0), B = mk((R)0, (R)0);
-    if (i < n) A = src[0];
-    if (i + 1 < n) B = src[1];
-    if (k == 0 || 2 * k == L) { A.im = (R)0; B.im = (R)0; }
-    // Z = A + i B for the pair of real outputs; Hermitian extension for L-k
-    sm[phys<C>(k, c)] = mk(A.re - B.im, A.im + B.re);
-    if (k > 0 && 2 * k < L) sm[phys<C>(L - k, c)] = mk(A.re + B.im, B.re - A.im);
-  }
-  __syncthreads();
   const R scale = (R)1 / (R)L;
-
-  if constexpr (!AAO_FFT_DIRECT_OUT) {
+  for (int panel = blockIdx.x; panel < npanels; panel += gridDim.x) {
+    const int i0 = panel * W;
+    if (AAO_FFT_PREFETCH) prefetch_spec<NK, W, T>(spec, n, n_pad, (panel + gridDim.x) * W);
+    for (int idx = threadIdx.x; idx < NK * C; idx += T) {
+      const int k = idx / C, c = idx - k * C;
+      const int i = i0 + 2 * c;
+      const cx<R> *src = spec + (size_t)k * n_pad + i;
+      cx<R> A = mk((R)0, (R)0), B = mk((R)0, (R)0);
+      if (i < n) A = src[0];
+      if (i + 1 < n) B = src[1];
+      if (k == 0 || 2 * k == L) { A.im = (R)0; B.im = (R)0; }
+      // Z = A + i B for the pair of real outputs; Hermitian extension for L-k
+      sm[phys<C>(k, c)] = mk(A.re - B.im, A.im + B.re);
+      if (k > 0 && 2 * k < L) sm[phys<C>(L - k, c)] = mk(A.re + B.im, B.re - A.im);
+    }
+    __syncthreads();
     transform<R, L, C, +1, T>(sm, twp);
     const R *smr = reinterpret_cast<const R *>(smraw);
 #pragma unroll 8
@@ -375,41 +413,7 @@ k_fft_inverse(const cx<R> *__restrict__ spec, double *__restrict__ y, int n, int
       const int t = idx / W, w = idx - t * W, i = i0 + w;
       if (i < n) y[(size_t)t * n + i] = to_double<R>(scale * smr[2 * phys<C>(t, w >> 1) + (w & 1)]);
     }
-    return;
-  }
-
-  constexpr int RL = (PL::NP <= 1) ? (L < 1 ? 1 : L) : 16;   // radix of the last pass
-  int Ns = 1;
-  if constexpr (PL::NP > 1) {
-    pass<R, L, C, PL::R1, +1, T>(sm, 1, twp);
-    Ns = PL::R1;
-#pragma unroll
-    for (int p = 1; p < PL::NP - 1; p++) {
-      pass<R, L, C, 16, +1, T>(sm, Ns, twp);
-      Ns *= 16;
-    }
-  }
-  constexpr int NB = E / RL;
-#pragma unroll
-  for (int q = 0; q < NB; q++) {
-    const int b = threadIdx.x + q * T;
-    const int c = b % C, j = b / C;   // j < L / RL = Ns
-    cx<R> v[RL];
-#pragma unroll
-    for (int r = 0; r < RL; r++) v[r] = sm[phys<C>(j + r * (L / RL), c)];
-    if (Ns > 1) {
-      const int step = j * (L / (Ns * RL));
-#pragma unroll
-      for (int r = 1; r < RL; r++) v[r] = twiddle<R, +1>(v[r], twp[step * r]);
-    }
-    dft<R, +1, RL>(v);
-    const int i = i0 + 2 * c;
-#pragma unroll
-    for (int r = 0; r < RL; r++) {
-      const size_t o = (size_t)(j + r * Ns) * n + i;
-      if (i < n) y[o] = to_double<R>(scale * v[r].re);
-      if (i + 1 < n) y[o + 1] = to_double<R>(scale * v[r].im);
-    }
+    __syncthreads();   // the work buffer is reused by the next panel
   }
 }
 

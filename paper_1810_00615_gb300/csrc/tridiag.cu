@@ -186,6 +186,204 @@ k_tridiag(cx<R> *__restrict__ spec, int n, int64_t n_pad, const TriTab<R, CH> *_
   }
 }
 
+// Recursive substructuring (see RecTab).  Level 0 lives in registers as in
+// k_tridiag; the higher levels are small and live in shared memory, one
+// padding slot per CH values so that the chunk-strided accesses of the
+// threads fall in distinct banks.
+template <int CH>
+__device__ __forceinline__ int rpos(int e) { return e + e / CH; }
+
+template <typename R, int CH>
+__global__ void __launch_bounds__(1024)
+k_tridiag_rec(cx<R> *__restrict__ spec, int n, int64_t n_pad,
+              const RecTab<R, CH> *__restrict__ tabs, int conj_sym, int levels, int4 lsz_lo,
+              int2 lsz_hi) {
+  const int k = blockIdx.x;
+  const int p = threadIdx.x;
+  const int P = blockDim.x;
+  const int M = P - 1;
+  const int lsz[kRecLevels] = {lsz_lo.x, lsz_lo.y, lsz_lo.z, lsz_lo.w, lsz_hi.x, lsz_hi.y};
+  __shared__ cx<R> s_invp[kRecLevels][CH], s_bp[kRecLevels][CH], s_fc[kRecLevels][CH];
+  __shared__ cx<R> s_e[kRecLevels];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  // level buffers B_1..B_{levels-1}, then the staged row
+  cx<R> *B[kRecLevels];
+  size_t off = 0;
+  for (int l = 1; l < levels; l++) {
+    B[l] = reinterpret_cast<cx<R> *>(smraw) + off;
+    off += (size_t)rpos<CH>(lsz[l]) + 1;
+  }
+  cx<R> *s_first = reinterpret_cast<cx<R> *>(smraw) + off;   // [P]
+  off += (size_t)P;
+  float4 *s_row = reinterpret_cast<float4 *>(smraw + ((off * sizeof(cx<R>) + 15) & ~(size_t)15));
+  constexpr int EPC = 16 / sizeof(cx<R>);
+  const int nchunks = (P * CH) / EPC;
+
+  const RecTab<R, CH> *tb = tabs + k;
+  for (int i = p; i < levels * CH; i += P) {
+    const int l = i / CH, j = i - l * CH;
+    s_invp[l][j] = ld_tab(tb->invp[l][j], conj_sym);
+    s_bp[l][j] = ld_tab(tb->bp[l][j], conj_sym);
+    s_fc[l][j] = ld_tab(tb->fc[l][j], conj_sym);
+  }
+  if (p < levels) s_e[p] = ld_tab(tb->e[p], conj_sym);
+
+  cx<R> *row = spec + (size_t)k * n_pad;
+  const int base = p * CH;
+  cx<R> v[CH];
+  {
+    const float4 *g = reinterpret_cast<const float4 *>(row);
+    for (int q = p; q < nchunks; q += P) s_row[swz(q)] = g[q];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < CH / EPC; j++) {
+      const float4 f = s_row[swz(p * (CH / EPC) + j)];
+      const cx<R> *z = reinterpret_cast<const cx<R> *>(&f);
+#pragma unroll
+      for (int u = 0; u < EPC; u++) v[j * EPC + u] = (base + j * EPC + u < n) ? z[u] : mk((R)0, (R)0);
+    }
+  }
+  __syncthreads();
+
+  // level 0: local Dirichlet solve of the chunk (CH-1 unknowns)
+  const cx<R> e0 = s_e[0];
+  v[0] = v[0] * s_invp[0][0];
+#pragma unroll
+  for (int i = 1; i < CH - 1; i++) v[i] = cfnms(v[i], e0, v[i - 1]) * s_invp[0][i];
+#pragma unroll
+  for (int i = CH - 3; i >= 0; i--) v[i] = cfnms(v[i], s_bp[0][i], v[i + 1]);
+
+  if (levels > 1) {
+    // separator right-hand sides of level 1: needs the first local value of
+    // the next chunk
+    cx<R> *B1 = B[1];
+    s_first[p] = v[0];
+    __syncthreads();
+    if (p < M) B1[rpos<CH>(p)] = cfnms(v[CH - 1], e0, v[CH - 2] + s_first[p + 1]);
+    __syncthreads();
+
+    // upward sweep over the chunked levels 1 .. levels-2
+    for (int l = 1; l < levels - 1; l++) {
+      const int nl = lsz[l];
+      const int Pl = (nl + 1) / CH, Ml = Pl - 1;
+      cx<R> *Bl = B[l];
+      const cx<R> el = s_e[l];
+      if (p < Pl) {
+        cx<R> w[CH];
+#pragma unroll
+        for (int i = 0; i < CH; i++) w[i] = (p * CH + i < nl) ? Bl[rpos<CH>(p * CH + i)] : mk((R)0, (R)0);
+        w[0] = w[0] * s_invp[l][0];
+#pragma unroll
+        for (int i = 1; i < CH - 1; i++) w[i] = cfnms(w[i], el, w[i - 1]) * s_invp[l][i];
+#pragma unroll
+        for (int i = CH - 3; i >= 0; i--) w[i] = cfnms(w[i], s_bp[l][i], w[i + 1]);
+#pragma unroll
+        for (int i = 0; i < CH - 1; i++) Bl[rpos<CH>(p * CH + i)] = w[i];
+      }
+      __syncthreads();
+      if (p < Ml) {
+        const cx<R> sep = Bl[rpos<CH>(p * CH + CH - 1)];
+        const cx<R> lastl = Bl[rpos<CH>(p * CH + CH - 2)];
+        const cx<R> firstr = Bl[rpos<CH>((p + 1) * CH)];
+        B[l + 1][rpos<CH>(p)] = cfnms(sep, el, lastl + firstr);
+      }
+      __syncthreads();
+    }
+
+    // last level: one Thomas sweep over lsz[L] <= CH-1 unknowns
+    {
+      const int L = levels - 1;
+      const int nl = lsz[L];
+      cx<R> *Bl = B[L];
+      if (p == 0) {
+        const cx<R> el = s_e[L];
+        cx<R> w[CH];
+#pragma unroll
+        for (int i = 0; i < CH; i++) w[i] = (i < nl) ? Bl[rpos<CH>(i)] : mk((R)0, (R)0);
+        w[0] = w[0] * s_invp[L][0];
+#pragma unroll
+        for (int i = 1; i < CH; i++)
+          if (i < nl) w[i] = cfnms(w[i], el, w[i - 1]) * s_invp[L][i];
+#pragma unroll
+        for (int i = CH - 2; i >= 0; i--)
+          if (i < nl - 1) w[i] = cfnms(w[i], s_bp[L][i], w[i + 1]);
+#pragma unroll
+        for (int i = 0; i < CH; i++)
+          if (i < nl) Bl[rpos<CH>(i)] = w[i];
+      }
+      __syncthreads();
+    }
+
+    // downward sweep: correct the chunked levels with their separators
+    for (int l = levels - 2; l >= 1; l--) {
+      const int nl = lsz[l];
+      const int Pl = (nl + 1) / CH, Ml = Pl - 1;
+      cx<R> *Bl = B[l];
+      const cx<R> *Bu = B[l + 1];
+      if (p < Pl) {
+        const cx<R> sl = (p > 0) ? Bu[rpos<CH>(p - 1)] : mk((R)0, (R)0);
+        const cx<R> sr = (p < Ml) ? Bu[rpos<CH>(p)] : mk((R)0, (R)0);
+#pragma unroll
+        for (int i = 0; i < CH - 1; i++) {
+          const int pos = rpos<CH>(p * CH + i);
+          Bl[pos] = cfma(cfma(Bl[pos], sl, s_fc[l][i]), sr, s_fc[l][CH - 2 - i]);
+        }
+        if (p < Ml) Bl[rpos<CH>(p * CH + CH - 1)] = sr;
+      }
+      __syncthreads();
+    }
+
+    // level 0 correction
+    const cx<R> sl = (p > 0) ? B1[rpos<CH>(p - 1)] : mk((R)0, (R)0);
+    const cx<R> sr = (p < M) ? B1[rpos<CH>(p)] : mk((R)0, (R)0);
+#pragma unroll
+    for (int i = 0; i < CH - 1; i++) v[i] = cfma(cfma(v[i], sl, s_fc[0][i]), sr, s_fc[0][CH - 2 - i]);
+    v[CH - 1] = sr;
+  }
+
+  // write back through the staging buffer
+#pragma unroll
+  for (int j = 0; j < CH / EPC; j++) {
+    float4 f;
+    cx<R> *z = reinterpret_cast<cx<R> *>(&f);
+#pragma unroll
+    for (int u = 0; u < EPC; u++) z[u] = v[j * EPC + u];
+    s_row[swz(p * (CH / EPC) + j)] = f;
+  }
+  __syncthreads();
+  float4 *g = reinterpret_cast<float4 *>(row);
+  const int nlive = (n + EPC - 1) / EPC;
+  for (int q = p; q < nlive; q += P) {
+    if ((q + 1) * EPC <= n) {
+      g[q] = s_row[swz(q)];
+    } else {
+      const float4 f = s_row[swz(q)];
+      const cx<R> *z = reinterpret_cast<const cx<R> *>(&f);
+      for (int u = 0; q * EPC + u < n; u++) row[q * EPC + u] = z[u];
+    }
+  }
+}
+
+template <typename R, int CH>
+static cudaError_t run_tridiag_rec(const Ctx &c, void *spec, const void *tab, int P, int conj,
+                                   int levels, const int *lsz, cudaStream_t s) {
+  size_t off = 0;
+  for (int l = 1; l < levels; l++) off += (size_t)(lsz[l] + lsz[l] / CH) + 1;
+  off += (size_t)P;
+  const size_t smem = ((off * sizeof(cx<R>) + 15) & ~(size_t)15) + (size_t)P * CH * sizeof(cx<R>);
+  auto kern = k_tridiag_rec<R, CH>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) { cudaGetLastError(); return e; }
+  const int4 lo = make_int4(lsz[0], lsz[1], lsz[2], lsz[3]);
+  const int2 hi = make_int2(lsz[4], lsz[5]);
+  kern<<<(unsigned)c.nk, P, smem, s>>>(static_cast<cx<R> *>(spec), (int)c.n, c.n_pad,
+                                       static_cast<const RecTab<R, CH> *>(tab), conj, levels,
+                                       lo, hi);
+  note_launch();
+  return cudaGetLastError();
+}
+
 template <typename R, int CH>
 static cudaError_t run_tridiag(const Ctx &c, void *spec, const void *tab, int P, int conj,
                                cudaStream_t s) {
@@ -197,7 +395,7 @@ static cudaError_t run_tridiag(const Ctx &c, void *spec, const void *tab, int P,
   auto kern = stage ? k_tridiag<R, CH, true> : k_tridiag<R, CH, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) { cudaGetLastError(); return e; }
   kern<<<(unsigned)c.nk, P, smem, s>>>(static_cast<cx<R> *>(spec), (int)c.n, c.n_pad,
                                        static_cast<const TriTab<R, CH> *>(tab), conj);
   note_launch();
@@ -205,6 +403,12 @@ static cudaError_t run_tridiag(const Ctx &c, void *spec, const void *tab, int P,
 }
 
 cudaError_t launch_tridiag(const Ctx &c, void *spec, int prec, int transpose, cudaStream_t s) {
+  if (prec == AAO_PREC_FP32 && c.lev32 > 0 && c.ch32 == 16)
+    return run_tridiag_rec<float, 16>(c, spec, c.rec32, c.P32, transpose, c.lev32, c.lsz32, s);
+  if (prec == AAO_PREC_FP64 && c.lev64 > 0 && c.ch64 == 8)
+    return run_tridiag_rec<double, 8>(c, spec, c.rec64, c.P64, transpose, c.lev64, c.lsz64, s);
+  if (prec == AAO_PREC_FP64 && c.lev64 > 0 && c.ch64 == 16)
+    return run_tridiag_rec<double, 16>(c, spec, c.rec64, c.P64, transpose, c.lev64, c.lsz64, s);
   if (prec == AAO_PREC_FP32) {
     if (c.ch32 == 16) return run_tridiag<float, 16>(c, spec, c.tab32, c.P32, transpose, s);
     return cudaErrorInvalidValue;

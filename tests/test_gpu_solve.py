@@ -76,14 +76,16 @@ def test_heat_n4095_ell4096(prec):
 
 def test_wave_bd2_n8191_ell2048():
     """BD2 with 16-mode displacement and velocity, FP32 preconditioner,
-    FGMRES(40), 1e-10."""
+    FGMRES(40).  The wave operator is far less damped than the heat one, so
+    a residual of 1e-10 leaves a solution error near 1e-8; the solve is run
+    to 2e-11 so that both bars (residual <= 1e-10, error <= 1e-8) hold."""
     torch = need_gpu()
     from paper_1810_00615_gb300 import AllAtOnce
     n, ell = 8191, 2048
     S = oracle_system("wave_bd2", n, ell)
     u0, v0 = syn.wave_initial(n, modes=16)
     a = AllAtOnce(n, ell, 1.0 / ell, equation="wave_bd2", precision="fp32", restart=40)
-    x, info = a.solve(a.build_rhs(to_dev(torch, u0), to_dev(torch, v0)), restart=40, rtol=1e-10)
+    x, info = a.solve(a.build_rhs(to_dev(torch, u0), to_dev(torch, v0)), restart=40, rtol=2e-11)
     assert info["converged"], info
     _check(S, system.rhs_bd2(S, u0, v0), to_host(x))
 
