@@ -207,6 +207,30 @@ int aao_profile_read(aao_ctx *ctx, double *ms, int64_t *launches, int reset);
 /* Total kernel launches made through this context since it was created. */
 int64_t aao_kernel_launches(const aao_ctx *ctx);
 
+/* y = P^{-1} x (or P^{-T} x) exactly like aao_precond_apply, but without a
+ * caller workspace: the frequency-domain scratch is a fixed array of 32 MiB
+ * inside the library (static device memory, reserved on every device that
+ * loads the library until the process exits), so this call allocates no
+ * memory at all.  It is for callers that cannot allocate device memory at the
+ * point where they apply the preconditioner -- code being recorded into a
+ * CUDA graph by stream capture, plug-ins that must not touch the host
+ * program's allocator or memory pool, or runtimes that forbid allocation
+ * after start-up.  The paper has no counterpart; it is a packaging choice.
+ *   - Limit: (ell/2 + 1) * round_up(n, 16) * 8 bytes (FP32 preconditioner) or
+ *     * 16 bytes (FP64) must fit in 32 MiB, e.g. n = 4095 with ell <= 1024 in
+ *     FP32; larger systems get AAO_EINVAL and aao_last_error says why.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls on a device share the one array and leave their spectrum in
+ *     it.  Nothing needs to start at zero (every call overwrites what it
+ *     reads), but two calls whose kernels overlap on the GPU (different
+ *     streams, or different host threads) race on the array: serialise them.
+ *   - The context itself still comes from aao_create, which allocates its
+ *     constant tables once; no workspace is needed for this call. */
+int aao_precond_apply_static(aao_ctx *ctx, const double *x, double *y, int transpose,
+                             void *stream);
+
 /* Text for a status code, and the last CUDA error seen by ctx ("" if none). */
 const char *aao_strerror(int status);
 const char *aao_last_error(const aao_ctx *ctx);

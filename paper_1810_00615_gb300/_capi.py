@@ -59,6 +59,8 @@ SIGNATURES = {
     "aao_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                    C.c_int]),
     "aao_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "aao_precond_apply_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                           C.c_void_p]),
     "aao_strerror": (C.c_char_p, [C.c_int]),
     "aao_last_error": (C.c_char_p, [C.c_void_p]),
 }
