@@ -164,6 +164,112 @@ def _blas_threads():
         return _cpu_cores()
 
 
+def _traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summaries
+    (a line 'dram_bytes_per_launch: <kernel> <bytes>'), else None."""
+    import glob
+    import re
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(f) as fh:
+            for line in fh:
+                m = re.match(r"dram_bytes_per_launch:\s*(\S+)\s+([0-9.eE+]+)", line.strip())
+                if m and m.group(1) == kernel:
+                    return float(m.group(2))
+    return None
+
+
+def _timed(fn, reps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(reps):
+        fn(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extra_rows(device, hbm_peak):
+    """The other rows of the hot path, each timed with CUDA events: the FP64
+    preconditioner apply, Neumann applies and solves on the perturbed grid,
+    the BD2 wave solve (n = 8191, ell = 2048) and the adjoint pass
+    (n = 16383, ell = 1024)."""
+    import torch
+    import synthetic as syn
+    from paper_1810_00615_gb300 import AllAtOnce
+    stream = torch.cuda.current_stream()
+    rows = {}
+    n, ell = N_SPACE, ELL
+    Nel = n * ell
+    spec = 8 * n * (ell // 2 + 1)
+    a = AllAtOnce(n, ell, 1.0 / ell, precision="fp64", restart=1, device=device)
+    x = [torch.randn(ell, n, dtype=torch.float64, device=device) for _ in range(2)]
+    y = [torch.empty_like(x[0]) for _ in range(2)]
+    ms = _timed(lambda i: a.precond_apply(x[i % 2], out=y[i % 2]), 5, stream)
+    b64 = 8 * Nel + 2 * spec + 2 * (2 * spec) + 2 * spec + 8 * Nel
+    rows["precond_apply_fp64"] = {"us": round(1e3 * ms, 1), "GB_s": round(b64 / ms / 1e6, 1),
+                                  "bytes": b64, "note": "FP64 pipe bound (FFT and solves in FP64)"}
+    # Neumann on the perturbed grid (delta = 0.5)
+    a.set_precision("fp32")
+    a.set_steps(syn.time_steps(ell, 0.5, syn.rng(3)))
+    for terms in (2, 3):
+        ms = _timed(lambda i: a.neumann_apply(x[i % 2], terms, out=y[i % 2]), 10, stream)
+        bts = 32 * Nel + (terms - 1) * 40 * Nel
+        rows[f"neumann_apply_terms{terms}"] = {"us": round(1e3 * ms, 1),
+                                              "GB_s": round(bts / ms / 1e6, 1),
+                                              "frac_of_hbm": round(bts / ms / 1e6 / hbm_peak, 3)}
+    del a, x, y
+    torch.cuda.empty_cache()
+    sv = AllAtOnce(n, ell, 1.0 / ell, precision="fp32", restart=RESTART, device=device)
+    sv.set_steps(syn.time_steps(ell, 0.5, syn.rng(3)))
+    bb = sv.build_rhs(torch.from_numpy(syn.heat_initial(n)).to(device))
+    for pc in (1, 2, 3):
+        sv.solve(bb, restart=RESTART, rtol=RTOL, precond=pc)
+        info = {}
+        ms = _timed(lambda i: info.update(sv.solve(bb, restart=RESTART, rtol=RTOL,
+                                                   precond=pc)[1]), 3, stream)
+        rows[f"solve_steps_delta0.5_precond{pc}"] = {"ms": round(ms, 3), "iters": info["iters"],
+                                                     "relres": info["relres_true"]}
+    del sv, bb
+    torch.cuda.empty_cache()
+    # BD2 wave, n = 8191, ell = 2048, 16-mode displacement and velocity
+    nw, lw = 8191, 2048
+    sw = AllAtOnce(nw, lw, 1.0 / lw, equation="wave_bd2", precision="fp32", restart=40,
+                   device=device)
+    u0, v0 = syn.wave_initial(nw, modes=16)
+    bw = sw.build_rhs(torch.from_numpy(u0).to(device), torch.from_numpy(v0).to(device))
+    sw.solve(bw, restart=40, rtol=RTOL)
+    info = {}
+    ms = _timed(lambda i: info.update(sw.solve(bw, restart=40, rtol=RTOL)[1]), 3, stream)
+    rows["wave_bd2_n8191_ell2048_solve"] = {"ms": round(ms, 3), "iters": info["iters"],
+                                            "relres": info["relres_true"]}
+    del sw, bw
+    torch.cuda.empty_cache()
+    # adjoint pass, n = 16383, ell = 1024: forward solve, adjoint solve, gradients
+    na, la = 16383, 1024
+    sa = AllAtOnce(na, la, 1.0 / la, precision="fp32", restart=RESTART, device=device)
+    g = syn.rng(2024)
+    u0a = torch.from_numpy(syn.sine_l2_projection(syn.sine_coefficients(8, g), na)).to(device)
+    obs = torch.randn(la, na, dtype=torch.float64, device=device) * 1e-3
+    res = {}
+
+    def adj(_):
+        U, i1 = sa.solve(sa.build_rhs(u0a), restart=RESTART, rtol=5e-10)
+        lam, i2 = sa.adjoint_solve(U - obs, restart=RESTART, rtol=5e-9)
+        gu, gk = sa.adjoint_grads(lam, U)
+        res.update(fwd=i1["iters"], adj=i2["iters"])
+    adj(0)
+    ms = _timed(adj, 2, stream)
+    rows["adjoint_n16383_ell1024_pass"] = {"ms": round(ms, 3), "fwd_iters": res["fwd"],
+                                           "adj_iters": res["adj"],
+                                           "note": "forward solve to 5e-10, adjoint solve to "
+                                                   "5e-9 (FP64 floors 2.7e-10 / 2.5e-9)"}
+    del sa
+    torch.cuda.empty_cache()
+    return rows
+
+
 # ------------------------------------------------------------ reference arm
 def run_reference(args):
     world, rank, _ = _dist_env()
@@ -243,6 +349,7 @@ def run_gpu(args):
     _barrier(dist_on)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed_region")    # ncu --nvtx --nvtx-include timed_region/
     for k in range(args.steps):
         flush.fill_(float(k))                      # L2 flush outside the step's events
         ev[k][0].record(stream)
@@ -250,6 +357,7 @@ def run_gpu(args):
         ev[k][1].record(stream)
         infos.append(info)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     _barrier(dist_on)
     wall = time.perf_counter() - wall0
     launches = solver.kernel_launches() - launches0
@@ -330,6 +438,7 @@ def run_gpu(args):
     total_prof = sum(v[0] for v in prof.values()) or 1.0
     shares = {k: round(v[0] / total_prof, 3) for k, v in prof.items()}
     dom = max(prof, key=lambda k: prof[k][0])
+    sm_mhz = clk.get("sm_mhz") or 2070.0
 
     if dom in per_kernel:
         pk = per_kernel[dom]
@@ -337,19 +446,29 @@ def run_gpu(args):
                     "unit": "GB/s", "frac": pk["frac"], "traffic": None,
                     "peak_kind": peak_kind}
     else:
-        # FP64 kernels of the outer loop: report bytes against HBM and FP64 ops
-        # against the FP64 issue rate (2 per clock per SM, 152 SMs)
+        # FP64 kernels of the outer loop are bound by the FP64 pipe: 2 FP64
+        # instructions per clock per SM (measured), 152 SMs.  Algorithmic
+        # work per element of the fused matvec A z - v: 6 FP64 instructions
+        # (2 adds, 1 mul, 3 fma) = 9 flops counting an fma as 2.
         t_ms, nl = prof[dom]
         avg_s = t_ms / max(nl, 1) / 1e3
-        sm_mhz = clk.get("sm_mhz") or 2070.0
-        fp64_peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12      # TFLOP/s (FMA = 2 flops)
-        flops_per_launch = {"matvec": 14 * Nel}.get(dom)
-        roofline = {"bound": "alu", "kernel": dom,
-                    "achieved": (flops_per_launch / avg_s / 1e12) if flops_per_launch else None,
-                    "peak": round(fp64_peak, 3), "unit": "TFLOP/s",
-                    "frac": (flops_per_launch / avg_s / 1e12 / fp64_peak)
-                    if flops_per_launch else None, "traffic": None,
-                    "note": "FP64 pipe bound; peak = 152 SMs x 2 DFMA/clk x sampled SM clock"}
+        fp64_peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12       # TFLOP/s with every op an FMA
+        inst_peak = 152 * 2 * sm_mhz * 1e6                   # FP64 instructions / s
+        per_elt = {"matvec": (9, 6)}.get(dom)
+        if per_elt:
+            fl, ins = per_elt
+            achieved = fl * Nel / avg_s / 1e12
+            roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4),
+                        "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                        "frac": round(achieved / fp64_peak, 4), "traffic": _traffic(dom),
+                        "fp64_issue_frac": round(ins * Nel / avg_s / inst_peak, 4),
+                        "note": "FP64 pipe bound; peak = 152 SMs x 2 FP64 FMA/clk x 2 flops x "
+                                "sampled SM clock; this kernel's mix (3 of 6 FP64 "
+                                "instructions are FMAs) caps frac at 0.75"}
+        else:
+            roofline = {"bound": "alu", "kernel": dom, "achieved": None,
+                        "peak": round(fp64_peak, 4), "unit": "TFLOP/s", "frac": None,
+                        "traffic": None}
 
     # ---- end to end through the C ABI with host buffers (u0 in, U out)
     u0_h = torch.from_numpy(u0).pin_memory()
@@ -365,6 +484,13 @@ def run_gpu(args):
         torch.cuda.synchronize()
         e2e.append(time.perf_counter() - t0)
     e2e_v = _max_over_ranks(float(np.mean(e2e)), dist_on, device)
+
+    # ---- the other rows of the path
+    extra = None
+    if not args.no_extra:
+        del solver
+        torch.cuda.empty_cache()
+        extra = extra_rows(device, hbm_peak)
 
     # ---- CPU oracle on the host cores (rank 0, N = 1 only)
     cpu = None
@@ -396,6 +522,7 @@ def run_gpu(args):
             "e2e": {"value": e2e_v, "unit": "s", "h2d_bytes_per_step": 8 * N_SPACE,
                     "d2h_bytes_per_step": 8 * Nel},
             "gpu_launches": launches, "wall_s": wall, "clocks": clk,
+            "rows": extra,
         }
         print(json.dumps(line), flush=True)
     if dist_on:
@@ -411,6 +538,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other rows of the path")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

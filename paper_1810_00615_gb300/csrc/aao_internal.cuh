@@ -80,6 +80,89 @@ __device__ __forceinline__ double to_f64(float f) {
   return __hiloint2double((int)hi, (int)(u << 29));
 }
 
+// ------------------------------------------------- L2 residency hints
+// The preconditioner's half spectrum (67 MB at n = 4095, ell = 4096) is
+// written by the forward FFT, read and rewritten by the tridiagonal solves
+// and read by the inverse FFT; the block vectors stream through once.
+// Marking the streams evict-first and the spectrum evict-last keeps the
+// spectrum in the 126 MB L2 between the three kernels.
+#ifndef AAO_L2_HINTS
+#define AAO_L2_HINTS 1
+#endif
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+  unsigned long long p = 0;
+#if AAO_L2_HINTS
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+#endif
+  return p;
+}
+__device__ __forceinline__ unsigned long long l2_evict_last() {
+  unsigned long long p = 0;
+#if AAO_L2_HINTS
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+#endif
+  return p;
+}
+__device__ __forceinline__ double ld_hint(const double *p, unsigned long long pol) {
+#if AAO_L2_HINTS
+  double v;
+  asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+#else
+  return __ldg(p);
+#endif
+}
+__device__ __forceinline__ float4 ld_hint4(const float4 *p, unsigned long long pol) {
+#if AAO_L2_HINTS
+  float4 v;
+  asm("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol));
+  return v;
+#else
+  return *p;
+#endif
+}
+__device__ __forceinline__ void st_hint4(float4 *p, float4 v, unsigned long long pol) {
+#if AAO_L2_HINTS
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
+               ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol) : "memory");
+#else
+  *p = v;
+#endif
+}
+template <typename R>
+__device__ __forceinline__ void st_hint(cx<R> *p, cx<R> v, unsigned long long pol) {
+#if AAO_L2_HINTS
+  if constexpr (sizeof(R) == 4) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;"
+                 ::"l"(p), "f"((float)v.re), "f"((float)v.im), "l"(pol) : "memory");
+  } else {
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;"
+                 ::"l"(p), "d"((double)v.re), "d"((double)v.im), "l"(pol) : "memory");
+  }
+#else
+  *p = v;
+#endif
+}
+template <typename R>
+__device__ __forceinline__ cx<R> ld_hintc(const cx<R> *p, unsigned long long pol) {
+#if AAO_L2_HINTS
+  cx<R> v;
+  if constexpr (sizeof(R) == 4) {
+    float a, b;
+    asm("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(a), "=f"(b) : "l"(p), "l"(pol));
+    v.re = a; v.im = b;
+  } else {
+    double a, b;
+    asm("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(a), "=d"(b) : "l"(p), "l"(pol));
+    v.re = a; v.im = b;
+  }
+  return v;
+#else
+  return *p;
+#endif
+}
+
 template <typename R> __device__ __forceinline__ R from_f64(double x);
 template <> __device__ __forceinline__ float from_f64<float>(double x) { return to_f32(x); }
 template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
@@ -145,6 +228,8 @@ struct Ctx {
   void *rec32 = nullptr;   // RecTab<float, ch32>[nk] when the recursive form applies
   void *rec64 = nullptr;   // RecTab<double, ch64>[nk]
   int lev32 = 0, lev64 = 0;             // levels of the recursive form (0: not applicable)
+  int clu32 = 1, clu64 = 1;             // CTAs per row (cluster size) for rows beyond one CTA
+  int cta32 = 0, cta64 = 0;             // threads per CTA in the cluster form
   int lsz32[kRecLevels] = {0}, lsz64[kRecLevels] = {0};   // unknowns per level
   cx<float> *tw32 = nullptr;      // exp(-2 pi i m/ell), m < ell
   cx<double> *tw64 = nullptr;

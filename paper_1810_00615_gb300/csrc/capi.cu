@@ -21,7 +21,8 @@ namespace {
 
 constexpr int kMaxRestart = 128;
 constexpr int64_t kMaxEll = 4096;
-constexpr int64_t kMaxN = 16383;
+constexpr int64_t kMaxN = 65535;
+constexpr int64_t kMaxNAnyShape = 16383;   // beyond this the row must split into clusters
 constexpr size_t kAlign = 256;
 constexpr int kPartials = 152 * 8 * 16;      // doubles for block partials
 constexpr int kSmall = 1024;                 // doubles for device-side small results
@@ -187,7 +188,6 @@ int rec_levels(int64_t n, int CH, int *lsz) {
     m = (m + 1) / CH - 1;
   }
   if (levels < 2) return 0;   // a single chunk: the plain kernel is as good
-  if ((n + 1) / CH > 1024) return 0;
   return levels;
 }
 
@@ -195,6 +195,26 @@ int rec_levels(int64_t n, int CH, int *lsz) {
 bool rec_fits(int64_t n, int CH, size_t elem) {
   return (size_t)((n + 1) / CH) * CH * elem <= 160 * 1024;
 }
+
+// Form of the per-frequency solve: one CTA per row (recursive form when the
+// staged row fits in shared memory), or a cluster of S CTAs of `tpb`
+// threads when the row is longer than one CTA can hold.
+void choose_form(int64_t n, int CH, size_t elem, int tpb, int &lev, int *lsz, int &clu, int &cta) {
+  clu = 1;
+  cta = 0;
+  lev = rec_levels(n, CH, lsz);
+  if (lev == 0) return;
+  const int64_t P = (n + 1) / CH;
+  if (P <= 1024 && rec_fits(n, CH, elem)) return;
+  if (P % tpb == 0 && P / tpb >= 2 && P / tpb <= 8) {
+    clu = (int)(P / tpb);
+    cta = tpb;
+    return;
+  }
+  lev = 0;
+}
+
+
 
 // Chunks of a row of n unknowns with chunk length CH (CH-1 unknowns + one
 // separator); returns the chunk count P and the last chunk's size cl.
@@ -293,13 +313,13 @@ int refresh_constants(Ctx &c) {
     }
   }
   // recursive tables where the row structure allows them
-  c.lev32 = rec_fits(c.n, c.ch32, sizeof(cx<float>)) ? rec_levels(c.n, c.ch32, c.lsz32) : 0;
+  choose_form(c.n, c.ch32, sizeof(cx<float>), 1024, c.lev32, c.lsz32, c.clu32, c.cta32);
   if (c.lev32 > 0) {
     std::vector<aao::RecTab<float, 16>> r32;
     build_rec_tables<float, 16>(c, c.lev32, r32);
     AAO_CK(c, upload(&c.rec32, r32));
   }
-  c.lev64 = rec_fits(c.n, c.ch64, sizeof(cx<double>)) ? rec_levels(c.n, c.ch64, c.lsz64) : 0;
+  choose_form(c.n, c.ch64, sizeof(cx<double>), 512, c.lev64, c.lsz64, c.clu64, c.cta64);
   if (c.lev64 > 0) {
     if (c.ch64 == 8) {
       std::vector<aao::RecTab<double, 8>> r64;
@@ -637,7 +657,17 @@ int aao_create(int64_t n, int64_t ell, double tau, int equation, aao_ctx **out) 
   c.ch32 = 16;
   c.ch64 = (n <= 8191) ? 8 : 16;
   cudaGetDevice(&c.device);
-  int st = refresh_constants(c);
+  int st = AAO_OK;
+  if (n > kMaxNAnyShape) {
+    // rows longer than one CTA need the recursive cluster form in both precisions
+    int l1[aao::kRecLevels], l2[aao::kRecLevels], lv, cl, ct;
+    choose_form(n, c.ch32, sizeof(cx<float>), 1024, lv, l1, cl, ct);
+    const bool ok32 = lv > 0 && cl > 1;
+    choose_form(n, c.ch64, sizeof(cx<double>), 512, lv, l2, cl, ct);
+    const bool ok64 = lv > 0 && cl > 1;
+    if (!ok32 || !ok64) st = AAO_EUNSUPPORTED;
+  }
+  if (st == AAO_OK) st = refresh_constants(c);
   if (st == AAO_OK) {
     std::vector<cx<float>> t32((size_t)ell);
     std::vector<cx<double>> t64((size_t)ell);

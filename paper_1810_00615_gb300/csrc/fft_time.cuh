@@ -242,7 +242,8 @@ template <typename R, int L> struct Shape {
 // all of its loads in flight at once; later passes go through shared memory.
 template <typename R, int L, bool NEUMANN>
 __device__ __forceinline__ R load_real(const double *__restrict__ x, const double *__restrict__ y,
-                                       const R *__restrict__ sigk, int n, int t, int i) {
+                                       const R *__restrict__ sigk, int n, int t, int i,
+                                       unsigned long long pol = 0) {
   if (i >= n) return (R)0;
   const size_t o = (size_t)t * n + i;
   if constexpr (NEUMANN) {
@@ -251,7 +252,7 @@ __device__ __forceinline__ R load_real(const double *__restrict__ x, const doubl
     const R yr = (i + 1 < n) ? from_f64<R>(__ldg(&y[o + 1])) : (R)0;
     return from_f64<R>(__ldg(&x[o])) - __ldg(&sigk[t]) * ((yc + yc) - yl - yr);
   } else {
-    return from_f64<R>(__ldg(&x[o]));
+    return from_f64<R>(ld_hint(&x[o], pol));
   }
 }
 
@@ -295,6 +296,7 @@ k_fft_forward(const double *__restrict__ x, const double *__restrict__ y,
     load_twiddles<R, L, T>(stw, tw);
     twp = stw;
   }
+  const unsigned long long pol_stream = l2_evict_first(), pol_keep = l2_evict_last();
   for (int panel = blockIdx.x; panel < npanels; panel += gridDim.x) {
     const int i0 = panel * W;
     if (AAO_FFT_PREFETCH && !NEUMANN) prefetch_rows<L, W, T>(x, n, (panel + gridDim.x) * W);
@@ -308,8 +310,8 @@ k_fft_forward(const double *__restrict__ x, const double *__restrict__ y,
 #pragma unroll
         for (int r = 0; r < R1; r++) {
           const int t = j + r * (L / R1);
-          v[q][r] = mk(load_real<R, L, NEUMANN>(x, y, sigk, n, t, i),
-                       load_real<R, L, NEUMANN>(x, y, sigk, n, t, i + 1));
+          v[q][r] = mk(load_real<R, L, NEUMANN>(x, y, sigk, n, t, i, pol_stream),
+                       load_real<R, L, NEUMANN>(x, y, sigk, n, t, i + 1, pol_stream));
         }
       }
 #pragma unroll
@@ -343,10 +345,10 @@ k_fft_forward(const double *__restrict__ x, const double *__restrict__ y,
       const int i = i0 + 2 * c;
       cx<R> *dst = spec + (size_t)k * n_pad + i;
       if (i + 1 < n) {
-        dst[0] = X;
-        dst[1] = Y;
+        st_hint(dst, X, pol_keep);
+        st_hint(dst + 1, Y, pol_keep);
       } else if (i < n) {
-        dst[0] = X;
+        st_hint(dst, X, pol_keep);
       }
     }
     __syncthreads();   // the work buffer is reused by the next panel
@@ -390,6 +392,7 @@ k_fft_inverse(const cx<R> *__restrict__ spec, double *__restrict__ y, int n, int
   }
   constexpr int NK = L / 2 + 1;
   const R scale = (R)1 / (R)L;
+  const unsigned long long pol_done = l2_evict_first();
   for (int panel = blockIdx.x; panel < npanels; panel += gridDim.x) {
     const int i0 = panel * W;
     if (AAO_FFT_PREFETCH) prefetch_spec<NK, W, T>(spec, n, n_pad, (panel + gridDim.x) * W);
@@ -398,8 +401,8 @@ k_fft_inverse(const cx<R> *__restrict__ spec, double *__restrict__ y, int n, int
       const int i = i0 + 2 * c;
       const cx<R> *src = spec + (size_t)k * n_pad + i;
       cx<R> A = mk((R)0, (R)0), B = mk((R)0, (R)0);
-      if (i < n) A = src[0];
-      if (i + 1 < n) B = src[1];
+      if (i < n) A = ld_hintc(src, pol_done);
+      if (i + 1 < n) B = ld_hintc(src + 1, pol_done);
       if (k == 0 || 2 * k == L) { A.im = (R)0; B.im = (R)0; }
       // Z = A + i B for the pair of real outputs; Hermitian extension for L-k
       sm[phys<C>(k, c)] = mk(A.re - B.im, A.im + B.re);

@@ -17,7 +17,11 @@
 //      nearly singular low frequencies (k = 0 is tau*kappa*K, the Laplacian)
 //      keep their accuracy in FP32.
 //   3. Each chunk is corrected with the two separator values around it.
+#include <cooperative_groups.h>
+
 #include "aao_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace aao {
 
@@ -230,10 +234,11 @@ k_tridiag_rec(cx<R> *__restrict__ spec, int n, int64_t n_pad,
 
   cx<R> *row = spec + (size_t)k * n_pad;
   const int base = p * CH;
+  const unsigned long long pol_keep = l2_evict_last();
   cx<R> v[CH];
   {
     const float4 *g = reinterpret_cast<const float4 *>(row);
-    for (int q = p; q < nchunks; q += P) s_row[swz(q)] = g[q];
+    for (int q = p; q < nchunks; q += P) s_row[swz(q)] = ld_hint4(&g[q], pol_keep);
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < CH / EPC; j++) {
@@ -355,13 +360,226 @@ k_tridiag_rec(cx<R> *__restrict__ spec, int n, int64_t n_pad,
   const int nlive = (n + EPC - 1) / EPC;
   for (int q = p; q < nlive; q += P) {
     if ((q + 1) * EPC <= n) {
-      g[q] = s_row[swz(q)];
+      st_hint4(&g[q], s_row[swz(q)], pol_keep);
     } else {
       const float4 f = s_row[swz(q)];
       const cx<R> *z = reinterpret_cast<const cx<R> *>(&f);
       for (int u = 0; q * EPC + u < n; u++) row[q * EPC + u] = z[u];
     }
   }
+}
+
+// Levels 1 .. levels-1 of the recursive form on shared-memory buffers:
+// B[1] holds the level-1 right-hand sides on entry and the level-1 solution
+// (the level-0 separator values) on exit.  Called by all threads of one CTA.
+template <typename R, int CH>
+__device__ __forceinline__ void rec_upper(cx<R> *const *B, const int *lsz, int levels,
+                                          const cx<R> (*s_invp)[CH], const cx<R> (*s_bp)[CH],
+                                          const cx<R> (*s_fc)[CH], const cx<R> *s_e, int p) {
+  for (int l = 1; l < levels - 1; l++) {
+    const int nl = lsz[l];
+    const int Pl = (nl + 1) / CH, Ml = Pl - 1;
+    cx<R> *Bl = B[l];
+    const cx<R> el = s_e[l];
+    for (int q = p; q < Pl; q += blockDim.x) {
+      cx<R> w[CH];
+#pragma unroll
+      for (int i = 0; i < CH; i++) w[i] = (q * CH + i < nl) ? Bl[rpos<CH>(q * CH + i)] : mk((R)0, (R)0);
+      w[0] = w[0] * s_invp[l][0];
+#pragma unroll
+      for (int i = 1; i < CH - 1; i++) w[i] = cfnms(w[i], el, w[i - 1]) * s_invp[l][i];
+#pragma unroll
+      for (int i = CH - 3; i >= 0; i--) w[i] = cfnms(w[i], s_bp[l][i], w[i + 1]);
+#pragma unroll
+      for (int i = 0; i < CH - 1; i++) Bl[rpos<CH>(q * CH + i)] = w[i];
+    }
+    __syncthreads();
+    for (int q = p; q < Ml; q += blockDim.x) {
+      const cx<R> sep = Bl[rpos<CH>(q * CH + CH - 1)];
+      const cx<R> lastl = Bl[rpos<CH>(q * CH + CH - 2)];
+      const cx<R> firstr = Bl[rpos<CH>((q + 1) * CH)];
+      B[l + 1][rpos<CH>(q)] = cfnms(sep, el, lastl + firstr);
+    }
+    __syncthreads();
+  }
+  {
+    const int L = levels - 1;
+    const int nl = lsz[L];
+    cx<R> *Bl = B[L];
+    if (p == 0) {
+      const cx<R> el = s_e[L];
+      cx<R> w[CH];
+#pragma unroll
+      for (int i = 0; i < CH; i++) w[i] = (i < nl) ? Bl[rpos<CH>(i)] : mk((R)0, (R)0);
+      w[0] = w[0] * s_invp[L][0];
+#pragma unroll
+      for (int i = 1; i < CH; i++)
+        if (i < nl) w[i] = cfnms(w[i], el, w[i - 1]) * s_invp[L][i];
+#pragma unroll
+      for (int i = CH - 2; i >= 0; i--)
+        if (i < nl - 1) w[i] = cfnms(w[i], s_bp[L][i], w[i + 1]);
+#pragma unroll
+      for (int i = 0; i < CH; i++)
+        if (i < nl) Bl[rpos<CH>(i)] = w[i];
+    }
+    __syncthreads();
+  }
+  for (int l = levels - 2; l >= 1; l--) {
+    const int nl = lsz[l];
+    const int Pl = (nl + 1) / CH, Ml = Pl - 1;
+    cx<R> *Bl = B[l];
+    const cx<R> *Bu = B[l + 1];
+    for (int q = p; q < Pl; q += blockDim.x) {
+      const cx<R> sl = (q > 0) ? Bu[rpos<CH>(q - 1)] : mk((R)0, (R)0);
+      const cx<R> sr = (q < Ml) ? Bu[rpos<CH>(q)] : mk((R)0, (R)0);
+#pragma unroll
+      for (int i = 0; i < CH - 1; i++) {
+        const int pos = rpos<CH>(q * CH + i);
+        Bl[pos] = cfma(cfma(Bl[pos], sl, s_fc[l][i]), sr, s_fc[l][CH - 2 - i]);
+      }
+      if (q < Ml) Bl[rpos<CH>(q * CH + CH - 1)] = sr;
+    }
+    __syncthreads();
+  }
+}
+
+// Rows longer than one CTA can hold (n up to 65535 in FP32): a cluster of S
+// CTAs shares one frequency; each CTA owns blockDim.x consecutive level-0
+// chunks.  The level-1 right-hand sides are gathered into the shared memory
+// of rank 0 through distributed shared memory, rank 0 solves levels >= 1,
+// and every CTA reads its two separators back from rank 0.
+template <typename R, int CH>
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512)
+k_tridiag_cluster(cx<R> *__restrict__ spec, int n, int64_t n_pad,
+                  const RecTab<R, CH> *__restrict__ tabs, int conj_sym, int levels, int4 lsz_lo,
+                  int2 lsz_hi) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int S = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int k = blockIdx.x / S;
+  const int p = threadIdx.x, T = blockDim.x;
+  const int g = rank * T + p;            // chunk index within the row
+  const int P = S * T, M = P - 1;
+  const int lsz[kRecLevels] = {lsz_lo.x, lsz_lo.y, lsz_lo.z, lsz_lo.w, lsz_hi.x, lsz_hi.y};
+  __shared__ cx<R> s_invp[kRecLevels][CH], s_bp[kRecLevels][CH], s_fc[kRecLevels][CH];
+  __shared__ cx<R> s_e[kRecLevels];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cx<R> *B[kRecLevels];
+  size_t off = 0;
+  for (int l = 1; l < levels; l++) {
+    B[l] = reinterpret_cast<cx<R> *>(smraw) + off;
+    off += (size_t)rpos<CH>(lsz[l]) + 1;
+  }
+  cx<R> *s_first = reinterpret_cast<cx<R> *>(smraw) + off;   // [T]
+  off += (size_t)T;
+  float4 *s_row = reinterpret_cast<float4 *>(smraw + ((off * sizeof(cx<R>) + 15) & ~(size_t)15));
+  constexpr int EPC = 16 / sizeof(cx<R>);
+  const int nchunks = (T * CH) / EPC;
+
+  const RecTab<R, CH> *tb = tabs + k;
+  for (int i = p; i < levels * CH; i += T) {
+    const int l = i / CH, j = i - l * CH;
+    s_invp[l][j] = ld_tab(tb->invp[l][j], conj_sym);
+    s_bp[l][j] = ld_tab(tb->bp[l][j], conj_sym);
+    s_fc[l][j] = ld_tab(tb->fc[l][j], conj_sym);
+  }
+  if (p < levels) s_e[p] = ld_tab(tb->e[p], conj_sym);
+
+  cx<R> *row = spec + (size_t)k * n_pad + (size_t)rank * T * CH;   // this CTA's segment
+  const int nseg = n - rank * T * CH;                                 // unknowns left from here
+  const unsigned long long pol_keep = l2_evict_last();
+  cx<R> v[CH];
+  {
+    const float4 *gsrc = reinterpret_cast<const float4 *>(row);
+    for (int q = p; q < nchunks; q += T) s_row[swz(q)] = ld_hint4(&gsrc[q], pol_keep);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < CH / EPC; j++) {
+      const float4 f = s_row[swz(p * (CH / EPC) + j)];
+      const cx<R> *z = reinterpret_cast<const cx<R> *>(&f);
+#pragma unroll
+      for (int u = 0; u < EPC; u++)
+        v[j * EPC + u] = (p * CH + j * EPC + u < nseg) ? z[u] : mk((R)0, (R)0);
+    }
+  }
+  const cx<R> e0 = s_e[0];
+  v[0] = v[0] * s_invp[0][0];
+#pragma unroll
+  for (int i = 1; i < CH - 1; i++) v[i] = cfnms(v[i], e0, v[i - 1]) * s_invp[0][i];
+#pragma unroll
+  for (int i = CH - 3; i >= 0; i--) v[i] = cfnms(v[i], s_bp[0][i], v[i + 1]);
+
+  s_first[p] = v[0];
+  cluster.sync();
+  cx<R> *B1root = cluster.map_shared_rank(B[1], 0);
+  if (g < M) {
+    cx<R> nxt;
+    if (p + 1 < T) nxt = s_first[p + 1];
+    else nxt = *cluster.map_shared_rank(s_first, rank + 1);
+    B1root[rpos<CH>(g)] = cfnms(v[CH - 1], e0, v[CH - 2] + nxt);
+  }
+  cluster.sync();
+  if (rank == 0) rec_upper<R, CH>(B, lsz, levels, s_invp, s_bp, s_fc, s_e, p);
+  cluster.sync();
+  const cx<R> sl = (g > 0) ? B1root[rpos<CH>(g - 1)] : mk((R)0, (R)0);
+  const cx<R> sr = (g < M) ? B1root[rpos<CH>(g)] : mk((R)0, (R)0);
+#pragma unroll
+  for (int i = 0; i < CH - 1; i++) v[i] = cfma(cfma(v[i], sl, s_fc[0][i]), sr, s_fc[0][CH - 2 - i]);
+  v[CH - 1] = sr;
+  cluster.sync();   // rank 0's shared memory is no longer read by others
+
+#pragma unroll
+  for (int j = 0; j < CH / EPC; j++) {
+    float4 f;
+    cx<R> *z = reinterpret_cast<cx<R> *>(&f);
+#pragma unroll
+    for (int u = 0; u < EPC; u++) z[u] = v[j * EPC + u];
+    s_row[swz(p * (CH / EPC) + j)] = f;
+  }
+  __syncthreads();
+  float4 *gdst = reinterpret_cast<float4 *>(row);
+  const int nlive = (nseg < T * CH) ? (nseg + EPC - 1) / EPC : nchunks;
+  for (int q = p; q < nlive; q += T) {
+    if ((q + 1) * EPC <= nseg) {
+      st_hint4(&gdst[q], s_row[swz(q)], pol_keep);
+    } else {
+      const float4 f = s_row[swz(q)];
+      const cx<R> *z = reinterpret_cast<const cx<R> *>(&f);
+      for (int u = 0; q * EPC + u < nseg; u++) row[q * EPC + u] = z[u];
+    }
+  }
+}
+
+template <typename R, int CH>
+static cudaError_t run_tridiag_cluster(const Ctx &c, void *spec, const void *tab, int T, int S,
+                                       int conj, int levels, const int *lsz, cudaStream_t s) {
+  size_t off = 0;
+  for (int l = 1; l < levels; l++) off += (size_t)(lsz[l] + lsz[l] / CH) + 1;
+  off += (size_t)T;
+  const size_t smem = ((off * sizeof(cx<R>) + 15) & ~(size_t)15) + (size_t)T * CH * sizeof(cx<R>);
+  auto kern = k_tridiag_cluster<R, CH>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) { cudaGetLastError(); return e; }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(c.nk * S), 1, 1);
+  cfg.blockDim = dim3((unsigned)T, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)S;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int4 lo = make_int4(lsz[0], lsz[1], lsz[2], lsz[3]);
+  const int2 hi = make_int2(lsz[4], lsz[5]);
+  e = cudaLaunchKernelEx(&cfg, kern, static_cast<cx<R> *>(spec), (int)c.n, c.n_pad,
+                         static_cast<const RecTab<R, CH> *>(tab), conj, levels, lo, hi);
+  note_launch();
+  if (e != cudaSuccess) { cudaGetLastError(); return e; }
+  return cudaGetLastError();
 }
 
 template <typename R, int CH>
@@ -403,6 +621,12 @@ static cudaError_t run_tridiag(const Ctx &c, void *spec, const void *tab, int P,
 }
 
 cudaError_t launch_tridiag(const Ctx &c, void *spec, int prec, int transpose, cudaStream_t s) {
+  if (prec == AAO_PREC_FP32 && c.clu32 > 1)
+    return run_tridiag_cluster<float, 16>(c, spec, c.rec32, c.cta32, c.clu32, transpose, c.lev32,
+                                          c.lsz32, s);
+  if (prec == AAO_PREC_FP64 && c.clu64 > 1)
+    return run_tridiag_cluster<double, 16>(c, spec, c.rec64, c.cta64, c.clu64, transpose,
+                                           c.lev64, c.lsz64, s);
   if (prec == AAO_PREC_FP32 && c.lev32 > 0 && c.ch32 == 16)
     return run_tridiag_rec<float, 16>(c, spec, c.rec32, c.P32, transpose, c.lev32, c.lsz32, s);
   if (prec == AAO_PREC_FP64 && c.lev64 > 0 && c.ch64 == 8)

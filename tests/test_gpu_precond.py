@@ -175,3 +175,21 @@ def test_precond_rejects_aliasing_and_missing_workspace():
     X = to_dev(torch, rand_block(15, 16, 1))
     with pytest.raises(AAOError):
         a.precond_apply(X, out=X)
+
+
+@pytest.mark.parametrize("n,ell", [(16383, 16), (32767, 8), (65535, 16)])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_precond_long_rows_cluster_form(n, ell, prec, transpose):
+    """Rows longer than one CTA holds (the n = 65535 workload's spatial size)
+    are solved by a cluster of CTAs sharing the separator system through
+    distributed shared memory; checked against the oracle's sine (x) Fourier
+    route."""
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    S = oracle_system("heat", n, ell)
+    X = rand_block(n, ell, 77 + n)
+    a = AllAtOnce(n, ell, 1.0 / ell, precision=prec, restart=1)
+    got = to_host(a.precond_apply(to_dev(torch, X), transpose=transpose))
+    want = precond.circulant_inverse_spectral(S, X, transpose=transpose)
+    assert rel_max(got, want) <= tol_for(S, "heat", prec, n, ell)

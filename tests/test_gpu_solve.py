@@ -215,3 +215,22 @@ def test_autograd_function_matches_oracle_and_finite_differences():
             return 0.5 * float(((Uk - to_dev(torch, U_obs)) ** 2).sum())
     fd = (f(0.8 + hs) - f(0.8 - hs)) / (2 * hs)
     assert abs(fd - k_t.grad.item()) <= 1e-6 * abs(k_t.grad.item())
+
+
+@pytest.mark.parametrize("ell", [512])
+def test_heat_n65535_large_workload(ell):
+    """The large workload's spatial size (n = 65535, 2.7e8 unknowns at
+    ell = 4096; here ell = 512 to keep the oracle's time stepping short):
+    FGMRES(20) with the FP32 circulant.  The FP64 representation floor of the
+    solution is 8.8e-9 here (extended-precision residual of the oracle's
+    solution), so the solve runs to 2e-8 and is checked for residual and for
+    solution error against time stepping."""
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    n = 65535
+    S = oracle_system("heat", n, ell)
+    u0 = syn.heat_initial(n, modes=8)
+    a = AllAtOnce(n, ell, 1.0 / ell, precision="fp32", restart=20)
+    x, info = a.solve(a.build_rhs(to_dev(torch, u0)), restart=20, rtol=2e-8)
+    assert info["converged"], info
+    _check(S, system.rhs_heat(S, u0), to_host(x), rtol=2e-8, errtol=1e-6)
