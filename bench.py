@@ -267,6 +267,28 @@ def extra_rows(device, hbm_peak):
                                                    "5e-9 (FP64 floors 2.7e-10 / 2.5e-9)"}
     del sa
     torch.cuda.empty_cache()
+    # large heat workload, n = 65535: sweep over ell, FGMRES(20), FP32 vs FP64
+    # preconditioner.  The FP64 representation floor of the solution is up to
+    # 8.8e-9 here (ell = 512), so both forms solve to 2e-8.
+    nl_ = 65535
+    sweep = {}
+    for ell_ in (512, 1024, 2048, 4096):
+        sl = AllAtOnce(nl_, ell_, 1.0 / ell_, precision="fp32", restart=20, device=device)
+        bl = sl.build_rhs(torch.from_numpy(syn.heat_initial(nl_)).to(device))
+        entry = {}
+        for prec in ("fp32", "fp64"):
+            sl.set_precision(prec)
+            sl.solve(bl, restart=20, rtol=2e-8)
+            info = {}
+            ms = _timed(lambda i: info.update(sl.solve(bl, restart=20, rtol=2e-8)[1]), 2, stream)
+            entry[prec] = {"ms": round(ms, 2), "iters": info["iters"],
+                           "relres": info["relres_true"]}
+        entry["unknowns"] = nl_ * ell_
+        entry["speedup_fp32_vs_fp64"] = round(entry["fp64"]["ms"] / entry["fp32"]["ms"], 3)
+        sweep[f"ell{ell_}"] = entry
+        del sl, bl
+        torch.cuda.empty_cache()
+    rows["heat_n65535_sweep_rtol2e-8"] = sweep
     return rows
 
 
@@ -443,7 +465,7 @@ def run_gpu(args):
     if dom in per_kernel:
         pk = per_kernel[dom]
         roofline = {"bound": "hbm", "kernel": dom, "achieved": pk["GB_s"], "peak": hbm_peak,
-                    "unit": "GB/s", "frac": pk["frac"], "traffic": None,
+                    "unit": "GB/s", "frac": pk["frac"], "traffic": _traffic(dom),
                     "peak_kind": peak_kind}
     else:
         # FP64 kernels of the outer loop are bound by the FP64 pipe: 2 FP64
