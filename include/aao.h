@@ -142,6 +142,18 @@ int aao_neumann_apply(aao_ctx *ctx, int terms, const double *x, double *y,
 int aao_matvec(aao_ctx *ctx, const double *x, double *y, int transpose,
                void *stream);
 
+/* y = A x or A^T x as aao_matvec, for an FP32 x (Section 2).  This is the
+ * product the mixed-precision solver forms with its FP32 preconditioned
+ * basis.  For the standard heat equation and BD2 the stencil sums are formed
+ * exactly in 64-bit fixed point per 32-column tile and rounded once to FP64,
+ * so y is within a few FP64 roundings of the exact product of the FP32
+ * values (elements below 2^-34 of their tile's largest contribute with an
+ * absolute error under 2^-57 of it); the literal heat form widens x and
+ * runs the FP64 stencil.  x: device, N floats; y: device, N doubles; no
+ * workspace needed.  An inf or NaN anywhere in a 32-column, 32-step tile
+ * makes that tile's outputs NaN. */
+int aao_matvec_f32(aao_ctx *ctx, const float *x, double *y, int transpose, void *stream);
+
 /* Right-hand side from initial data (Section 2): heat b = [M u0; 0; ...];
  * BD2 b = [A0 (u0 + tau v0); -M u0; 0; ...] (v0 may be NULL = at rest, which
  * is the paper's b_BD2).  u0, v0: device, n doubles; b: device, N doubles. */

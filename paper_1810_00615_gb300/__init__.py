@@ -41,9 +41,9 @@ def _stream(stream=None) -> int:
     return int(s.cuda_stream)
 
 
-def _dev_f64(t: torch.Tensor, numel: int, name: str) -> torch.Tensor:
-    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
-        raise TypeError(f"{name} must be a CUDA float64 tensor")
+def _dev_f64(t: torch.Tensor, numel: int, name: str, dtype=torch.float64) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype:
+        raise TypeError(f"{name} must be a CUDA {str(dtype).replace('torch.', '')} tensor")
     if not t.is_contiguous() or t.numel() != numel:
         raise ValueError(f"{name} must be contiguous with {numel} elements")
     return t
@@ -150,6 +150,16 @@ class AllAtOnce:
         y = self._out(out)
         check(self.lib.aao_matvec(self._ctx, x.data_ptr(), y.data_ptr(), int(bool(transpose)),
                                   _stream(stream)), "aao_matvec", self._ctx)
+        return y
+
+    def matvec_f32(self, x, transpose=False, out=None, stream=None):
+        """y = A x (or A^T x) of an FP32 x, in FP64 (the product the mixed
+        solver forms with its FP32 preconditioned basis)."""
+        x = _dev_f64(x, self.N, "x", torch.float32)
+        y = self._out(out)
+        check(self.lib.aao_matvec_f32(self._ctx, x.data_ptr(), y.data_ptr(),
+                                      int(bool(transpose)), _stream(stream)),
+              "aao_matvec_f32", self._ctx)
         return y
 
     def build_rhs(self, u0, v0=None, out=None, stream=None):

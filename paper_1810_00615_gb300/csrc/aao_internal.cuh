@@ -169,6 +169,17 @@ template <> __device__ __forceinline__ double from_f64<double>(double x) { retur
 template <typename R> __device__ __forceinline__ double to_double(R x);
 template <> __device__ __forceinline__ double to_double<float>(float x) { return to_f64(x); }
 template <> __device__ __forceinline__ double to_double<double>(double x) { return x; }
+// Conversions between a stored element type and a compute type (exact where
+// the target is wider; round-to-nearest-even where it is narrower).
+template <typename R> __device__ __forceinline__ R from_any(double x) { return from_f64<R>(x); }
+template <typename R> __device__ __forceinline__ R from_any(float x) {
+  if constexpr (sizeof(R) == 4) return x; else return to_f64(x);
+}
+template <typename R, typename OT> __device__ __forceinline__ OT to_out(R v) {
+  if constexpr (sizeof(OT) == sizeof(R)) return v;
+  else if constexpr (sizeof(OT) == 8) return to_f64(v);
+  else return to_f32(v);
+}
 
 // ------------------------------------------------- per-frequency tables
 // Tridiagonal solve of one frequency block T_k = tridiag(e, d, e), n x n,
@@ -285,10 +296,17 @@ cudaError_t fft_inverse_f32(const Ctx &c, const void *spec, double *y, cudaStrea
 cudaError_t fft_forward_f64(const Ctx &c, const double *x, const double *yprev, void *spec,
                             cudaStream_t s);
 cudaError_t fft_inverse_f64(const Ctx &c, const void *spec, double *y, cudaStream_t s);
+// FP32 preconditioner with an FP32 Neumann iterate / FP32 result (the stored
+// preconditioned basis of the mixed solver).
+cudaError_t fft_forward_f32_yf(const Ctx &c, const double *x, const float *yprev, void *spec,
+                               cudaStream_t s);
+cudaError_t fft_inverse_f32_to_f32(const Ctx &c, const void *spec, float *y, cudaStream_t s);
 cudaError_t launch_tridiag(const Ctx &c, void *spec, int prec, int transpose,
                            cudaStream_t s);
 // y = A x (or A^T x); with `sub`, y = A x - sub (fused, for the shifted Arnoldi).
 cudaError_t launch_matvec(const Ctx &c, const double *x, double *y, int transpose,
+                          cudaStream_t s, const double *sub = nullptr);
+cudaError_t launch_matvec(const Ctx &c, const float *x, double *y, int transpose,
                           cudaStream_t s, const double *sub = nullptr);
 cudaError_t launch_rhs(const Ctx &c, const double *u0, const double *v0, double *b,
                        cudaStream_t s);
@@ -308,6 +326,8 @@ cudaError_t launch_update_dots(const double *const *V, int nv, const double *h,
                                double *out2, cudaStream_t s, const double *hf = nullptr);
 // x += sum_j y[j] Z_j (y on device)
 cudaError_t launch_combine(const double *const *Z, int nv, const double *y, double *x,
+                           int64_t N, cudaStream_t s);
+cudaError_t launch_combine(const float *const *Z, int nv, const double *y, double *x,
                            int64_t N, cudaStream_t s);
 // y = a*x (a on device, *a_scale of index)
 cudaError_t launch_scale(const double *x, double *y, const double *a, int64_t N,

@@ -54,6 +54,9 @@ __global__ void k_finish(const double *__restrict__ partials, int nb, int nv,
 struct Ptrs8 {
   const double *p[8];
 };
+template <typename T> struct PtrsT {
+  const T *p[8];
+};
 struct Coef8 {
   double c[8];
 };
@@ -78,9 +81,14 @@ int red_blocks(int64_t N) {
 constexpr int kMvCols = 128;   // columns per CTA
 constexpr int kMvRows = 32;    // time steps per thread
 
-template <int NB, bool TR, bool SUB>
+// x is FP64, or FP32 for the preconditioned basis of the mixed solver (then
+// widened exactly with integer operations: no FP64 conversion instruction).
+__device__ __forceinline__ double wide(double v) { return v; }
+__device__ __forceinline__ double wide(float v) { return to_f64(v); }
+
+template <int NB, bool TR, bool SUB, typename XT>
 __global__ void __launch_bounds__(kMvCols)
-k_matvec(const double *__restrict__ x, double *__restrict__ y, int n, int ell,
+k_matvec(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
          const double *__restrict__ d0, const double *__restrict__ o0,
          double d1, double o1, double d2, double o2, const double *__restrict__ sub) {
   const int i = blockIdx.x * kMvCols + threadIdx.x;
@@ -88,10 +96,10 @@ k_matvec(const double *__restrict__ x, double *__restrict__ y, int n, int ell,
   const int c0 = blockIdx.y * kMvRows;
   const int c1 = min(ell, c0 + kMvRows);
   auto row_vals = [&](int t, double &xc, double &sn) {
-    const double *xr = x + (int64_t)t * n;
-    xc = xr[i];
-    const double l = (i > 0) ? xr[i - 1] : 0.0;
-    const double r = (i + 1 < n) ? xr[i + 1] : 0.0;
+    const XT *xr = x + (int64_t)t * n;
+    xc = wide(xr[i]);
+    const double l = (i > 0) ? wide(xr[i - 1]) : 0.0;
+    const double r = (i + 1 < n) ? wide(xr[i + 1]) : 0.0;
     sn = l + r;
   };
   // registers: previous (p1) and second previous (p2) step in walk order
@@ -122,20 +130,136 @@ k_matvec(const double *__restrict__ x, double *__restrict__ y, int n, int ell,
   }
 }
 
-template <int NB, bool TR>
-static void mv_sub(const Ctx &c, dim3 grid, const double *x, double *y, const double *sub,
+// ------------------------------------------- matvec on an FP32 basis vector
+// With the FP32 preconditioner the FGMRES basis z_j holds FP32 numbers, and
+// for the standard heat equation (any steps) and BD2 every block is
+// a M + b K with M = (h/6) tridiag(1,4,1), K = (1/h) tridiag(-1,2,-1)
+// (Section 2).  With q_t = 4 x_t + x_{t,i-1} + x_{t,i+1} and
+// s_t = 2 x_t - x_{t,i-1} - x_{t,i+1}:
+//   heat  (A x)_t = (h/6)(q_t - q_{t-1})            + beta_t s_t
+//   BD2   (A x)_t = (h/6)(q_t - 2 q_{t-1} + q_{t-2}) + beta   s_t
+// (transpose: t+1, t+2 instead of t-1, t-2).  Each warp converts its tile of
+// x (its 32 columns, one halo column each side, the time steps it needs) to
+// 64-bit fixed point at the tile's largest exponent, forms both sums exactly
+// in integers (no cancellation error however much the terms cancel), rounds
+// them once to FP64 and finishes with two FMAs.  GB300 issues integer
+// operations at 64 per clock per SM and FP64 at 2, so this replaces five of
+// the seven FP64 operations per element of the FP64 form with integer work.
+// Elements more than 2^34 below the tile maximum are truncated at 2^-57 of
+// that maximum; everything else is exact up to the final two roundings.
+constexpr int kFxRows = 32;   // output time steps per warp tile
+
+__device__ __forceinline__ int f32_exp(float v) {
+  const int e = (int)((__float_as_uint(v) >> 23) & 0xffu);
+  return e ? e : 1;   // subnormals share exponent 1 with the smallest normals
+}
+
+// x * 2^(184 - emax) as an integer (|.| < 2^58), emax >= the exponent of x.
+__device__ __forceinline__ long long fx_from_f32(float v, int emax) {
+  const unsigned b = __float_as_uint(v);
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned mant = (b & 0x7fffffu) | (e ? 0x800000u : 0u);
+  const int sh = min(emax - (e ? (int)e : 1), 63);
+  const unsigned long long u = ((unsigned long long)mant << 34) >> sh;
+  return (b >> 31) ? -(long long)u : (long long)u;
+}
+
+// S * 2^(emax - 184) rounded to nearest even, for |S| < 2^63, 1 <= emax <= 254
+// (the result is always a normal FP64 number).
+__device__ __forceinline__ double fx_to_f64(long long S, int emax) {
+  const unsigned long long neg = (unsigned long long)(S >> 63);
+  unsigned long long u = ((unsigned long long)S ^ neg) - neg;
+  const int lz = __clzll(u);
+  u <<= (lz & 63);
+  unsigned long long mant = u >> 11;                       // 53 bits, top one set
+  mant += (((unsigned)u & 0x7ffu) + (unsigned)(mant & 1u) + 0x3ffu) >> 11;
+  const unsigned long long bits =
+      ((unsigned long long)(901 + emax - lz) << 52) + mant + (neg << 63);
+  return S ? __longlong_as_double((long long)bits) : 0.0;
+}
+
+template <int NB, bool TR, bool SUB>
+__global__ void __launch_bounds__(kMvCols)
+k_matvec_fx(const float *__restrict__ x, double *__restrict__ y, int n, int ell, double mh,
+            const double *__restrict__ beta, const double *__restrict__ sub) {
+  constexpr int R = kFxRows, IN = R + NB - 1;   // input time steps per tile
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kMvCols + threadIdx.x;
+  const int iw = i - lane;                      // first column of the warp
+  if (iw >= n) return;                          // whole warp past the end
+  const int c0 = blockIdx.y * R;
+  // input row r is time step c0 - (NB-1) + r (forward) or c0 + r (transpose)
+  auto trow = [&](int r) { return TR ? c0 + r : c0 - (NB - 1) + r; };
+  auto ld = [&](int col, int r) -> float {
+    const int t = trow(r);
+    return (r < IN && col >= 0 && col < n && t >= 0 && t < ell)
+               ? __ldg(&x[(int64_t)t * n + col]) : 0.0f;
+  };
+  float zc[IN];
+#pragma unroll
+  for (int r = 0; r < IN; r++) zc[r] = ld(i, r);
+  // halo columns iw - 1 and iw + 32: lane l holds rows l and l + 32
+  const float hl0 = ld(iw - 1, lane), hr0 = ld(iw + 32, lane);
+  const float hl1 = (IN > 32) ? ld(iw - 1, lane + 32) : 0.0f;
+  const float hr1 = (IN > 32) ? ld(iw + 32, lane + 32) : 0.0f;
+  int em = max(max(f32_exp(hl0), f32_exp(hr0)), max(f32_exp(hl1), f32_exp(hr1)));
+#pragma unroll
+  for (int r = 0; r < IN; r++) em = max(em, f32_exp(zc[r]));
+  em = (int)__reduce_max_sync(0xffffffffu, (unsigned)em);
+  const int t_lo = c0, t_hi = min(ell, c0 + R);
+  if (em == 255) {                              // an inf or NaN in the tile
+    if (i < n)
+      for (int t = t_lo; t < t_hi; t++) y[(int64_t)t * n + i] = __longlong_as_double(0x7ff8000000000000ll);
+    return;
+  }
+  const long long XL0 = fx_from_f32(hl0, em), XR0 = fx_from_f32(hr0, em);
+  const long long XL1 = fx_from_f32(hl1, em), XR1 = fx_from_f32(hr1, em);
+  long long q1 = 0, q2 = 0;                     // q of the previous one or two rows walked
+#pragma unroll
+  for (int k = 0; k < IN; k++) {
+    const int r = TR ? IN - 1 - k : k;
+    const long long X = fx_from_f32(zc[r], em);
+    long long Xl = __shfl_up_sync(0xffffffffu, X, 1);
+    long long Xr = __shfl_down_sync(0xffffffffu, X, 1);
+    const long long hl = __shfl_sync(0xffffffffu, r < 32 ? XL0 : XL1, r & 31);
+    const long long hr = __shfl_sync(0xffffffffu, r < 32 ? XR0 : XR1, r & 31);
+    if (lane == 0) Xl = hl;
+    if (lane == 31) Xr = hr;
+    const long long P = Xl + Xr;
+    const long long q = 4 * X + P;
+    if (k >= NB - 1) {
+      const int t = trow(r);
+      if (i < n && t < ell) {
+        const long long sm = (NB == 2) ? q - q1 : q - 2 * q1 + q2;
+        const long long sk = 2 * X - P;
+        const double bt = __ldg(&beta[t]);
+        const double skd = fx_to_f64(sk, em), smd = fx_to_f64(sm, em);
+        const int64_t o = (int64_t)t * n + i;
+        double acc = SUB ? fma(bt, skd, -__ldg(&sub[o])) : bt * skd;
+        y[o] = fma(mh, smd, acc);
+      }
+    }
+    q2 = q1;
+    q1 = q;
+  }
+}
+
+template <int NB, bool TR, typename XT>
+static void mv_sub(const Ctx &c, dim3 grid, const XT *x, double *y, const double *sub,
                    cudaStream_t s) {
   const int n = (int)c.n, ell = (int)c.ell;
   if (sub)
-    k_matvec<NB, TR, true><<<grid, kMvCols, 0, s>>>(x, y, n, ell, c.mv_d0, c.mv_o0, c.mv_d1,
-                                                    c.mv_o1, c.mv_d2, c.mv_o2, sub);
+    k_matvec<NB, TR, true, XT><<<grid, kMvCols, 0, s>>>(x, y, n, ell, c.mv_d0, c.mv_o0, c.mv_d1,
+                                                        c.mv_o1, c.mv_d2, c.mv_o2, sub);
   else
-    k_matvec<NB, TR, false><<<grid, kMvCols, 0, s>>>(x, y, n, ell, c.mv_d0, c.mv_o0, c.mv_d1,
-                                                     c.mv_o1, c.mv_d2, c.mv_o2, nullptr);
+    k_matvec<NB, TR, false, XT><<<grid, kMvCols, 0, s>>>(x, y, n, ell, c.mv_d0, c.mv_o0,
+                                                         c.mv_d1, c.mv_o1, c.mv_d2, c.mv_o2,
+                                                         nullptr);
 }
 
-cudaError_t launch_matvec(const Ctx &c, const double *x, double *y, int transpose,
-                          cudaStream_t s, const double *sub) {
+template <typename XT>
+static cudaError_t matvec_any(const Ctx &c, const XT *x, double *y, int transpose,
+                              cudaStream_t s, const double *sub) {
   const int n = (int)c.n, ell = (int)c.ell;
   const dim3 grid((unsigned)((n + kMvCols - 1) / kMvCols),
                   (unsigned)((ell + kMvRows - 1) / kMvRows));
@@ -144,6 +268,35 @@ cudaError_t launch_matvec(const Ctx &c, const double *x, double *y, int transpos
   else if (bd2) mv_sub<3, false>(c, grid, x, y, sub, s);
   else if (transpose) mv_sub<2, true>(c, grid, x, y, sub, s);
   else mv_sub<2, false>(c, grid, x, y, sub, s);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matvec(const Ctx &c, const double *x, double *y, int transpose,
+                          cudaStream_t s, const double *sub) {
+  return matvec_any(c, x, y, transpose, s, sub);
+}
+
+template <int NB, bool TR>
+static void mv_fx(const Ctx &c, dim3 grid, const float *x, double *y, const double *sub,
+                  cudaStream_t s) {
+  const int n = (int)c.n, ell = (int)c.ell;
+  const double mh = c.h / 6.0;
+  if (sub) k_matvec_fx<NB, TR, true><<<grid, kMvCols, 0, s>>>(x, y, n, ell, mh, c.beta, sub);
+  else k_matvec_fx<NB, TR, false><<<grid, kMvCols, 0, s>>>(x, y, n, ell, mh, c.beta, nullptr);
+}
+
+cudaError_t launch_matvec(const Ctx &c, const float *x, double *y, int transpose,
+                          cudaStream_t s, const double *sub) {
+  if (c.equation == AAO_HEAT_LITERAL) return matvec_any(c, x, y, transpose, s, sub);
+  const int n = (int)c.n, ell = (int)c.ell;
+  const dim3 grid((unsigned)((n + kMvCols - 1) / kMvCols),
+                  (unsigned)((ell + kFxRows - 1) / kFxRows));
+  const bool bd2 = c.equation == AAO_WAVE_BD2;
+  if (bd2 && transpose) mv_fx<3, true>(c, grid, x, y, sub, s);
+  else if (bd2) mv_fx<3, false>(c, grid, x, y, sub, s);
+  else if (transpose) mv_fx<2, true>(c, grid, x, y, sub, s);
+  else mv_fx<2, false>(c, grid, x, y, sub, s);
   note_launch();
   return cudaGetLastError();
 }
@@ -332,9 +485,9 @@ cudaError_t launch_update_dots(const double *const *V, int nv, const double *h, 
 }
 
 // ------------------------------------------------------------ x += Z y
-template <int NV>
+template <int NV, typename ZT>
 __global__ void __launch_bounds__(kThreads)
-k_combine(Ptrs8 Z, const double *__restrict__ yv, double *__restrict__ x, int64_t N) {
+k_combine(PtrsT<ZT> Z, const double *__restrict__ yv, double *__restrict__ x, int64_t N) {
   double c[NV];
 #pragma unroll
   for (int j = 0; j < NV; j++) c[j] = yv[j];
@@ -342,28 +495,39 @@ k_combine(Ptrs8 Z, const double *__restrict__ yv, double *__restrict__ x, int64_
        g += (int64_t)gridDim.x * kThreads) {
     double a = x[g];
 #pragma unroll
-    for (int j = 0; j < NV; j++) a = fma(c[j], __ldg(&Z.p[j][g]), a);
+    for (int j = 0; j < NV; j++) a = fma(c[j], wide(__ldg(&Z.p[j][g])), a);
     x[g] = a;
   }
 }
 
-cudaError_t launch_combine(const double *const *Z, int nv, const double *y, double *x,
-                           int64_t N, cudaStream_t s) {
+template <typename ZT>
+static cudaError_t combine_any(const ZT *const *Z, int nv, const double *y, double *x, int64_t N,
+                               cudaStream_t s) {
   int64_t blocks = (N + kThreads - 1) / kThreads;
   if (blocks > 152 * 16) blocks = 152 * 16;
   int done = 0;
   while (done < nv) {
     const int g = (nv - done) > 8 ? 8 : (nv - done);
-    Ptrs8 P{};
+    PtrsT<ZT> P{};
     for (int j = 0; j < g; j++) P.p[j] = Z[done + j];
     switch (g) {
-#define AAO_CB(G) case G: k_combine<G><<<(unsigned)blocks, kThreads, 0, s>>>(P, y + done, x, N); note_launch(); break;
+#define AAO_CB(G) case G: k_combine<G, ZT><<<(unsigned)blocks, kThreads, 0, s>>>(P, y + done, x, N); note_launch(); break;
       AAO_CB(1) AAO_CB(2) AAO_CB(3) AAO_CB(4) AAO_CB(5) AAO_CB(6) AAO_CB(7) AAO_CB(8)
 #undef AAO_CB
     }
     done += g;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const double *const *Z, int nv, const double *y, double *x,
+                           int64_t N, cudaStream_t s) {
+  return combine_any(Z, nv, y, x, N, s);
+}
+
+cudaError_t launch_combine(const float *const *Z, int nv, const double *y, double *x,
+                           int64_t N, cudaStream_t s) {
+  return combine_any(Z, nv, y, x, N, s);
 }
 
 // ------------------------------------------------------------ misc

@@ -420,29 +420,36 @@ int check_ws(const Ctx &c, int restart) {
   return AAO_OK;
 }
 
-cudaError_t precond_once(Ctx &c, const double *x, const double *yprev, double *y, int tr,
+// One application of P^{-1} (or P^{-T}); with yprev, of P^{-1}(x - E yprev).
+// YT = float stores an FP32 result (FP32 preconditioner only): the values
+// the FP32 inverse transform produces are then kept as they are.
+template <typename YT>
+cudaError_t precond_once(Ctx &c, const double *x, const YT *yprev, YT *y, int tr,
                          cudaStream_t s) {
   void *spec = c.ws + aao::ws_layout(c, 0).spec;
   const bool f32 = c.prec == AAO_PREC_FP32;
   cudaError_t e = run(c, AAO_K_FFT_FORWARD, s, [&] {
-    return f32 ? aao::fft_forward_f32(c, x, yprev, spec, s)
-               : aao::fft_forward_f64(c, x, yprev, spec, s);
+    if constexpr (sizeof(YT) == 4) return aao::fft_forward_f32_yf(c, x, yprev, spec, s);
+    else return f32 ? aao::fft_forward_f32(c, x, yprev, spec, s)
+                    : aao::fft_forward_f64(c, x, yprev, spec, s);
   });
   if (e != cudaSuccess) return e;
   e = run(c, AAO_K_TRIDIAG, s, [&] { return aao::launch_tridiag(c, spec, c.prec, tr, s); });
   if (e != cudaSuccess) return e;
   return run(c, AAO_K_FFT_INVERSE, s, [&] {
-    return f32 ? aao::fft_inverse_f32(c, spec, y, s) : aao::fft_inverse_f64(c, spec, y, s);
+    if constexpr (sizeof(YT) == 4) return aao::fft_inverse_f32_to_f32(c, spec, y, s);
+    else return f32 ? aao::fft_inverse_f32(c, spec, y, s) : aao::fft_inverse_f64(c, spec, y, s);
   });
 }
 
 // Q_i^{-1} x (or Q_i^{-T} x) by y_0 = P^{-1} x, y_m = P^{-1}(x - E y_{m-1}).
-cudaError_t neumann(Ctx &c, int terms, const double *x, double *y, int tr, cudaStream_t s) {
-  cudaError_t e = precond_once(c, x, nullptr, y, tr, s);
+template <typename YT>
+cudaError_t neumann(Ctx &c, int terms, const double *x, YT *y, int tr, cudaStream_t s) {
+  cudaError_t e = precond_once<YT>(c, x, nullptr, y, tr, s);
   if (e != cudaSuccess) return e;
   if (!c.variable_steps) return cudaSuccess;   // E = 0: every further term is P^{-1} x
   for (int m = 1; m < terms; m++)
-    if ((e = precond_once(c, x, y, y, tr, s)) != cudaSuccess) return e;
+    if ((e = precond_once<YT>(c, x, y, y, tr, s)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
@@ -474,6 +481,12 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
   std::vector<double *> V((size_t)m + 1), Z((size_t)m);
   for (int j = 0; j <= m; j++) V[(size_t)j] = vec_at(c, L, j);
   for (int j = 0; j < m; j++) Z[(size_t)j] = precond ? vec_at(c, L, m + 1 + j) : V[(size_t)j];
+  // With the FP32 preconditioner the basis z_j = P^{-1} v_j is stored in FP32:
+  // its values are FP32 numbers already, and flexible GMRES needs only that
+  // A z_j is formed from the z_j that x is later built from.
+  const bool zf = precond >= 1 && c.prec == AAO_PREC_FP32;
+  std::vector<float *> Zf((size_t)m);
+  for (int j = 0; j < m; j++) Zf[(size_t)j] = reinterpret_cast<float *>(Z[(size_t)j]);
   for (auto *v : V)
     if (overlap(v, b, vb) || overlap(v, x, vb)) return AAO_EINVAL;
 
@@ -528,12 +541,20 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
     int jd = 0;
     bool numeric_fail = false;
     for (int j = 0; j < m; j++) {
-      if (precond == 1) AAO_CK(c, precond_once(c, V[(size_t)j], nullptr, Z[(size_t)j], tr, s));
-      else if (precond >= 2) AAO_CK(c, neumann(c, precond, V[(size_t)j], Z[(size_t)j], tr, s));
+      if (zf) {
+        if (precond == 1)
+          AAO_CK(c, precond_once<float>(c, V[(size_t)j], nullptr, Zf[(size_t)j], tr, s));
+        else AAO_CK(c, neumann<float>(c, precond, V[(size_t)j], Zf[(size_t)j], tr, s));
+      } else if (precond == 1) {
+        AAO_CK(c, precond_once<double>(c, V[(size_t)j], nullptr, Z[(size_t)j], tr, s));
+      } else if (precond >= 2) {
+        AAO_CK(c, neumann<double>(c, precond, V[(size_t)j], Z[(size_t)j], tr, s));
+      }
       double *w = V[(size_t)j + 1];
       // w~ = A z_j - V_j (unscaled; the true vector is sc[j] times it)
       AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] {
-        return aao::launch_matvec(c, Z[(size_t)j], w, tr, s, V[(size_t)j]);
+        return zf ? aao::launch_matvec(c, Zf[(size_t)j], w, tr, s, V[(size_t)j])
+                  : aao::launch_matvec(c, Z[(size_t)j], w, tr, s, V[(size_t)j]);
       }));
       const int nv = j + 1;
       for (int i = 0; i < nv; i++) sc2[(size_t)i] = sc[(size_t)i] * sc[(size_t)i];
@@ -601,7 +622,10 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
     }
     for (int i = 0; i < jd; i++) hs[480 + i] = y[(size_t)i] * sc[(size_t)i];   // z_i = sc_i Z_i
     AAO_CK(c, cudaMemcpyAsync(d_y, hs + 480, jd * sizeof(double), cudaMemcpyHostToDevice, s));
-    AAO_CK(c, run(c, AAO_K_COMBINE, s, [&] { return aao::launch_combine(Z.data(), jd, d_y, x, N, s); }));
+    AAO_CK(c, run(c, AAO_K_COMBINE, s, [&] {
+      return zf ? aao::launch_combine(Zf.data(), jd, d_y, x, N, s)
+                : aao::launch_combine(Z.data(), jd, d_y, x, N, s);
+    }));
     restarts++;
   }
   AAO_CK(c, cudaStreamSynchronize(s));
@@ -752,7 +776,7 @@ int aao_precond_apply(aao_ctx *ctx, const double *x, double *y, int transpose, v
   if (!ctx || !x || !y) return AAO_EINVAL;
   Ctx &c = ctx->c;
   if (overlap(x, y, (size_t)c.N * sizeof(double)) || check_ws(c, 0) != AAO_OK) return AAO_EINVAL;
-  AAO_CK(c, precond_once(c, x, nullptr, y, transpose ? 1 : 0, as_stream(stream)));
+  AAO_CK(c, precond_once<double>(c, x, nullptr, y, transpose ? 1 : 0, as_stream(stream)));
   return AAO_OK;
 }
 
@@ -769,6 +793,15 @@ int aao_matvec(aao_ctx *ctx, const double *x, double *y, int transpose, void *st
   if (!ctx || !x || !y) return AAO_EINVAL;
   Ctx &c = ctx->c;
   if (overlap(x, y, (size_t)c.N * sizeof(double))) return AAO_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] { return aao::launch_matvec(c, x, y, transpose ? 1 : 0, s); }));
+  return AAO_OK;
+}
+
+int aao_matvec_f32(aao_ctx *ctx, const float *x, double *y, int transpose, void *stream) {
+  if (!ctx || !x || !y) return AAO_EINVAL;
+  Ctx &c = ctx->c;
+  if (overlap2(x, (size_t)c.N * sizeof(float), y, (size_t)c.N * sizeof(double))) return AAO_EINVAL;
   cudaStream_t s = as_stream(stream);
   AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] { return aao::launch_matvec(c, x, y, transpose ? 1 : 0, s); }));
   return AAO_OK;

@@ -19,37 +19,21 @@ static int persistent_grid(K kern, int threads, size_t smem, int npanels) {
   return g < npanels ? g : npanels;
 }
 
-#ifndef AAO_FFT_PIPE
-#define AAO_FFT_PIPE 0
-#endif
-
-template <typename R, int L>
-static cudaError_t run_forward(int64_t n, int64_t n_pad, const double *x, const double *y,
+template <typename R, int L, typename YT>
+static cudaError_t run_forward(int64_t n, int64_t n_pad, const double *x, const YT *y,
                                const R *sigk, cx<R> *spec, const cx<R> *tw, cudaStream_t s) {
-  if (!y && AAO_FFT_PIPE) {
-    using P = PShape<R, L>;
-    const int np = (int)((n + 2 * P::C - 1) / (2 * P::C));
-    auto kern = k_fft_forward_pipe<R, L>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)P::SMEM_F);
-    if (e != cudaSuccess) { cudaGetLastError(); return e; }
-    const int g = persistent_grid(kern, P::T, P::SMEM_F, np);
-    kern<<<g, P::T, P::SMEM_F, s>>>(x, spec, (int)n, n_pad, tw, np);
-    note_launch();
-    return cudaGetLastError();
-  }
   using S = Shape<R, L>;
   const int W = 2 * S::C;
   const int np = (int)((n + W - 1) / W);
   cudaError_t e;
   if (y) {
-    auto kern = k_fft_forward<R, L, true>;
+    auto kern = k_fft_forward<R, L, true, YT>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
     if (e != cudaSuccess) { cudaGetLastError(); return e; }
     const int g = persistent_grid(kern, S::T, S::SMEM, np);
     kern<<<g, S::T, S::SMEM, s>>>(x, y, sigk, spec, (int)n, n_pad, tw, np);
   } else {
-    auto kern = k_fft_forward<R, L, false>;
+    auto kern = k_fft_forward<R, L, false, double>;   // no iterate: one instantiation
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
     if (e != cudaSuccess) { cudaGetLastError(); return e; }
     const int g = persistent_grid(kern, S::T, S::SMEM, np);
@@ -59,30 +43,18 @@ static cudaError_t run_forward(int64_t n, int64_t n_pad, const double *x, const 
   return cudaGetLastError();
 }
 
-template <typename R, int L>
-static cudaError_t run_inverse(int64_t n, int64_t n_pad, const cx<R> *spec, double *y,
+template <typename R, int L, typename OT>
+static cudaError_t run_inverse(int64_t n, int64_t n_pad, const cx<R> *spec, OT *y,
                                const cx<R> *tw, cudaStream_t s) {
-  if (!AAO_FFT_PIPE) {
-    using S = Shape<R, L>;
-    const int W = 2 * S::C;
-    const int np = (int)((n + W - 1) / W);
-    auto kern = k_fft_inverse<R, L>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)S::SMEM);
-    if (e != cudaSuccess) { cudaGetLastError(); return e; }
-    const int g = persistent_grid(kern, S::T, S::SMEM, np);
-    kern<<<g, S::T, S::SMEM, s>>>(spec, y, (int)n, n_pad, tw, np);
-    note_launch();
-    return cudaGetLastError();
-  }
-  using P = PShape<R, L>;
-  const int np = (int)((n + 2 * P::C - 1) / (2 * P::C));
-  auto kern = k_fft_inverse_pipe<R, L>;
+  using S = Shape<R, L>;
+  const int W = 2 * S::C;
+  const int np = (int)((n + W - 1) / W);
+  auto kern = k_fft_inverse<R, L, OT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)P::SMEM_I);
+                                       (int)S::SMEM);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
-  const int g = persistent_grid(kern, P::T, P::SMEM_I, np);
-  kern<<<g, P::T, P::SMEM_I, s>>>(spec, y, (int)n, n_pad, tw, np);
+  const int g = persistent_grid(kern, S::T, S::SMEM, np);
+  kern<<<g, S::T, S::SMEM, s>>>(spec, y, (int)n, n_pad, tw, np);
   note_launch();
   return cudaGetLastError();
 }
@@ -90,22 +62,22 @@ static cudaError_t run_inverse(int64_t n, int64_t n_pad, const cx<R> *spec, doub
 #define AAO_FFT_CASES(X) \
   X(1) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
 
-template <typename R>
-cudaError_t forward_any(int64_t ell, int64_t n, int64_t n_pad, const double *x, const double *y,
+template <typename R, typename YT>
+cudaError_t forward_any(int64_t ell, int64_t n, int64_t n_pad, const double *x, const YT *y,
                         const R *sigk, cx<R> *spec, const cx<R> *tw, cudaStream_t s) {
   switch (ell) {
-#define AAO_F(L) case L: return run_forward<R, L>(n, n_pad, x, y, sigk, spec, tw, s);
+#define AAO_F(L) case L: return run_forward<R, L, YT>(n, n_pad, x, y, sigk, spec, tw, s);
     AAO_FFT_CASES(AAO_F)
 #undef AAO_F
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <typename R>
-cudaError_t inverse_any(int64_t ell, int64_t n, int64_t n_pad, const cx<R> *spec, double *y,
+template <typename R, typename OT>
+cudaError_t inverse_any(int64_t ell, int64_t n, int64_t n_pad, const cx<R> *spec, OT *y,
                         const cx<R> *tw, cudaStream_t s) {
   switch (ell) {
-#define AAO_I(L) case L: return run_inverse<R, L>(n, n_pad, spec, y, tw, s);
+#define AAO_I(L) case L: return run_inverse<R, L, OT>(n, n_pad, spec, y, tw, s);
     AAO_FFT_CASES(AAO_I)
 #undef AAO_I
     default: return cudaErrorInvalidValue;

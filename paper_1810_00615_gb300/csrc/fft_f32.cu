@@ -4,11 +4,20 @@
 namespace aao {
 cudaError_t fft_forward_f32(const Ctx &c, const double *x, const double *y, void *spec,
                             cudaStream_t s) {
-  return fft::forward_any<float>(c.ell, c.n, c.n_pad, x, y, c.sigk32,
+  return fft::forward_any<float, double>(c.ell, c.n, c.n_pad, x, y, c.sigk32,
                                  static_cast<cx<float> *>(spec), c.tw32, s);
 }
 cudaError_t fft_inverse_f32(const Ctx &c, const void *spec, double *y, cudaStream_t s) {
-  return fft::inverse_any<float>(c.ell, c.n, c.n_pad, static_cast<const cx<float> *>(spec), y,
-                                 c.tw32, s);
+  return fft::inverse_any<float, double>(c.ell, c.n, c.n_pad,
+                                         static_cast<const cx<float> *>(spec), y, c.tw32, s);
+}
+cudaError_t fft_forward_f32_yf(const Ctx &c, const double *x, const float *y, void *spec,
+                               cudaStream_t s) {
+  return fft::forward_any<float, float>(c.ell, c.n, c.n_pad, x, y, c.sigk32,
+                                        static_cast<cx<float> *>(spec), c.tw32, s);
+}
+cudaError_t fft_inverse_f32_to_f32(const Ctx &c, const void *spec, float *y, cudaStream_t s) {
+  return fft::inverse_any<float, float>(c.ell, c.n, c.n_pad,
+                                        static_cast<const cx<float> *>(spec), y, c.tw32, s);
 }
 }  // namespace aao

@@ -4,11 +4,11 @@
 namespace aao {
 cudaError_t fft_forward_f64(const Ctx &c, const double *x, const double *y, void *spec,
                             cudaStream_t s) {
-  return fft::forward_any<double>(c.ell, c.n, c.n_pad, x, y, c.sigk,
+  return fft::forward_any<double, double>(c.ell, c.n, c.n_pad, x, y, c.sigk,
                                   static_cast<cx<double> *>(spec), c.tw64, s);
 }
 cudaError_t fft_inverse_f64(const Ctx &c, const void *spec, double *y, cudaStream_t s) {
-  return fft::inverse_any<double>(c.ell, c.n, c.n_pad, static_cast<const cx<double> *>(spec),
+  return fft::inverse_any<double, double>(c.ell, c.n, c.n_pad, static_cast<const cx<double> *>(spec),
                                   y, c.tw64, s);
 }
 }  // namespace aao

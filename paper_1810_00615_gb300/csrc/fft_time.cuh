@@ -240,16 +240,16 @@ template <typename R, int L> struct Shape {
 // The first Stockham pass (radix R1, no twiddles) reads its 2*R1 real inputs
 // per butterfly straight from global memory into registers, so a thread has
 // all of its loads in flight at once; later passes go through shared memory.
-template <typename R, int L, bool NEUMANN>
-__device__ __forceinline__ R load_real(const double *__restrict__ x, const double *__restrict__ y,
+template <typename R, int L, bool NEUMANN, typename YT>
+__device__ __forceinline__ R load_real(const double *__restrict__ x, const YT *__restrict__ y,
                                        const R *__restrict__ sigk, int n, int t, int i,
                                        unsigned long long pol = 0) {
   if (i >= n) return (R)0;
   const size_t o = (size_t)t * n + i;
   if constexpr (NEUMANN) {
-    const R yc = from_f64<R>(__ldg(&y[o]));
-    const R yl = (i > 0) ? from_f64<R>(__ldg(&y[o - 1])) : (R)0;
-    const R yr = (i + 1 < n) ? from_f64<R>(__ldg(&y[o + 1])) : (R)0;
+    const R yc = from_any<R>(__ldg(&y[o]));
+    const R yl = (i > 0) ? from_any<R>(__ldg(&y[o - 1])) : (R)0;
+    const R yr = (i + 1 < n) ? from_any<R>(__ldg(&y[o + 1])) : (R)0;
     return from_f64<R>(__ldg(&x[o])) - __ldg(&sigk[t]) * ((yc + yc) - yl - yr);
   } else {
     return from_f64<R>(ld_hint(&x[o], pol));
@@ -278,9 +278,9 @@ __device__ __forceinline__ void prefetch_rows(const double *__restrict__ x, int 
   }
 }
 
-template <typename R, int L, bool NEUMANN>
+template <typename R, int L, bool NEUMANN, typename YT>
 __global__ void __launch_bounds__(Shape<R, L>::T)
-k_fft_forward(const double *__restrict__ x, const double *__restrict__ y,
+k_fft_forward(const double *__restrict__ x, const YT *__restrict__ y,
               const R *__restrict__ sigk, cx<R> *__restrict__ spec, int n, int64_t n_pad,
               const cx<R> *__restrict__ tw, int npanels) {
   using S = Shape<R, L>;
@@ -310,8 +310,8 @@ k_fft_forward(const double *__restrict__ x, const double *__restrict__ y,
 #pragma unroll
         for (int r = 0; r < R1; r++) {
           const int t = j + r * (L / R1);
-          v[q][r] = mk(load_real<R, L, NEUMANN>(x, y, sigk, n, t, i, pol_stream),
-                       load_real<R, L, NEUMANN>(x, y, sigk, n, t, i + 1, pol_stream));
+          v[q][r] = mk(load_real<R, L, NEUMANN, YT>(x, y, sigk, n, t, i, pol_stream),
+                       load_real<R, L, NEUMANN, YT>(x, y, sigk, n, t, i + 1, pol_stream));
         }
       }
 #pragma unroll
@@ -355,13 +355,11 @@ k_fft_forward(const double *__restrict__ x, const double *__restrict__ y,
   }
 }
 
-// Inverse: half spectrum -> y (FP64), scaled by 1/L.  With AAO_FFT_DIRECT_OUT
-// the last Stockham pass (where j < Ns, so output index j + r Ns is time step
-// t) writes straight to global memory; otherwise the result goes through
-// shared memory and is written row by row (2C contiguous doubles per step).
-#ifndef AAO_FFT_DIRECT_OUT
-#define AAO_FFT_DIRECT_OUT 0
-#endif
+// Inverse: half spectrum -> y, scaled by 1/L.  The result goes through shared
+// memory and is written row by row (2C contiguous values per time step).  OT
+// is the stored type: double for the public entry points, float for the
+// preconditioned FGMRES basis of the mixed solver (the FP32 results are
+// stored exactly either way).
 template <int NK, int W, int T, typename CXT>
 __device__ __forceinline__ void prefetch_spec(const CXT *__restrict__ spec, int n, int64_t n_pad,
                                               int i0) {
@@ -375,9 +373,9 @@ __device__ __forceinline__ void prefetch_spec(const CXT *__restrict__ spec, int 
   }
 }
 
-template <typename R, int L>
+template <typename R, int L, typename OT>
 __global__ void __launch_bounds__(Shape<R, L>::T)
-k_fft_inverse(const cx<R> *__restrict__ spec, double *__restrict__ y, int n, int64_t n_pad,
+k_fft_inverse(const cx<R> *__restrict__ spec, OT *__restrict__ y, int n, int64_t n_pad,
               const cx<R> *__restrict__ tw, int npanels) {
   using S = Shape<R, L>;
   using PL = Passes<L>;
@@ -414,221 +412,9 @@ k_fft_inverse(const cx<R> *__restrict__ spec, double *__restrict__ y, int n, int
 #pragma unroll 8
     for (int idx = threadIdx.x; idx < L * W; idx += T) {
       const int t = idx / W, w = idx - t * W, i = i0 + w;
-      if (i < n) y[(size_t)t * n + i] = to_double<R>(scale * smr[2 * phys<C>(t, w >> 1) + (w & 1)]);
+      if (i < n) y[(size_t)t * n + i] = to_out<R, OT>(scale * smr[2 * phys<C>(t, w >> 1) + (w & 1)]);
     }
     __syncthreads();   // the work buffer is reused by the next panel
-  }
-}
-
-// ------------------------------------------------ pipelined persistent FFTs
-// The kernels above move their panel in one burst and then compute, so with
-// one or two CTAs per SM the DRAM is idle during the passes.  The persistent
-// variants below keep a second shared buffer: while a CTA transforms panel
-// p, cp.async (asynchronous global -> shared copies) bring in panel p + grid
-// so that the loads overlap the passes.
-
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  const int sz = valid ? 8 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  const int sz = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz)
-               : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-#ifndef AAO_FFT_PCAP32
-#define AAO_FFT_PCAP32 8192
-#endif
-#ifndef AAO_FFT_PCAP64
-#define AAO_FFT_PCAP64 4096
-#endif
-template <typename R> struct PCap;   // complex points of the work buffer
-template <> struct PCap<float> { static constexpr int V = AAO_FFT_PCAP32; };
-template <> struct PCap<double> { static constexpr int V = AAO_FFT_PCAP64; };
-
-template <typename R, int L> struct PShape {
-  static constexpr int C0 = PCap<R>::V / L;
-  static constexpr int C = C0 > 16 ? 16 : (C0 < 1 ? 1 : C0);
-  static constexpr int E = (L < 16) ? L : 16;
-  static constexpr int T = L * C / E;
-  static constexpr size_t WORK = ((size_t)(L + (L >> 4) + 1) * C * sizeof(cx<R>) + 15) & ~(size_t)15;
-  static constexpr size_t STAGE_F = (size_t)L * 2 * C * sizeof(double);          // raw FP64 rows
-  static constexpr size_t STAGE_I = (size_t)(L / 2 + 1) * 2 * C * sizeof(cx<R>);  // half spectrum
-  static constexpr size_t SMEM_F = WORK + STAGE_F;
-  static constexpr size_t SMEM_I = WORK + STAGE_I;
-};
-
-template <typename R, int L>
-__device__ __forceinline__ void stage_rows(double *stage, const double *__restrict__ x, int n,
-                                           int i0) {
-  using S = PShape<R, L>;
-  constexpr int W = 2 * S::C;
-  for (int q = threadIdx.x; q < L * W; q += S::T) {
-    const int t = q / W, w = q - t * W, i = i0 + w;
-    const bool ok = i < n;
-    cp_async8(&stage[q], ok ? &x[(size_t)t * n + i] : x, ok);
-  }
-  cp_commit();
-}
-
-template <typename R, int L>
-__global__ void __launch_bounds__(PShape<R, L>::T)
-k_fft_forward_pipe(const double *__restrict__ x, cx<R> *__restrict__ spec, int n, int64_t n_pad,
-                   const cx<R> *__restrict__ tw, int npanels) {
-  using S = PShape<R, L>;
-  using PL = Passes<L>;
-  constexpr int C = S::C, T = S::T, E = S::E, W = 2 * C;
-  constexpr int R1 = PL::R1 < 1 ? 1 : PL::R1;
-  constexpr int NB = E / R1;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
-  double *stage = reinterpret_cast<double *>(smraw + S::WORK);
-
-  int panel = blockIdx.x;
-  if (panel < npanels) stage_rows<R, L>(stage, x, n, panel * W);
-  for (; panel < npanels; panel += gridDim.x) {
-    const int i0 = panel * W;
-    cp_wait_all();
-    __syncthreads();
-    cx<R> v[NB][R1];
-#pragma unroll
-    for (int q = 0; q < NB; q++) {
-      const int b = threadIdx.x + q * T;
-      const int c = b % C, j = b / C;
-#pragma unroll
-      for (int r = 0; r < R1; r++) {
-        const int t = j + r * (L / R1);
-        const double2 d = *reinterpret_cast<const double2 *>(&stage[t * W + 2 * c]);
-        v[q][r] = mk(from_f64<R>(d.x), from_f64<R>(d.y));
-      }
-    }
-    __syncthreads();                       // stage free: prefetch the next panel
-    if (panel + (int)gridDim.x < npanels) stage_rows<R, L>(stage, x, n, (panel + gridDim.x) * W);
-#pragma unroll
-    for (int q = 0; q < NB; q++) {
-      const int b = threadIdx.x + q * T;
-      const int c = b % C, j = b / C;
-      dft<R, -1, R1>(v[q]);
-#pragma unroll
-      for (int r = 0; r < R1; r++) sm[phys<C>(j * R1 + r, c)] = v[q][r];
-    }
-    __syncthreads();
-    if constexpr (PL::NP > 1) {
-      int Ns = R1;
-#pragma unroll
-      for (int p = 1; p < PL::NP; p++) {
-        pass<R, L, C, 16, -1, T>(sm, Ns, tw);
-        Ns *= 16;
-      }
-    }
-    constexpr int NK = L / 2 + 1;
-    for (int idx = threadIdx.x; idx < NK * C; idx += T) {
-      const int k = idx / C, c = idx - k * C;
-      const cx<R> zk = sm[phys<C>(k, c)];
-      const cx<R> zm = sm[phys<C>((L - k) & (L - 1), c)];
-      const R hf = (R)0.5;
-      const cx<R> X = mk(hf * (zk.re + zm.re), hf * (zk.im - zm.im));
-      const cx<R> Y = mk(hf * (zk.im + zm.im), hf * (zm.re - zk.re));
-      const int i = i0 + 2 * c;
-      cx<R> *dst = spec + (size_t)k * n_pad + i;
-      if (i + 1 < n) {
-        dst[0] = X;
-        dst[1] = Y;
-      } else if (i < n) {
-        dst[0] = X;
-      }
-    }
-    __syncthreads();                       // work buffer reused by the next panel
-  }
-}
-
-template <typename R, int L>
-__device__ __forceinline__ void stage_spec(cx<R> *stage, const cx<R> *__restrict__ spec, int n,
-                                           int64_t n_pad, int i0) {
-  using S = PShape<R, L>;
-  constexpr int W = 2 * S::C;
-  constexpr int EPC = 16 / sizeof(cx<R>);   // complex per 16-byte copy
-  constexpr int CPR = W / EPC;               // copies per row
-  constexpr int NK = L / 2 + 1;
-  for (int q = threadIdx.x; q < NK * CPR; q += S::T) {
-    const int k = q / CPR, u = q - k * CPR, i = i0 + u * EPC;
-    const bool ok = i < n;                   // i < n <= n_pad: the 16 bytes lie in the row
-    cp_async16(&stage[k * W + u * EPC], ok ? &spec[(size_t)k * n_pad + i] : spec, ok);
-  }
-  cp_commit();
-}
-
-template <typename R, int L>
-__global__ void __launch_bounds__(PShape<R, L>::T)
-k_fft_inverse_pipe(const cx<R> *__restrict__ spec, double *__restrict__ y, int n, int64_t n_pad,
-                   const cx<R> *__restrict__ tw, int npanels) {
-  using S = PShape<R, L>;
-  using PL = Passes<L>;
-  constexpr int C = S::C, T = S::T, E = S::E, W = 2 * C;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
-  cx<R> *stage = reinterpret_cast<cx<R> *>(smraw + S::WORK);
-  constexpr int NK = L / 2 + 1;
-  constexpr int RL = (PL::NP <= 1) ? (L < 1 ? 1 : L) : 16;
-  constexpr int NB = E / RL;
-  const R scale = (R)1 / (R)L;
-
-  int panel = blockIdx.x;
-  if (panel < npanels) stage_spec<R, L>(stage, spec, n, n_pad, panel * W);
-  for (; panel < npanels; panel += gridDim.x) {
-    const int i0 = panel * W;
-    cp_wait_all();
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < NK * C; idx += T) {
-      const int k = idx / C, c = idx - k * C;
-      const int i = i0 + 2 * c;
-      cx<R> A = (i < n) ? stage[k * W + 2 * c] : mk((R)0, (R)0);
-      cx<R> B = (i + 1 < n) ? stage[k * W + 2 * c + 1] : mk((R)0, (R)0);
-      if (k == 0 || 2 * k == L) { A.im = (R)0; B.im = (R)0; }
-      sm[phys<C>(k, c)] = mk(A.re - B.im, A.im + B.re);
-      if (k > 0 && 2 * k < L) sm[phys<C>(L - k, c)] = mk(A.re + B.im, B.re - A.im);
-    }
-    __syncthreads();                       // stage free: prefetch the next panel
-    if (panel + (int)gridDim.x < npanels)
-      stage_spec<R, L>(stage, spec, n, n_pad, (panel + gridDim.x) * W);
-    int Ns = 1;
-    if constexpr (PL::NP > 1) {
-      pass<R, L, C, PL::R1, +1, T>(sm, 1, tw);
-      Ns = PL::R1;
-#pragma unroll
-      for (int p = 1; p < PL::NP - 1; p++) {
-        pass<R, L, C, 16, +1, T>(sm, Ns, tw);
-        Ns *= 16;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < NB; q++) {
-      const int b = threadIdx.x + q * T;
-      const int c = b % C, j = b / C;
-      cx<R> v[RL];
-#pragma unroll
-      for (int r = 0; r < RL; r++) v[r] = sm[phys<C>(j + r * (L / RL), c)];
-      if (Ns > 1) {
-        const int step = j * (L / (Ns * RL));
-#pragma unroll
-        for (int r = 1; r < RL; r++) v[r] = twiddle<R, +1>(v[r], tw[step * r]);
-      }
-      dft<R, +1, RL>(v);
-      const int i = i0 + 2 * c;
-#pragma unroll
-      for (int r = 0; r < RL; r++) {
-        const size_t o = (size_t)(j + r * Ns) * n + i;
-        if (i < n) y[o] = to_double<R>(scale * v[r].re);
-        if (i + 1 < n) y[o + 1] = to_double<R>(scale * v[r].im);
-      }
-    }
-    __syncthreads();                       // work buffer reused by the next panel
   }
 }
 

@@ -4,7 +4,8 @@ profilers (ncu) and quick timing.
     python -m paper_1810_00615_gb300.profile_case --op precond --n 4095 --ell 4096 \\
         --prec fp32 --reps 3
 
---op precond | neumann | matvec | solve.  Prints one line with the mean CUDA-
+--op precond | neumann | matvec | matvec_f32 | solve (matvec_f32: the product
+of an FP32 vector, as the mixed solver forms it).  Prints one line with the mean CUDA-
 event time per call.  Inputs are seeded standard-normal block vectors (or the
 8-mode heat initial data for `solve`).
 """
@@ -23,7 +24,7 @@ if ROOT not in sys.path:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", default="precond", choices=["precond", "neumann", "matvec", "solve"])
+    ap.add_argument("--op", default="precond", choices=["precond", "neumann", "matvec", "matvec_f32", "solve"])
     ap.add_argument("--n", type=int, default=4095)
     ap.add_argument("--ell", type=int, default=4096)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
@@ -44,6 +45,7 @@ def main(argv=None):
     g = torch.Generator(device="cuda").manual_seed(1)
     x = torch.randn(a.ell, a.n, dtype=torch.float64, device="cuda", generator=g)
     y = torch.empty_like(x)
+    x32 = x.float() if a.op == "matvec_f32" else None
     if a.op == "solve":
         b = s.build_rhs(torch.from_numpy(syn.heat_initial(a.n)).cuda())
 
@@ -54,6 +56,8 @@ def main(argv=None):
             s.neumann_apply(x, a.terms, out=y)
         elif a.op == "matvec":
             s.matvec(x, out=y)
+        elif a.op == "matvec_f32":
+            s.matvec_f32(x32, out=y)
         else:
             s.solve(b, restart=30, rtol=1e-10)
 
