@@ -279,6 +279,7 @@ namespace aao {
 // Workspace layout (offsets in bytes from ws, each 256-byte aligned).
 struct WsLayout {
   size_t spec = 0, spec_bytes = 0;
+  size_t inter = 0, inter_bytes = 0;   // two-kernel forward FFT scratch (0: none)
   size_t red = 0, red_bytes = 0;
   size_t vecs = 0;        // first FP64 vector (V_0 ...)
   size_t vec_bytes = 0;   // bytes per vector (rounded)
@@ -286,21 +287,34 @@ struct WsLayout {
 };
 WsLayout ws_layout(const Ctx &c, int restart);
 
+// Once per (kernel, device, block size, dynamic shared memory): opt the kernel
+// in to that much dynamic shared memory and count the CTAs the device holds
+// at once (SMs x resident CTAs per SM).  Later calls are a cached lookup, so
+// launch paths stay free of driver queries.
+cudaError_t kernel_setup(const void *kern, int threads, size_t smem, int *resident = nullptr);
+
 // ------------------------------------------------------------ launchers
 // All return cudaGetLastError() of the launch.
 // Time-axis FFTs: x (and, for a Neumann term, the previous iterate y) ->
 // half spectrum; half spectrum -> y.  One instantiation per precision.
+// `inter` (may be NULL: single-kernel transform) is the scratch of the
+// two-kernel forward transform, fft_inter_bytes_* bytes.
 cudaError_t fft_forward_f32(const Ctx &c, const double *x, const double *yprev, void *spec,
-                            cudaStream_t s);
-cudaError_t fft_inverse_f32(const Ctx &c, const void *spec, double *y, cudaStream_t s);
+                            cudaStream_t s, void *inter = nullptr);
+cudaError_t fft_inverse_f32(const Ctx &c, const void *spec, double *y, cudaStream_t s,
+                            void *inter = nullptr);
 cudaError_t fft_forward_f64(const Ctx &c, const double *x, const double *yprev, void *spec,
-                            cudaStream_t s);
-cudaError_t fft_inverse_f64(const Ctx &c, const void *spec, double *y, cudaStream_t s);
+                            cudaStream_t s, void *inter = nullptr);
+size_t fft_inter_bytes_f32(const Ctx &c);
+size_t fft_inter_bytes_f64(const Ctx &c);
+cudaError_t fft_inverse_f64(const Ctx &c, const void *spec, double *y, cudaStream_t s,
+                            void *inter = nullptr);
 // FP32 preconditioner with an FP32 Neumann iterate / FP32 result (the stored
 // preconditioned basis of the mixed solver).
 cudaError_t fft_forward_f32_yf(const Ctx &c, const double *x, const float *yprev, void *spec,
-                               cudaStream_t s);
-cudaError_t fft_inverse_f32_to_f32(const Ctx &c, const void *spec, float *y, cudaStream_t s);
+                               cudaStream_t s, void *inter = nullptr);
+cudaError_t fft_inverse_f32_to_f32(const Ctx &c, const void *spec, float *y, cudaStream_t s,
+                                   void *inter = nullptr);
 cudaError_t launch_tridiag(const Ctx &c, void *spec, int prec, int transpose,
                            cudaStream_t s);
 // y = A x (or A^T x); with `sub`, y = A x - sub (fused, for the shifted Arnoldi).

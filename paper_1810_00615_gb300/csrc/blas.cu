@@ -178,8 +178,11 @@ __device__ __forceinline__ double fx_to_f64(long long S, int emax) {
   return S ? __longlong_as_double((long long)bits) : 0.0;
 }
 
+#ifndef AAO_MVFX_MINB
+#define AAO_MVFX_MINB 1
+#endif
 template <int NB, bool TR, bool SUB>
-__global__ void __launch_bounds__(kMvCols)
+__global__ void __launch_bounds__(kMvCols, AAO_MVFX_MINB)
 k_matvec_fx(const float *__restrict__ x, double *__restrict__ y, int n, int ell, double mh,
             const double *__restrict__ beta, const double *__restrict__ sub) {
   constexpr int R = kFxRows, IN = R + NB - 1;   // input time steps per tile
@@ -195,16 +198,13 @@ k_matvec_fx(const float *__restrict__ x, double *__restrict__ y, int n, int ell,
     return (r < IN && col >= 0 && col < n && t >= 0 && t < ell)
                ? __ldg(&x[(int64_t)t * n + col]) : 0.0f;
   };
-  float zc[IN];
-#pragma unroll
-  for (int r = 0; r < IN; r++) zc[r] = ld(i, r);
-  // halo columns iw - 1 and iw + 32: lane l holds rows l and l + 32
+  // pass 1: the tile's largest exponent (the values land in L1 for pass 2)
   const float hl0 = ld(iw - 1, lane), hr0 = ld(iw + 32, lane);
   const float hl1 = (IN > 32) ? ld(iw - 1, lane + 32) : 0.0f;
   const float hr1 = (IN > 32) ? ld(iw + 32, lane + 32) : 0.0f;
   int em = max(max(f32_exp(hl0), f32_exp(hr0)), max(f32_exp(hl1), f32_exp(hr1)));
-#pragma unroll
-  for (int r = 0; r < IN; r++) em = max(em, f32_exp(zc[r]));
+#pragma unroll 8
+  for (int r = 0; r < IN; r++) em = max(em, f32_exp(ld(i, r)));
   em = (int)__reduce_max_sync(0xffffffffu, (unsigned)em);
   const int t_lo = c0, t_hi = min(ell, c0 + R);
   if (em == 255) {                              // an inf or NaN in the tile
@@ -215,32 +215,54 @@ k_matvec_fx(const float *__restrict__ x, double *__restrict__ y, int n, int ell,
   const long long XL0 = fx_from_f32(hl0, em), XR0 = fx_from_f32(hr0, em);
   const long long XL1 = fx_from_f32(hl1, em), XR1 = fx_from_f32(hr1, em);
   long long q1 = 0, q2 = 0;                     // q of the previous one or two rows walked
+  // pass 2 walks the rows; x and the subtrahend are fetched kPre rows ahead
+  // so that their latency hides behind the integer work of the rows between
+  constexpr int kPre = 4;
+  float zpre[kPre];
+  double vpre[kPre];
+  auto ld_sub = [&](int k) -> double {
+    if (!SUB || k < NB - 1 || k >= IN) return 0.0;
+    const int t = trow(TR ? IN - 1 - k : k);
+    return (i < n && t < ell) ? __ldg(&sub[(int64_t)t * n + i]) : 0.0;
+  };
+  auto ld_z = [&](int k) -> float { return k < IN ? ld(i, TR ? IN - 1 - k : k) : 0.0f; };
 #pragma unroll
-  for (int k = 0; k < IN; k++) {
-    const int r = TR ? IN - 1 - k : k;
-    const long long X = fx_from_f32(zc[r], em);
-    long long Xl = __shfl_up_sync(0xffffffffu, X, 1);
-    long long Xr = __shfl_down_sync(0xffffffffu, X, 1);
-    const long long hl = __shfl_sync(0xffffffffu, r < 32 ? XL0 : XL1, r & 31);
-    const long long hr = __shfl_sync(0xffffffffu, r < 32 ? XR0 : XR1, r & 31);
-    if (lane == 0) Xl = hl;
-    if (lane == 31) Xr = hr;
-    const long long P = Xl + Xr;
-    const long long q = 4 * X + P;
-    if (k >= NB - 1) {
+  for (int k = 0; k < kPre; k++) { zpre[k] = ld_z(k); vpre[k] = ld_sub(k); }
+  // unrolled by the prefetch depth only: a fully unrolled walk is tens of KB
+  // of code and stalls on instruction fetch
+#pragma unroll 1
+  for (int kb = 0; kb < IN; kb += kPre) {
+#pragma unroll
+    for (int u = 0; u < kPre; u++) {
+      const int k = kb + u;
+      const float zk = zpre[u];
+      const double vk = vpre[u];
+      zpre[u] = ld_z(k + kPre);
+      vpre[u] = ld_sub(k + kPre);
+      const int r = TR ? IN - 1 - k : k;
+      const long long X = fx_from_f32(zk, em);
+      long long Xl = __shfl_up_sync(0xffffffffu, X, 1);
+      long long Xr = __shfl_down_sync(0xffffffffu, X, 1);
+      const int src = r & 31;
+      const long long hl = __shfl_sync(0xffffffffu, r < 32 ? XL0 : XL1, src);
+      const long long hr = __shfl_sync(0xffffffffu, r < 32 ? XR0 : XR1, src);
+      if (lane == 0) Xl = hl;
+      if (lane == 31) Xr = hr;
+      const long long P = Xl + Xr;
+      const long long q = 4 * X + P;
       const int t = trow(r);
-      if (i < n && t < ell) {
+      if (k < IN && k >= NB - 1 && i < n && t < ell) {
         const long long sm = (NB == 2) ? q - q1 : q - 2 * q1 + q2;
         const long long sk = 2 * X - P;
         const double bt = __ldg(&beta[t]);
         const double skd = fx_to_f64(sk, em), smd = fx_to_f64(sm, em);
         const int64_t o = (int64_t)t * n + i;
-        double acc = SUB ? fma(bt, skd, -__ldg(&sub[o])) : bt * skd;
+        const double acc = SUB ? fma(bt, skd, -vk) : bt * skd;
         y[o] = fma(mh, smd, acc);
       }
+      q2 = q1;
+      q1 = q;
     }
-    q2 = q1;
-    q1 = q;
   }
 }
 

@@ -1,5 +1,9 @@
 // C ABI of the all-at-once solver: context, per-frequency symbols, the
 // preconditioner applies, the matvec and the flexible GMRES driver.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <complex>
 #include <cmath>
 #include <cstdio>
@@ -394,11 +398,47 @@ cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
 }  // namespace
 
 namespace aao {
+cudaError_t kernel_setup(const void *kern, int threads, size_t smem, int *resident) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  // the opt-in is one value per function and device: keep the largest set
+  static std::map<std::pair<const void *, int>, size_t> optin;
+  static std::map<std::tuple<const void *, int, int, size_t>, int> grid;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t &have = optin[std::make_pair(kern, dev)];
+  if (smem > have || have == 0) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) { cudaGetLastError(); return e; }
+    have = smem > have ? smem : have;
+  }
+  const auto key = std::make_tuple(kern, dev, threads, smem);
+  auto it = grid.find(key);
+  if (it == grid.end()) {
+    int sms = 1, per = 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 1;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess ||
+        per < 1) {
+      cudaGetLastError();
+      per = 1;
+    }
+    it = grid.emplace(key, sms * per).first;
+  }
+  if (resident) *resident = it->second;
+  return cudaSuccess;
+}
+
 WsLayout ws_layout(const Ctx &c, int restart) {
   WsLayout L;
   L.spec = 0;
   L.spec_bytes = round_up((size_t)c.nk * (size_t)c.n_pad * sizeof(cx<double>), kAlign);
-  L.red = L.spec + L.spec_bytes;
+  L.inter = L.spec + L.spec_bytes;
+  L.inter_bytes = round_up(std::max(fft_inter_bytes_f32(c), fft_inter_bytes_f64(c)), kAlign);
+  L.red = L.inter + L.inter_bytes;
   L.red_bytes = round_up((size_t)(kPartials + kSmall) * sizeof(double), kAlign);
   L.vecs = L.red + L.red_bytes;
   L.vec_bytes = round_up((size_t)c.N * sizeof(double), kAlign);
@@ -426,19 +466,22 @@ int check_ws(const Ctx &c, int restart) {
 template <typename YT>
 cudaError_t precond_once(Ctx &c, const double *x, const YT *yprev, YT *y, int tr,
                          cudaStream_t s) {
-  void *spec = c.ws + aao::ws_layout(c, 0).spec;
+  const aao::WsLayout L = aao::ws_layout(c, 0);
+  void *spec = c.ws + L.spec;
+  void *inter = L.inter_bytes ? c.ws + L.inter : nullptr;
   const bool f32 = c.prec == AAO_PREC_FP32;
   cudaError_t e = run(c, AAO_K_FFT_FORWARD, s, [&] {
-    if constexpr (sizeof(YT) == 4) return aao::fft_forward_f32_yf(c, x, yprev, spec, s);
-    else return f32 ? aao::fft_forward_f32(c, x, yprev, spec, s)
-                    : aao::fft_forward_f64(c, x, yprev, spec, s);
+    if constexpr (sizeof(YT) == 4) return aao::fft_forward_f32_yf(c, x, yprev, spec, s, inter);
+    else return f32 ? aao::fft_forward_f32(c, x, yprev, spec, s, inter)
+                    : aao::fft_forward_f64(c, x, yprev, spec, s, inter);
   });
   if (e != cudaSuccess) return e;
   e = run(c, AAO_K_TRIDIAG, s, [&] { return aao::launch_tridiag(c, spec, c.prec, tr, s); });
   if (e != cudaSuccess) return e;
   return run(c, AAO_K_FFT_INVERSE, s, [&] {
-    if constexpr (sizeof(YT) == 4) return aao::fft_inverse_f32_to_f32(c, spec, y, s);
-    else return f32 ? aao::fft_inverse_f32(c, spec, y, s) : aao::fft_inverse_f64(c, spec, y, s);
+    if constexpr (sizeof(YT) == 4) return aao::fft_inverse_f32_to_f32(c, spec, y, s, inter);
+    else return f32 ? aao::fft_inverse_f32(c, spec, y, s, inter)
+                    : aao::fft_inverse_f64(c, spec, y, s, inter);
   });
 }
 

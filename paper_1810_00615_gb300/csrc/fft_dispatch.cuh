@@ -6,37 +6,60 @@ namespace aao {
 namespace fft {
 
 // Persistent grid: as many CTAs as fit on the device at once, capped by the
-// panel count.
+// panel count (the dynamic shared-memory opt-in happens in the same cached
+// setup).  Returns 0 when the kernel cannot be set up.
 template <class K>
 static int persistent_grid(K kern, int threads, size_t smem, int npanels) {
-  int dev = 0, sms = 1, per = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess ||
-      per < 1)
-    per = 1;
-  const int g = sms * per;
+  int g = 0;
+  if (kernel_setup((const void *)kern, threads, smem, &g) != cudaSuccess) return 0;
   return g < npanels ? g : npanels;
+}
+
+#ifndef AAO_FFT_SPLIT
+#define AAO_FFT_SPLIT 1
+#endif
+
+// Bytes of the panel-major intermediate of the two-kernel forward transform
+// (0 where the single kernel is used).
+template <typename R, int L>
+static size_t inter_bytes_l(int64_t n) {
+  if (!(AAO_FFT_SPLIT && Split<R, L>::OK)) return 0;
+  const int W = 2 * Shape<R, L>::C;
+  return (size_t)((n + W - 1) / W) * Split<R, L>::PANEL;
 }
 
 template <typename R, int L, typename YT>
 static cudaError_t run_forward(int64_t n, int64_t n_pad, const double *x, const YT *y,
-                               const R *sigk, cx<R> *spec, const cx<R> *tw, cudaStream_t s) {
+                               const R *sigk, cx<R> *spec, const cx<R> *tw, cudaStream_t s,
+                               void *inter) {
   using S = Shape<R, L>;
   const int W = 2 * S::C;
   const int np = (int)((n + W - 1) / W);
-  cudaError_t e;
+  if constexpr (AAO_FFT_SPLIT && Split<R, L>::OK) {
+    if (inter) {
+      const int ncx = np * S::C;
+      const dim3 g1((unsigned)((ncx + kRowThreads - 1) / kRowThreads), (unsigned)Split<R, L>::LR);
+      cx<R> *ip = static_cast<cx<R> *>(inter);
+      if (y) k_fft_forward_rows<R, L, true, YT><<<g1, kRowThreads, 0, s>>>(x, y, sigk, ip, (int)n, ncx);
+      else k_fft_forward_rows<R, L, false, double><<<g1, kRowThreads, 0, s>>>(x, nullptr, sigk, ip, (int)n, ncx);
+      note_launch();
+      auto kern = k_fft_forward_panels<R, L>;
+      const int g = persistent_grid(kern, S::T, S::SMEM, np);
+      if (g <= 0) return cudaErrorInvalidConfiguration;
+      kern<<<g, S::T, S::SMEM, s>>>(ip, spec, (int)n, n_pad, tw, np);
+      note_launch();
+      return cudaGetLastError();
+    }
+  }
   if (y) {
     auto kern = k_fft_forward<R, L, true, YT>;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
-    if (e != cudaSuccess) { cudaGetLastError(); return e; }
     const int g = persistent_grid(kern, S::T, S::SMEM, np);
+    if (g <= 0) return cudaErrorInvalidConfiguration;
     kern<<<g, S::T, S::SMEM, s>>>(x, y, sigk, spec, (int)n, n_pad, tw, np);
   } else {
     auto kern = k_fft_forward<R, L, false, double>;   // no iterate: one instantiation
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
-    if (e != cudaSuccess) { cudaGetLastError(); return e; }
     const int g = persistent_grid(kern, S::T, S::SMEM, np);
+    if (g <= 0) return cudaErrorInvalidConfiguration;
     kern<<<g, S::T, S::SMEM, s>>>(x, nullptr, nullptr, spec, (int)n, n_pad, tw, np);
   }
   note_launch();
@@ -45,15 +68,28 @@ static cudaError_t run_forward(int64_t n, int64_t n_pad, const double *x, const 
 
 template <typename R, int L, typename OT>
 static cudaError_t run_inverse(int64_t n, int64_t n_pad, const cx<R> *spec, OT *y,
-                               const cx<R> *tw, cudaStream_t s) {
+                               const cx<R> *tw, cudaStream_t s, void *inter) {
   using S = Shape<R, L>;
   const int W = 2 * S::C;
   const int np = (int)((n + W - 1) / W);
+  if constexpr (AAO_FFT_SPLIT && Split<R, L>::OK) {
+    if (inter) {
+      cx<R> *ip = static_cast<cx<R> *>(inter);
+      auto kern = k_fft_inverse_panels<R, L>;
+      const int g = persistent_grid(kern, S::T, S::SMEM, np);
+      if (g <= 0) return cudaErrorInvalidConfiguration;
+      kern<<<g, S::T, S::SMEM, s>>>(spec, ip, (int)n, n_pad, tw, np);
+      note_launch();
+      const int ncx = np * S::C;
+      const dim3 g2((unsigned)((ncx + kRowThreads - 1) / kRowThreads), (unsigned)(L / 16));
+      k_fft_inverse_rows<R, L, OT><<<g2, kRowThreads, 0, s>>>(ip, y, (int)n, ncx, tw);
+      note_launch();
+      return cudaGetLastError();
+    }
+  }
   auto kern = k_fft_inverse<R, L, OT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)S::SMEM);
-  if (e != cudaSuccess) { cudaGetLastError(); return e; }
   const int g = persistent_grid(kern, S::T, S::SMEM, np);
+  if (g <= 0) return cudaErrorInvalidConfiguration;
   kern<<<g, S::T, S::SMEM, s>>>(spec, y, (int)n, n_pad, tw, np);
   note_launch();
   return cudaGetLastError();
@@ -64,20 +100,31 @@ static cudaError_t run_inverse(int64_t n, int64_t n_pad, const cx<R> *spec, OT *
 
 template <typename R, typename YT>
 cudaError_t forward_any(int64_t ell, int64_t n, int64_t n_pad, const double *x, const YT *y,
-                        const R *sigk, cx<R> *spec, const cx<R> *tw, cudaStream_t s) {
+                        const R *sigk, cx<R> *spec, const cx<R> *tw, cudaStream_t s,
+                        void *inter) {
   switch (ell) {
-#define AAO_F(L) case L: return run_forward<R, L, YT>(n, n_pad, x, y, sigk, spec, tw, s);
+#define AAO_F(L) case L: return run_forward<R, L, YT>(n, n_pad, x, y, sigk, spec, tw, s, inter);
     AAO_FFT_CASES(AAO_F)
 #undef AAO_F
     default: return cudaErrorInvalidValue;
   }
 }
 
+template <typename R>
+size_t inter_bytes_any(int64_t ell, int64_t n) {
+  switch (ell) {
+#define AAO_B(L) case L: return inter_bytes_l<R, L>(n);
+    AAO_FFT_CASES(AAO_B)
+#undef AAO_B
+    default: return 0;
+  }
+}
+
 template <typename R, typename OT>
 cudaError_t inverse_any(int64_t ell, int64_t n, int64_t n_pad, const cx<R> *spec, OT *y,
-                        const cx<R> *tw, cudaStream_t s) {
+                        const cx<R> *tw, cudaStream_t s, void *inter) {
   switch (ell) {
-#define AAO_I(L) case L: return run_inverse<R, L, OT>(n, n_pad, spec, y, tw, s);
+#define AAO_I(L) case L: return run_inverse<R, L, OT>(n, n_pad, spec, y, tw, s, inter);
     AAO_FFT_CASES(AAO_I)
 #undef AAO_I
     default: return cudaErrorInvalidValue;

@@ -3,21 +3,24 @@
 
 namespace aao {
 cudaError_t fft_forward_f32(const Ctx &c, const double *x, const double *y, void *spec,
-                            cudaStream_t s) {
+                            cudaStream_t s, void *inter) {
   return fft::forward_any<float, double>(c.ell, c.n, c.n_pad, x, y, c.sigk32,
-                                 static_cast<cx<float> *>(spec), c.tw32, s);
+                                         static_cast<cx<float> *>(spec), c.tw32, s, inter);
 }
-cudaError_t fft_inverse_f32(const Ctx &c, const void *spec, double *y, cudaStream_t s) {
+cudaError_t fft_inverse_f32(const Ctx &c, const void *spec, double *y, cudaStream_t s,
+                            void *inter) {
   return fft::inverse_any<float, double>(c.ell, c.n, c.n_pad,
-                                         static_cast<const cx<float> *>(spec), y, c.tw32, s);
+                                         static_cast<const cx<float> *>(spec), y, c.tw32, s, inter);
 }
 cudaError_t fft_forward_f32_yf(const Ctx &c, const double *x, const float *y, void *spec,
-                               cudaStream_t s) {
+                               cudaStream_t s, void *inter) {
   return fft::forward_any<float, float>(c.ell, c.n, c.n_pad, x, y, c.sigk32,
-                                        static_cast<cx<float> *>(spec), c.tw32, s);
+                                        static_cast<cx<float> *>(spec), c.tw32, s, inter);
 }
-cudaError_t fft_inverse_f32_to_f32(const Ctx &c, const void *spec, float *y, cudaStream_t s) {
+size_t fft_inter_bytes_f32(const Ctx &c) { return fft::inter_bytes_any<float>(c.ell, c.n); }
+cudaError_t fft_inverse_f32_to_f32(const Ctx &c, const void *spec, float *y, cudaStream_t s,
+                                   void *inter) {
   return fft::inverse_any<float, float>(c.ell, c.n, c.n_pad,
-                                        static_cast<const cx<float> *>(spec), y, c.tw32, s);
+                                        static_cast<const cx<float> *>(spec), y, c.tw32, s, inter);
 }
 }  // namespace aao

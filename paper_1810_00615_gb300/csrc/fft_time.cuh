@@ -355,6 +355,186 @@ k_fft_forward(const double *__restrict__ x, const YT *__restrict__ y,
   }
 }
 
+// ------------------------------------------------ forward in two kernels
+// The single kernel above reads its panel as 2C doubles per time step, a
+// 32-64 byte piece of each of L rows far apart in memory, and that pattern
+// holds DRAM well below its streaming rate; its passes then run while the
+// DRAM idles.  For L >= 256 the forward transform is split instead:
+//
+//  rows   the first Stockham pass (radix R1, Ns = 1: no twiddles) needs time
+//         steps j + r L/R1 of a column, r < R1.  A CTA takes one j and 256
+//         complex columns, so it reads R1 row segments of 512 doubles each;
+//         it writes its R1 outputs per column into a panel-major intermediate
+//         laid out exactly like the panel kernel's shared-memory buffer.
+//  panels a persistent CTA copies one panel of that intermediate (one
+//         contiguous block, resident in L2) into shared memory with 16-byte
+//         asynchronous copies, runs passes 2..NP and writes the half spectrum.
+constexpr int kRowThreads = 256;
+
+template <typename R, int L> struct Split {
+  static constexpr bool OK = Passes<L>::NP >= 2;
+  static constexpr int R1 = Passes<L>::R1;
+  static constexpr int LR = L / (R1 < 1 ? 1 : R1);                    // butterflies per column
+  static constexpr size_t PANEL = Shape<R, L>::WORK;                   // bytes per panel
+};
+
+template <typename R, int L, bool NEUMANN, typename YT>
+__global__ void __launch_bounds__(kRowThreads)
+k_fft_forward_rows(const double *__restrict__ x, const YT *__restrict__ y,
+                   const R *__restrict__ sigk, cx<R> *__restrict__ inter, int n, int ncx) {
+  using S = Shape<R, L>;
+  using P = Split<R, L>;
+  constexpr int C = S::C, R1 = P::R1;
+  const int j = blockIdx.y;                                   // butterfly (time offset)
+  const int cg = blockIdx.x * kRowThreads + threadIdx.x;      // complex column
+  if (cg >= ncx) return;
+  const int i = 2 * cg;
+  const unsigned long long pol_stream = l2_evict_first(), pol_keep = l2_evict_last();
+  cx<R> v[R1];
+#pragma unroll
+  for (int r = 0; r < R1; r++) {
+    const int t = j + r * P::LR;
+    v[r] = mk(load_real<R, L, NEUMANN, YT>(x, y, sigk, n, t, i, pol_stream),
+              load_real<R, L, NEUMANN, YT>(x, y, sigk, n, t, i + 1, pol_stream));
+  }
+  dft<R, -1, R1>(v);
+  cx<R> *dst = reinterpret_cast<cx<R> *>(reinterpret_cast<unsigned char *>(inter) +
+                                         (size_t)(cg / C) * P::PANEL) + (cg % C);
+#pragma unroll
+  for (int r = 0; r < R1; r++) st_hint(dst + phys<C>(j * R1 + r, 0), v[r], pol_keep);
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <typename R, int L>
+__global__ void __launch_bounds__(Shape<R, L>::T)
+k_fft_forward_panels(const cx<R> *__restrict__ inter, cx<R> *__restrict__ spec, int n,
+                     int64_t n_pad, const cx<R> *__restrict__ tw, int npanels) {
+  using S = Shape<R, L>;
+  using PL = Passes<L>;
+  using P = Split<R, L>;
+  constexpr int C = S::C, T = S::T, W = 2 * C;
+  constexpr int CHUNKS = (int)(P::PANEL / 16);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
+  const unsigned long long pol_keep = l2_evict_last();
+  for (int panel = blockIdx.x; panel < npanels; panel += gridDim.x) {
+    const unsigned char *src = reinterpret_cast<const unsigned char *>(inter) + (size_t)panel * P::PANEL;
+    for (int q = threadIdx.x; q < CHUNKS; q += T) cp_async16(smraw + 16 * q, src + 16 * q);
+    cp_async_wait_all();
+    __syncthreads();
+    int Ns = P::R1;
+#pragma unroll
+    for (int p = 1; p < PL::NP; p++) {
+      pass<R, L, C, 16, -1, T>(sm, Ns, tw);
+      Ns *= 16;
+    }
+    const int i0 = panel * W;
+    constexpr int NK = L / 2 + 1;
+    for (int idx = threadIdx.x; idx < NK * C; idx += T) {
+      const int k = idx / C, c = idx - k * C;
+      const cx<R> zk = sm[phys<C>(k, c)];
+      const cx<R> zm = sm[phys<C>((L - k) & (L - 1), c)];
+      const R hf = (R)0.5;
+      const cx<R> X = mk(hf * (zk.re + zm.re), hf * (zk.im - zm.im));
+      const cx<R> Y = mk(hf * (zk.im + zm.im), hf * (zm.re - zk.re));
+      const int i = i0 + 2 * c;
+      cx<R> *dst = spec + (size_t)k * n_pad + i;
+      if (i + 1 < n) {
+        st_hint(dst, X, pol_keep);
+        st_hint(dst + 1, Y, pol_keep);
+      } else if (i < n) {
+        st_hint(dst, X, pol_keep);
+      }
+    }
+    __syncthreads();   // the work buffer is reused by the next panel
+  }
+}
+
+// ------------------------------------------------ inverse in two kernels
+// Mirror of the forward split (L >= 256): a persistent panel kernel loads the
+// half spectrum of its panel, extends it to the Hermitian full spectrum, runs
+// all Stockham passes but the last and stores its shared-memory image to the
+// panel-major intermediate; a row kernel runs the last radix-16 pass (whose
+// butterfly j yields time steps j + r L/16) and writes those rows of y as
+// contiguous segments of 512 columns.
+template <typename R, int L>
+__global__ void __launch_bounds__(Shape<R, L>::T)
+k_fft_inverse_panels(const cx<R> *__restrict__ spec, cx<R> *__restrict__ inter, int n,
+                     int64_t n_pad, const cx<R> *__restrict__ tw, int npanels) {
+  using S = Shape<R, L>;
+  using PL = Passes<L>;
+  using P = Split<R, L>;
+  constexpr int C = S::C, T = S::T, W = 2 * C;
+  constexpr int CHUNKS = (int)(P::PANEL / 16);
+  constexpr int NK = L / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
+  const unsigned long long pol_done = l2_evict_first(), pol_keep = l2_evict_last();
+  for (int panel = blockIdx.x; panel < npanels; panel += gridDim.x) {
+    const int i0 = panel * W;
+    for (int idx = threadIdx.x; idx < NK * C; idx += T) {
+      const int k = idx / C, c = idx - k * C;
+      const int i = i0 + 2 * c;
+      const cx<R> *src = spec + (size_t)k * n_pad + i;
+      cx<R> A = mk((R)0, (R)0), B = mk((R)0, (R)0);
+      if (i < n) A = ld_hintc(src, pol_done);
+      if (i + 1 < n) B = ld_hintc(src + 1, pol_done);
+      if (k == 0 || 2 * k == L) { A.im = (R)0; B.im = (R)0; }
+      sm[phys<C>(k, c)] = mk(A.re - B.im, A.im + B.re);
+      if (k > 0 && 2 * k < L) sm[phys<C>(L - k, c)] = mk(A.re + B.im, B.re - A.im);
+    }
+    __syncthreads();
+    pass<R, L, C, P::R1, +1, T>(sm, 1, tw);
+    int Ns = P::R1;
+#pragma unroll
+    for (int p = 1; p < PL::NP - 1; p++) {
+      pass<R, L, C, 16, +1, T>(sm, Ns, tw);
+      Ns *= 16;
+    }
+    float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(inter) +
+                                             (size_t)panel * P::PANEL);
+    const float4 *srcs = reinterpret_cast<const float4 *>(smraw);
+    for (int q = threadIdx.x; q < CHUNKS; q += T) st_hint4(dst + q, srcs[q], pol_keep);
+    __syncthreads();   // the work buffer is reused by the next panel
+  }
+}
+
+template <typename R, int L, typename OT>
+__global__ void __launch_bounds__(kRowThreads)
+k_fft_inverse_rows(const cx<R> *__restrict__ inter, OT *__restrict__ y, int n, int ncx,
+                   const cx<R> *__restrict__ tw) {
+  using S = Shape<R, L>;
+  using P = Split<R, L>;
+  constexpr int C = S::C, NS = L / 16;                        // last pass: radix 16, Ns = L/16
+  const int j = blockIdx.y;                                   // butterfly = first time step
+  const int cg = blockIdx.x * kRowThreads + threadIdx.x;
+  if (cg >= ncx) return;
+  const unsigned long long pol_done = l2_evict_first();
+  const cx<R> *src = reinterpret_cast<const cx<R> *>(reinterpret_cast<const unsigned char *>(inter) +
+                                                     (size_t)(cg / C) * P::PANEL) + (cg % C);
+  cx<R> v[16];
+#pragma unroll
+  for (int r = 0; r < 16; r++) v[r] = ld_hintc(src + phys<C>(j + r * NS, 0), pol_done);
+#pragma unroll
+  for (int r = 1; r < 16; r++) v[r] = twiddle<R, +1>(v[r], tw[j * r]);
+  dft<R, +1, 16>(v);
+  const R scale = (R)1 / (R)L;
+  const int i = 2 * cg;
+#pragma unroll
+  for (int r = 0; r < 16; r++) {
+    const size_t o = (size_t)(j + r * NS) * n + i;
+    if (i < n) y[o] = to_out<R, OT>(scale * v[r].re);
+    if (i + 1 < n) y[o + 1] = to_out<R, OT>(scale * v[r].im);
+  }
+}
+
 // Inverse: half spectrum -> y, scaled by 1/L.  The result goes through shared
 // memory and is written row by row (2C contiguous values per time step).  OT
 // is the stored type: double for the public entry points, float for the

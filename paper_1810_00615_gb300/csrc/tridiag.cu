@@ -558,8 +558,7 @@ static cudaError_t run_tridiag_cluster(const Ctx &c, void *spec, const void *tab
   off += (size_t)T;
   const size_t smem = ((off * sizeof(cx<R>) + 15) & ~(size_t)15) + (size_t)T * CH * sizeof(cx<R>);
   auto kern = k_tridiag_cluster<R, CH>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = kernel_setup((const void *)kern, T, smem);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(c.nk * S), 1, 1);
@@ -590,8 +589,7 @@ static cudaError_t run_tridiag_rec(const Ctx &c, void *spec, const void *tab, in
   off += (size_t)P;
   const size_t smem = ((off * sizeof(cx<R>) + 15) & ~(size_t)15) + (size_t)P * CH * sizeof(cx<R>);
   auto kern = k_tridiag_rec<R, CH>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = kernel_setup((const void *)kern, P, smem);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
   const int4 lo = make_int4(lsz[0], lsz[1], lsz[2], lsz[3]);
   const int2 hi = make_int2(lsz[4], lsz[5]);
@@ -611,8 +609,7 @@ static cudaError_t run_tridiag(const Ctx &c, void *spec, const void *tab, int P,
   const bool stage = stage_smem <= 200 * 1024;
   const size_t smem = stage ? stage_smem : base_smem;
   auto kern = stage ? k_tridiag<R, CH, true> : k_tridiag<R, CH, false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = kernel_setup((const void *)kern, P, smem);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
   kern<<<(unsigned)c.nk, P, smem, s>>>(static_cast<cx<R> *>(spec), (int)c.n, c.n_pad,
                                        static_cast<const TriTab<R, CH> *>(tab), conj);
