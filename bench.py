@@ -164,18 +164,23 @@ def _blas_threads():
         return _cpu_cores()
 
 
-def _traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summaries
-    (a line 'dram_bytes_per_launch: <kernel> <bytes>'), else None."""
+def _profile_value(key, kernel):
+    """A per-launch figure from the committed ncu summaries (a line
+    '<key>: <kernel> <value>'), else None."""
     import glob
     import re
     for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         with open(f) as fh:
             for line in fh:
-                m = re.match(r"dram_bytes_per_launch:\s*(\S+)\s+([0-9.eE+]+)", line.strip())
-                if m and m.group(1) == kernel:
-                    return float(m.group(2))
+                m = re.match(r"(\S+):\s*(\S+)\s+([0-9.eE+]+)", line.strip())
+                if m and m.group(1) == key and m.group(2) == kernel:
+                    return float(m.group(3))
     return None
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summaries."""
+    return _profile_value("dram_bytes_per_launch", kernel)
 
 
 def _timed(fn, reps, stream):
@@ -473,30 +478,44 @@ def run_gpu(args):
         roofline = {"bound": "hbm", "kernel": dom, "achieved": pk["GB_s"], "peak": hbm_peak,
                     "unit": "GB/s", "frac": pk["frac"], "traffic": _traffic(dom),
                     "peak_kind": peak_kind}
+    elif dom == "matvec":
+        # Four of the six matvecs of a solve are the fixed-point product
+        # w = A z - v of the FP32 basis (the other two, the residuals, run the
+        # same kernel on FP64 x).  Integer-ALU bound: the GB300 ALU pipe issues
+        # 64 lanes per clock per SM; achieved = ALU-pipe instructions per
+        # launch (ncu, committed summary) / the launch's event time here.
+        z32 = xs[0].float()
+        mv_reps = 20
+        ts = []
+        for k in range(mv_reps + 3):
+            flush.fill_(float(k))
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            solver.matvec_f32(z32, sub=xs[1], out=ys[0])
+            a1.record(stream)
+            torch.cuda.synchronize()
+            if k >= 3:
+                ts.append(a0.elapsed_time(a1) * 1e-3)
+        mv_s = float(np.median(ts))
+        alu = _profile_value("alu_inst_per_launch", "matvec_f32")
+        alu_peak = 152 * 64 * sm_mhz * 1e6 / 1e9                 # Gop/s
+        mv_bytes = Nel * (4 + 8 + 8)                              # z (FP32), v, w
+        achieved = alu / mv_s / 1e9 if alu else None
+        roofline = {"bound": "alu", "kernel": "matvec_f32: w = A z - v, fixed point",
+                    "achieved": round(achieved, 1) if achieved else None,
+                    "peak": round(alu_peak, 1), "unit": "Gop/s",
+                    "frac": round(achieved / alu_peak, 4) if achieved else None,
+                    "traffic": _traffic("matvec_f32"), "us": round(mv_s * 1e6, 1),
+                    "algorithmic_bytes": mv_bytes,
+                    "hbm_GB_s": round(mv_bytes / mv_s / 1e9, 1),
+                    "hbm_frac": round(mv_bytes / mv_s / 1e9 / hbm_peak, 3),
+                    "note": "integer ALU pipe bound; peak = 152 SMs x 64 ALU lanes/clk x "
+                            "sampled SM clock; achieved = ncu ALU-pipe instructions per "
+                            "launch / event time"}
     else:
-        # FP64 kernels of the outer loop are bound by the FP64 pipe: 2 FP64
-        # instructions per clock per SM (measured), 152 SMs.  Algorithmic
-        # work per element of the fused matvec A z - v: 6 FP64 instructions
-        # (2 adds, 1 mul, 3 fma) = 9 flops counting an fma as 2.
-        t_ms, nl = prof[dom]
-        avg_s = t_ms / max(nl, 1) / 1e3
-        fp64_peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12       # TFLOP/s with every op an FMA
-        inst_peak = 152 * 2 * sm_mhz * 1e6                   # FP64 instructions / s
-        per_elt = {"matvec": (9, 6)}.get(dom)
-        if per_elt:
-            fl, ins = per_elt
-            achieved = fl * Nel / avg_s / 1e12
-            roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4),
-                        "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
-                        "frac": round(achieved / fp64_peak, 4), "traffic": _traffic(dom),
-                        "fp64_issue_frac": round(ins * Nel / avg_s / inst_peak, 4),
-                        "note": "FP64 pipe bound; peak = 152 SMs x 2 FP64 FMA/clk x 2 flops x "
-                                "sampled SM clock; this kernel's mix (3 of 6 FP64 "
-                                "instructions are FMAs) caps frac at 0.75"}
-        else:
-            roofline = {"bound": "alu", "kernel": dom, "achieved": None,
-                        "peak": round(fp64_peak, 4), "unit": "TFLOP/s", "frac": None,
-                        "traffic": None}
+        roofline = {"bound": "alu", "kernel": dom, "achieved": None, "peak": None,
+                    "unit": "TFLOP/s", "frac": None, "traffic": _traffic(dom),
+                    "note": "FP64 pipe bound Arnoldi kernel"}
 
     # ---- end to end through the C ABI with host buffers (u0 in, U out)
     u0_h = torch.from_numpy(u0).pin_memory()

@@ -138,21 +138,27 @@ int aao_neumann_apply(aao_ctx *ctx, int terms, const double *x, double *y,
 /* y = A x (transpose = 0) or A^T x (transpose = 1) in FP64 (Section 2; the
  * monolithic matrix is never formed).  Heat: y_t = M(x_t - x_{t-1}) +
  * tau_t kappa K x_t; BD2: y_t = M(x_t - 2x_{t-1} + x_{t-2}) + tau^2 K x_t;
- * the transpose shifts the other way.  No workspace needed. */
+ * the transpose shifts the other way.  For these two forms the stencil sums
+ * are formed exactly in 64-bit fixed point per 32-column, 32-step tile and
+ * rounded once (elements more than 2^5 below their tile's largest enter with
+ * an absolute error under 2^-57 of it); the literal heat form runs the FP64
+ * stencil.  An inf or NaN in a tile makes that tile's outputs NaN.  No
+ * workspace needed. */
 int aao_matvec(aao_ctx *ctx, const double *x, double *y, int transpose,
                void *stream);
 
-/* y = A x or A^T x as aao_matvec, for an FP32 x (Section 2).  This is the
- * product the mixed-precision solver forms with its FP32 preconditioned
- * basis.  For the standard heat equation and BD2 the stencil sums are formed
- * exactly in 64-bit fixed point per 32-column tile and rounded once to FP64,
- * so y is within a few FP64 roundings of the exact product of the FP32
- * values (elements below 2^-34 of their tile's largest contribute with an
- * absolute error under 2^-57 of it); the literal heat form widens x and
- * runs the FP64 stencil.  x: device, N floats; y: device, N doubles; no
+/* y = A x - sub or A^T x - sub (sub may be NULL: y = A x) as aao_matvec, for
+ * an FP32 x (Section 2).  With sub this is exactly the product the
+ * mixed-precision solver forms with its FP32 preconditioned basis in the
+ * shifted Arnoldi step, w = A z_j - v_j.  Same fixed-point evaluation as aao_matvec, so y is within a few
+ * FP64 roundings of the exact product of the FP32 values (elements more than
+ * 2^34 below their tile's largest enter with an absolute error under 2^-57
+ * of it); the literal heat form widens x and runs the FP64 stencil.  x:
+ * device, N floats; sub, y: device, N doubles (sub must not overlap y); no
  * workspace needed.  An inf or NaN anywhere in a 32-column, 32-step tile
  * makes that tile's outputs NaN. */
-int aao_matvec_f32(aao_ctx *ctx, const float *x, double *y, int transpose, void *stream);
+int aao_matvec_f32(aao_ctx *ctx, const float *x, const double *sub, double *y, int transpose,
+                   void *stream);
 
 /* Right-hand side from initial data (Section 2): heat b = [M u0; 0; ...];
  * BD2 b = [A0 (u0 + tau v0); -M u0; 0; ...] (v0 may be NULL = at rest, which

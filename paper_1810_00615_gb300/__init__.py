@@ -152,12 +152,13 @@ class AllAtOnce:
                                   _stream(stream)), "aao_matvec", self._ctx)
         return y
 
-    def matvec_f32(self, x, transpose=False, out=None, stream=None):
-        """y = A x (or A^T x) of an FP32 x, in FP64 (the product the mixed
-        solver forms with its FP32 preconditioned basis)."""
+    def matvec_f32(self, x, transpose=False, out=None, sub=None, stream=None):
+        """y = A x (or A^T x) of an FP32 x, in FP64; with sub, y = A x - sub
+        (the shifted-Arnoldi product the mixed solver forms)."""
         x = _dev_f64(x, self.N, "x", torch.float32)
+        sp = _dev_f64(sub, self.N, "sub").data_ptr() if sub is not None else None
         y = self._out(out)
-        check(self.lib.aao_matvec_f32(self._ctx, x.data_ptr(), y.data_ptr(),
+        check(self.lib.aao_matvec_f32(self._ctx, x.data_ptr(), sp, y.data_ptr(),
                                       int(bool(transpose)), _stream(stream)),
               "aao_matvec_f32", self._ctx)
         return y

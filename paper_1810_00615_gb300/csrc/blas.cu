@@ -130,9 +130,8 @@ k_matvec(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
   }
 }
 
-// ------------------------------------------- matvec on an FP32 basis vector
-// With the FP32 preconditioner the FGMRES basis z_j holds FP32 numbers, and
-// for the standard heat equation (any steps) and BD2 every block is
+// ------------------------------------------------ fixed-point matvec
+// For the standard heat equation (any steps) and BD2 every block is
 // a M + b K with M = (h/6) tridiag(1,4,1), K = (1/h) tridiag(-1,2,-1)
 // (Section 2).  With q_t = 4 x_t + x_{t,i-1} + x_{t,i+1} and
 // s_t = 2 x_t - x_{t,i-1} - x_{t,i+1}:
@@ -145,120 +144,178 @@ k_matvec(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
 // them once to FP64 and finishes with two FMAs.  GB300 issues integer
 // operations at 64 per clock per SM and FP64 at 2, so this replaces five of
 // the seven FP64 operations per element of the FP64 form with integer work.
-// Elements more than 2^34 below the tile maximum are truncated at 2^-57 of
-// that maximum; everything else is exact up to the final two roundings.
+// The largest element of a tile keeps 58 bits (FP32 input: 34 binades below
+// it are exact, FP64 input: 5); anything smaller is truncated at 2^-57 of
+// the tile maximum.  x is FP64 (the solution, the public matvec) or FP32
+// (the preconditioned basis of the mixed solver).
 constexpr int kFxRows = 32;   // output time steps per warp tile
 
-__device__ __forceinline__ int f32_exp(float v) {
-  const int e = (int)((__float_as_uint(v) >> 23) & 0xffu);
-  return e ? e : 1;   // subnormals share exponent 1 with the smallest normals
-}
+template <typename XT> struct Fx;
+template <> struct Fx<float> {
+  static constexpr int kNonFinite = 255;   // exponent field of inf and NaN
+  __device__ static int exp(float v) {
+    const int e = (int)((__float_as_uint(v) >> 23) & 0xffu);
+    return e ? e : 1;                       // subnormals scale like exponent 1
+  }
+  // v * 2^(184 - emax) as an integer (|.| < 2^58), emax >= exp(v)
+  __device__ static long long fixed(float v, int emax) {
+    const unsigned b = __float_as_uint(v);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned long long mant = (b & 0x7fffffu) | (e ? 0x800000u : 0u);
+    const int sh = min(emax - (e ? (int)e : 1), 63);
+    const unsigned long long u = (mant << 34) >> sh;
+    return (b >> 31) ? -(long long)u : (long long)u;
+  }
+  __device__ static int unit(int emax) { return emax - 184; }   // log2 of one unit
+};
+template <> struct Fx<double> {
+  static constexpr int kNonFinite = 2047;
+  __device__ static int exp(double v) {
+    const int e = (int)(((unsigned)__double2hiint(v) >> 20) & 0x7ffu);
+    return e ? e : 1;
+  }
+  // v * 2^(1080 - emax) as an integer (|.| < 2^58), emax >= exp(v)
+  __device__ static long long fixed(double v, int emax) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ffu);
+    const unsigned long long mant = (b & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
+    const int sh = min(emax - (e ? e : 1), 63);
+    const unsigned long long u = (mant << 5) >> sh;
+    return (b >> 63) ? -(long long)u : (long long)u;
+  }
+  __device__ static int unit(int emax) { return emax - 1080; }
+};
 
-// x * 2^(184 - emax) as an integer (|.| < 2^58), emax >= the exponent of x.
-__device__ __forceinline__ long long fx_from_f32(float v, int emax) {
-  const unsigned b = __float_as_uint(v);
-  const unsigned e = (b >> 23) & 0xffu;
-  const unsigned mant = (b & 0x7fffffu) | (e ? 0x800000u : 0u);
-  const int sh = min(emax - (e ? (int)e : 1), 63);
-  const unsigned long long u = ((unsigned long long)mant << 34) >> sh;
-  return (b >> 31) ? -(long long)u : (long long)u;
-}
-
-// S * 2^(emax - 184) rounded to nearest even, for |S| < 2^63, 1 <= emax <= 254
-// (the result is always a normal FP64 number).
-__device__ __forceinline__ double fx_to_f64(long long S, int emax) {
+// S * 2^unit rounded to nearest even (|S| < 2^63).  With RANGE, results
+// below the FP64 normal range flush to zero and above it give infinity (FP64
+// input); FP32 input keeps every result in range, so the checks are dropped.
+template <bool RANGE>
+__device__ __forceinline__ double fx_to_f64(long long S, int unit) {
   const unsigned long long neg = (unsigned long long)(S >> 63);
   unsigned long long u = ((unsigned long long)S ^ neg) - neg;
   const int lz = __clzll(u);
   u <<= (lz & 63);
   unsigned long long mant = u >> 11;                       // 53 bits, top one set
   mant += (((unsigned)u & 0x7ffu) + (unsigned)(mant & 1u) + 0x3ffu) >> 11;
-  const unsigned long long bits =
-      ((unsigned long long)(901 + emax - lz) << 52) + mant + (neg << 63);
-  return S ? __longlong_as_double((long long)bits) : 0.0;
+  const int field = 1085 + unit - lz;                      // biased exponent - 1
+  const unsigned long long bits = ((unsigned long long)field << 52) + mant + (neg << 63);
+  if (RANGE) {
+    if (!S || field < 0) return neg ? -0.0 : 0.0;
+    if (field >= 2046) return neg ? -INFINITY : INFINITY;
+  } else if (!S) {
+    return 0.0;
+  }
+  return __longlong_as_double((long long)bits);
 }
 
 #ifndef AAO_MVFX_MINB
 #define AAO_MVFX_MINB 1
 #endif
-template <int NB, bool TR, bool SUB>
+template <int NB, bool TR, bool SUB, typename XT>
 __global__ void __launch_bounds__(kMvCols, AAO_MVFX_MINB)
-k_matvec_fx(const float *__restrict__ x, double *__restrict__ y, int n, int ell, double mh,
+k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell, double mh,
             const double *__restrict__ beta, const double *__restrict__ sub) {
   constexpr int R = kFxRows, IN = R + NB - 1;   // input time steps per tile
-  const int lane = threadIdx.x & 31;
+  constexpr int kWarps = kMvCols / 32;
+  using F = Fx<XT>;
+  __shared__ long long s_halo[kWarps][2][IN];   // converted halo columns, walk order
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i = blockIdx.x * kMvCols + threadIdx.x;
   const int iw = i - lane;                      // first column of the warp
   if (iw >= n) return;                          // whole warp past the end
+  const bool col_ok = i < n;
+  // walk step k = 0..IN-1 visits time step t0 + k dir: forward from the
+  // oldest lag up, transpose from the newest lead down
+  constexpr int dir = TR ? -1 : 1;
   const int c0 = blockIdx.y * R;
-  // input row r is time step c0 - (NB-1) + r (forward) or c0 + r (transpose)
-  auto trow = [&](int r) { return TR ? c0 + r : c0 - (NB - 1) + r; };
-  auto ld = [&](int col, int r) -> float {
-    const int t = trow(r);
-    return (r < IN && col >= 0 && col < n && t >= 0 && t < ell)
-               ? __ldg(&x[(int64_t)t * n + col]) : 0.0f;
-  };
+  const int t0 = TR ? c0 + IN - 1 : c0 - (NB - 1);
+  const int64_t step = (int64_t)dir * n;
+  const int ic = col_ok ? i : iw;               // a valid column for every lane
+  const XT *px0 = x + (int64_t)t0 * n + ic;     // dereferenced only on valid steps
+  auto t_ok = [&](int t) { return (unsigned)t < (unsigned)ell; };
+
   // pass 1: the tile's largest exponent (the values land in L1 for pass 2)
-  const float hl0 = ld(iw - 1, lane), hr0 = ld(iw + 32, lane);
-  const float hl1 = (IN > 32) ? ld(iw - 1, lane + 32) : 0.0f;
-  const float hr1 = (IN > 32) ? ld(iw + 32, lane + 32) : 0.0f;
-  int em = max(max(f32_exp(hl0), f32_exp(hr0)), max(f32_exp(hl1), f32_exp(hr1)));
-#pragma unroll 8
-  for (int r = 0; r < IN; r++) em = max(em, f32_exp(ld(i, r)));
+  auto halo = [&](int col, int k) -> XT {
+    const int t = t0 + k * dir;
+    return (k < IN && col >= 0 && col < n && t_ok(t)) ? __ldg(&x[(int64_t)t * n + col]) : (XT)0;
+  };
+  const XT hl0 = halo(iw - 1, lane), hr0 = halo(iw + 32, lane);
+  const XT hl1 = (IN > 32) ? halo(iw - 1, lane + 32) : (XT)0;
+  const XT hr1 = (IN > 32) ? halo(iw + 32, lane + 32) : (XT)0;
+  int em = max(max(F::exp(hl0), F::exp(hr0)), max(F::exp(hl1), F::exp(hr1)));
+  {
+    const XT *p = px0;
+    int t = t0;
+#pragma unroll 4
+    for (int k = 0; k < IN; k++, p += step, t += dir)
+      if (col_ok && t_ok(t)) em = max(em, F::exp(__ldg(p)));
+  }
   em = (int)__reduce_max_sync(0xffffffffu, (unsigned)em);
-  const int t_lo = c0, t_hi = min(ell, c0 + R);
-  if (em == 255) {                              // an inf or NaN in the tile
-    if (i < n)
-      for (int t = t_lo; t < t_hi; t++) y[(int64_t)t * n + i] = __longlong_as_double(0x7ff8000000000000ll);
+  if (em == F::kNonFinite) {                    // an inf or NaN in the tile
+    if (col_ok)
+      for (int t = c0; t < min(ell, c0 + R); t++)
+        y[(int64_t)t * n + i] = __longlong_as_double(0x7ff8000000000000ll);
     return;
   }
-  const long long XL0 = fx_from_f32(hl0, em), XR0 = fx_from_f32(hr0, em);
-  const long long XL1 = fx_from_f32(hl1, em), XR1 = fx_from_f32(hr1, em);
-  long long q1 = 0, q2 = 0;                     // q of the previous one or two rows walked
-  // pass 2 walks the rows; x and the subtrahend are fetched kPre rows ahead
-  // so that their latency hides behind the integer work of the rows between
+  const int unit = F::unit(em);
+  if (lane < IN) {
+    s_halo[warp][0][lane] = F::fixed(hl0, em);
+    s_halo[warp][1][lane] = F::fixed(hr0, em);
+  }
+  if (IN > 32 && lane + 32 < IN) {
+    s_halo[warp][0][lane + 32] = F::fixed(hl1, em);
+    s_halo[warp][1][lane + 32] = F::fixed(hr1, em);
+  }
+  __syncwarp();
+
+  // pass 2: walk the steps; x and the subtrahend come kPre steps ahead so
+  // their latency hides behind the integer work of the steps in between
   constexpr int kPre = 4;
-  float zpre[kPre];
+  const double *pv0 = SUB ? sub + (int64_t)t0 * n + ic : nullptr;
+  XT zpre[kPre];
   double vpre[kPre];
-  auto ld_sub = [&](int k) -> double {
-    if (!SUB || k < NB - 1 || k >= IN) return 0.0;
-    const int t = trow(TR ? IN - 1 - k : k);
-    return (i < n && t < ell) ? __ldg(&sub[(int64_t)t * n + i]) : 0.0;
-  };
-  auto ld_z = [&](int k) -> float { return k < IN ? ld(i, TR ? IN - 1 - k : k) : 0.0f; };
 #pragma unroll
-  for (int k = 0; k < kPre; k++) { zpre[k] = ld_z(k); vpre[k] = ld_sub(k); }
-  // unrolled by the prefetch depth only: a fully unrolled walk is tens of KB
-  // of code and stalls on instruction fetch
+  for (int k = 0; k < kPre; k++) {
+    const int t = t0 + k * dir;
+    const bool ok = col_ok && t_ok(t);
+    zpre[k] = ok ? __ldg(px0 + k * step) : (XT)0;
+    vpre[k] = (SUB && ok && k >= NB - 1) ? __ldg(pv0 + k * step) : 0.0;
+  }
+  const XT *pz = px0 + kPre * step;
+  const double *pv = SUB ? pv0 + kPre * step : nullptr;
+  double *py = y + (int64_t)t0 * n + ic;
+  long long q1 = 0, q2 = 0;                     // q of the previous one or two steps walked
 #pragma unroll 1
   for (int kb = 0; kb < IN; kb += kPre) {
 #pragma unroll
     for (int u = 0; u < kPre; u++) {
       const int k = kb + u;
-      const float zk = zpre[u];
+      const int t = t0 + k * dir;
+      const XT zk = zpre[u];
       const double vk = vpre[u];
-      zpre[u] = ld_z(k + kPre);
-      vpre[u] = ld_sub(k + kPre);
-      const int r = TR ? IN - 1 - k : k;
-      const long long X = fx_from_f32(zk, em);
+      {
+        const int tn = t + kPre * dir;
+        const bool okn = col_ok && t_ok(tn) && k + kPre < IN;
+        zpre[u] = okn ? __ldg(pz) : (XT)0;
+        if (SUB) vpre[u] = okn ? __ldg(pv) : 0.0;
+        pz += step;
+        if (SUB) pv += step;
+      }
+      const long long X = F::fixed(zk, em);
       long long Xl = __shfl_up_sync(0xffffffffu, X, 1);
       long long Xr = __shfl_down_sync(0xffffffffu, X, 1);
-      const int src = r & 31;
-      const long long hl = __shfl_sync(0xffffffffu, r < 32 ? XL0 : XL1, src);
-      const long long hr = __shfl_sync(0xffffffffu, r < 32 ? XR0 : XR1, src);
-      if (lane == 0) Xl = hl;
-      if (lane == 31) Xr = hr;
+      if (lane == 0) Xl = s_halo[warp][0][k < IN ? k : 0];
+      if (lane == 31) Xr = s_halo[warp][1][k < IN ? k : 0];
       const long long P = Xl + Xr;
       const long long q = 4 * X + P;
-      const int t = trow(r);
-      if (k < IN && k >= NB - 1 && i < n && t < ell) {
+      if (k >= NB - 1 && k < IN && col_ok && t_ok(t)) {
         const long long sm = (NB == 2) ? q - q1 : q - 2 * q1 + q2;
         const long long sk = 2 * X - P;
         const double bt = __ldg(&beta[t]);
-        const double skd = fx_to_f64(sk, em), smd = fx_to_f64(sm, em);
-        const int64_t o = (int64_t)t * n + i;
+        constexpr bool RANGE = sizeof(XT) == 8;
+        const double skd = fx_to_f64<RANGE>(sk, unit), smd = fx_to_f64<RANGE>(sm, unit);
         const double acc = SUB ? fma(bt, skd, -vk) : bt * skd;
-        y[o] = fma(mh, smd, acc);
+        py[(int64_t)k * step] = fma(mh, smd, acc);
       }
       q2 = q1;
       q1 = q;
@@ -294,22 +351,20 @@ static cudaError_t matvec_any(const Ctx &c, const XT *x, double *y, int transpos
   return cudaGetLastError();
 }
 
-cudaError_t launch_matvec(const Ctx &c, const double *x, double *y, int transpose,
-                          cudaStream_t s, const double *sub) {
-  return matvec_any(c, x, y, transpose, s, sub);
-}
-
-template <int NB, bool TR>
-static void mv_fx(const Ctx &c, dim3 grid, const float *x, double *y, const double *sub,
+template <int NB, bool TR, typename XT>
+static void mv_fx(const Ctx &c, dim3 grid, const XT *x, double *y, const double *sub,
                   cudaStream_t s) {
   const int n = (int)c.n, ell = (int)c.ell;
   const double mh = c.h / 6.0;
-  if (sub) k_matvec_fx<NB, TR, true><<<grid, kMvCols, 0, s>>>(x, y, n, ell, mh, c.beta, sub);
-  else k_matvec_fx<NB, TR, false><<<grid, kMvCols, 0, s>>>(x, y, n, ell, mh, c.beta, nullptr);
+  if (sub) k_matvec_fx<NB, TR, true, XT><<<grid, kMvCols, 0, s>>>(x, y, n, ell, mh, c.beta, sub);
+  else k_matvec_fx<NB, TR, false, XT><<<grid, kMvCols, 0, s>>>(x, y, n, ell, mh, c.beta, nullptr);
 }
 
-cudaError_t launch_matvec(const Ctx &c, const float *x, double *y, int transpose,
-                          cudaStream_t s, const double *sub) {
+// Heat and BD2 take the fixed-point kernel; the literal heat form (whose M
+// coefficients differ between A0 and A1) the FP64 stencil.
+template <typename XT>
+static cudaError_t matvec_dispatch(const Ctx &c, const XT *x, double *y, int transpose,
+                                   cudaStream_t s, const double *sub) {
   if (c.equation == AAO_HEAT_LITERAL) return matvec_any(c, x, y, transpose, s, sub);
   const int n = (int)c.n, ell = (int)c.ell;
   const dim3 grid((unsigned)((n + kMvCols - 1) / kMvCols),
@@ -321,6 +376,16 @@ cudaError_t launch_matvec(const Ctx &c, const float *x, double *y, int transpose
   else mv_fx<2, false>(c, grid, x, y, sub, s);
   note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_matvec(const Ctx &c, const double *x, double *y, int transpose,
+                          cudaStream_t s, const double *sub) {
+  return matvec_dispatch(c, x, y, transpose, s, sub);
+}
+
+cudaError_t launch_matvec(const Ctx &c, const float *x, double *y, int transpose,
+                          cudaStream_t s, const double *sub) {
+  return matvec_dispatch(c, x, y, transpose, s, sub);
 }
 
 // --------------------------------------------------------------------- rhs

@@ -841,12 +841,17 @@ int aao_matvec(aao_ctx *ctx, const double *x, double *y, int transpose, void *st
   return AAO_OK;
 }
 
-int aao_matvec_f32(aao_ctx *ctx, const float *x, double *y, int transpose, void *stream) {
+int aao_matvec_f32(aao_ctx *ctx, const float *x, const double *sub, double *y, int transpose,
+                   void *stream) {
   if (!ctx || !x || !y) return AAO_EINVAL;
   Ctx &c = ctx->c;
-  if (overlap2(x, (size_t)c.N * sizeof(float), y, (size_t)c.N * sizeof(double))) return AAO_EINVAL;
+  const size_t vb = (size_t)c.N * sizeof(double);
+  if (overlap2(x, (size_t)c.N * sizeof(float), y, vb)) return AAO_EINVAL;
+  if (sub && overlap(sub, y, vb)) return AAO_EINVAL;
   cudaStream_t s = as_stream(stream);
-  AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] { return aao::launch_matvec(c, x, y, transpose ? 1 : 0, s); }));
+  AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] {
+    return aao::launch_matvec(c, x, y, transpose ? 1 : 0, s, sub);
+  }));
   return AAO_OK;
 }
 

@@ -5,7 +5,7 @@ profilers (ncu) and quick timing.
         --prec fp32 --reps 3
 
 --op precond | neumann | matvec | matvec_f32 | solve (matvec_f32: the product
-of an FP32 vector, as the mixed solver forms it).  Prints one line with the mean CUDA-
+w = A z - v of an FP32 z, as the mixed solver forms it in its Arnoldi step).  Prints one line with the mean CUDA-
 event time per call.  Inputs are seeded standard-normal block vectors (or the
 8-mode heat initial data for `solve`).
 """
@@ -57,7 +57,7 @@ def main(argv=None):
         elif a.op == "matvec":
             s.matvec(x, out=y)
         elif a.op == "matvec_f32":
-            s.matvec_f32(x32, out=y)
+            s.matvec_f32(x32, out=y, sub=x)
         else:
             s.solve(b, restart=30, rtol=1e-10)
 

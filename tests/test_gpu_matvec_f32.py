@@ -1,11 +1,11 @@
-"""Parity of the matvec of an FP32 vector (aao_matvec_f32, the product the
-mixed solver forms with its FP32 preconditioned basis) with the oracle's
-A x (Section 2) on the same FP32 values.
+"""Parity of the fixed-point matvec with the oracle's A x (Section 2): for an
+FP32 vector (aao_matvec_f32, the product the mixed solver forms with its FP32
+preconditioned basis) and for an FP64 one (aao_matvec, heat and BD2 forms).
 
-The heat and BD2 forms are evaluated in 64-bit fixed point per warp tile and
-rounded once to FP64, so besides the max-relative parity used for the FP64
-matvec, every element is held to a few FP64 roundings of sum_j |A_ij| |x_j|
-against an extended-precision product of the oracle's matrices."""
+Both evaluate the stencil sums in 64-bit fixed point per warp tile and round
+them once to FP64, so besides the max-relative parity, every element is held
+to a few FP64 roundings of sum_j |A_ij| |x_j| against an extended-precision
+product of the oracle's matrices."""
 import numpy as np
 import pytest
 
@@ -20,6 +20,17 @@ EPS = 2.0 ** -53
 
 def _f32_dev(torch, X):
     return torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+
+
+def _apply(torch, a, X, dtype, transpose=False):
+    """The GPU product of X (already representable in dtype) in FP64."""
+    if dtype == "f32":
+        return to_host(a.matvec_f32(_f32_dev(torch, X), transpose=transpose))
+    return to_host(a.matvec(torch.from_numpy(np.ascontiguousarray(X)).cuda(), transpose=transpose))
+
+
+def _rounded(X, dtype):
+    return X.astype(np.float32).astype(np.float64) if dtype == "f32" else X
 
 
 def _abs_system(S):
@@ -40,6 +51,31 @@ def _context(kind, n, ell):
     if taus is not None:
         a.set_steps(taus)
     return S, a
+
+
+def _tile_max(X):
+    """For each output (t, i): max |x| over the fixed-point tile that forms it
+    (its 32 columns with one halo column each side, its 32 steps with the two
+    lag steps on either side)."""
+    ell, n = X.shape
+    A = np.abs(X)
+    T = np.zeros_like(A)
+    for t0 in range(0, ell, 32):
+        for i0 in range(0, n, 32):
+            blk = A[max(0, t0 - 2):min(ell, t0 + 34), max(0, i0 - 1):min(n, i0 + 33)]
+            T[t0:t0 + 32, i0:i0 + 32] = blk.max()
+    return T
+
+
+def _bound(S, X, transpose):
+    """8 FP64 roundings of (|A| |x|)_i plus the documented truncation: inputs
+    far below their tile maximum enter with an absolute error under 2^-57 of
+    it (2^-56 here for margin), times the row sums of |A|."""
+    absS = _abs_system(S)
+    f = system.matvec_T if transpose else system.matvec
+    mag = f(absS, np.abs(X))
+    rows = f(absS, np.ones_like(X))
+    return 8 * EPS * mag + 2.0 ** -56 * rows * _tile_max(X)
 
 
 def _exact(S, X, transpose):
@@ -79,13 +115,19 @@ def test_matvec_f32_matches_oracle(n, ell, kind, transpose):
     # the FP64 entry point on the same values agrees as closely
     fp64 = to_host(a.matvec(torch.from_numpy(X).cuda(), transpose=transpose))
     assert rel_max(got, fp64) <= 1e-13
+    # the fused shifted-Arnoldi form y = A x - v
+    V = rand_block(n, ell, 29 + n)
+    fused = to_host(a.matvec_f32(_f32_dev(torch, X), transpose=transpose,
+                                 sub=torch.from_numpy(V).cuda()))
+    assert rel_max(fused, want - V) <= 1e-13
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
 @pytest.mark.parametrize("kind", ["heat", "wave_bd2", "steps"])
 @pytest.mark.parametrize("transpose", [False, True])
-def test_matvec_f32_elementwise_rounding_bound(kind, transpose):
-    """A near-cancelling input (the FP32-rounded time-stepping solution) and a
-    random one: |y - A x| <= 8 eps (|A| |x|) in every element."""
+def test_matvec_elementwise_rounding_bound(kind, transpose, dtype):
+    """A near-cancelling input (the rounded time-stepping solution) and a
+    random one: every element within the documented bound (_bound)."""
     torch = need_gpu()
     n, ell = 70, 64
     S, a = _context(kind, n, ell)
@@ -96,40 +138,38 @@ def test_matvec_f32_elementwise_rounding_bound(kind, transpose):
         B = system.rhs_heat(S, syn.heat_initial(n, modes=8))
     U = system.forward_substitution(S, B)
     for X in (U, rand_block(n, ell, 77)):
-        X = X.astype(np.float32).astype(np.float64)
-        got = to_host(a.matvec_f32(_f32_dev(torch, X), transpose=transpose)).astype(np.longdouble)
+        X = _rounded(X, dtype)
+        got = _apply(torch, a, X, dtype, transpose).astype(np.longdouble)
         exact = _exact(S, X, transpose)
-        absS = _abs_system(S)
-        mag = (system.matvec_T if transpose else system.matvec)(absS, np.abs(X))
         err = np.abs(got - exact).astype(np.float64)
-        assert np.all(err <= 8 * EPS * mag + 1e-300)
+        assert np.all(err <= _bound(S, X, transpose) + 1e-300)
 
 
-def test_matvec_f32_wide_dynamic_range_in_a_tile():
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_matvec_wide_dynamic_range_in_a_tile(dtype):
     """Values spanning 2^0 .. 2^-70 inside one 32 x 32 tile: the small ones are
     truncated at 2^-57 of the tile maximum, far below an FP64 rounding of it."""
     torch = need_gpu()
     n, ell = 64, 32
     S, a = _context("heat", n, ell)
     r = syn.rng(5)
-    X = r.standard_normal((ell, n)) * np.exp2(-r.integers(0, 71, size=(ell, n)))
-    X = X.astype(np.float32).astype(np.float64)
-    got = to_host(a.matvec_f32(_f32_dev(torch, X))).astype(np.longdouble)
+    X = _rounded(r.standard_normal((ell, n)) * np.exp2(-r.integers(0, 71, size=(ell, n))), dtype)
+    got = _apply(torch, a, X, dtype).astype(np.longdouble)
     exact = _exact(S, X, False)
     scale = np.max(np.abs(system.matvec(_abs_system(S), np.abs(X))))
     assert float(np.max(np.abs(got - exact))) <= 8 * EPS * scale
 
 
-def test_matvec_f32_zero_and_nonfinite():
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_matvec_zero_and_nonfinite(dtype):
     torch = need_gpu()
     n, ell = 100, 64
     S, a = _context("heat", n, ell)
-    X = np.zeros((ell, n))
-    assert np.all(to_host(a.matvec_f32(_f32_dev(torch, X))) == 0.0)
+    assert np.all(_apply(torch, a, np.zeros((ell, n)), dtype) == 0.0)
     for bad in (np.nan, np.inf):
-        X = rand_block(n, ell, 8)
+        X = _rounded(rand_block(n, ell, 8), dtype)
         X[40, 50] = bad                 # tile: columns 32..63, steps 32..63
-        got = to_host(a.matvec_f32(_f32_dev(torch, X)))
+        got = _apply(torch, a, X, dtype)
         assert np.isnan(got[40, 50])
         assert np.all(np.isfinite(got[:32]))          # earlier steps untouched
         assert np.all(np.isfinite(got[:, :32]))       # other column tiles untouched
