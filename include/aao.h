@@ -54,7 +54,7 @@ enum { AAO_HEAT = 0, AAO_WAVE_BD2 = 1, AAO_HEAT_LITERAL = 2 };
 
 /* Arithmetic of the preconditioner (FFTs and tridiagonal solves).  The outer
  * GMRES, the matvec and the true residual are FP64 in both cases. */
-enum { AAO_PREC_FP64 = 0, AAO_PREC_FP32 = 1 };
+enum { AAO_PREC_FP64 = 0, AAO_PREC_FP32 = 1, AAO_PREC_FP32_REFINED = 2 };
 
 enum {
   AAO_OK = 0,
@@ -104,7 +104,15 @@ int aao_set_kappa(aao_ctx *ctx, double kappa);
  * NULL restores uniform steps.  Heat only (AAO_EINVAL otherwise). */
 int aao_set_steps(aao_ctx *ctx, const double *tau_steps_host);
 
-/* AAO_PREC_FP32 or AAO_PREC_FP64 for the preconditioner. */
+/* Precision of the preconditioner apply: AAO_PREC_FP64 (FFTs and solves in
+ * FP64), AAO_PREC_FP32 (in FP32), or AAO_PREC_FP32_REFINED: the FP32 apply
+ * followed by one refinement sweep z = z0 - P^{-1}(P z0 - x), where P z0 is
+ * formed exactly (fixed point, or FP64 for the literal heat form) and the
+ * correction applied in FP32 again.  The refined apply is as accurate as the
+ * product of two FP32 errors (about 1e-9 relative where FP32 alone gives
+ * 3e-7), so FGMRES needs the iterations of the FP64 preconditioner at about
+ * twice the cost of an FP32 apply.  The paper has no counterpart: it is a
+ * choice of how to evaluate the Section 3 preconditioner on this hardware. */
 int aao_set_precision(aao_ctx *ctx, int prec);
 
 /* Bytes of device workspace that the solve calls need for GMRES(restart)
@@ -207,16 +215,18 @@ int aao_solve_host(aao_ctx *ctx, const double *u0_host, const double *v0_host,
                    int precond, aao_solve_info *info, void *stream);
 
 /* Kernel classes for aao_profile_read: the three stages of a preconditioner
- * apply, the matvec, and the Arnoldi kernels. */
+ * apply, the matvec, the Arnoldi kernels, and the residual P z0 - x (or the
+ * Neumann right-hand side) of the refined FP32 apply. */
 enum {
   AAO_K_FFT_FORWARD = 0, AAO_K_TRIDIAG = 1, AAO_K_FFT_INVERSE = 2, AAO_K_MATVEC = 3,
-  AAO_K_DOTS = 4, AAO_K_UPDATE = 5, AAO_K_COMBINE = 6, AAO_K_OTHER = 7, AAO_K_COUNT = 8
+  AAO_K_DOTS = 4, AAO_K_UPDATE = 5, AAO_K_COMBINE = 6, AAO_K_OTHER = 7, AAO_K_REFINE = 8,
+  AAO_K_COUNT = 9
 };
 
 /* Profiling (not in the paper): while on != 0 every kernel the context
  * launches is bracketed by two CUDA events on its stream.  aao_profile_read
- * waits for the recorded events, adds their durations per class to ms[8]
- * (milliseconds) and the number of kernel launches per class to launches[8]
+ * waits for the recorded events, adds their durations per class to ms[9]
+ * (milliseconds) and the number of kernel launches per class to launches[9]
  * (either may be NULL), and clears the totals if reset != 0.  Launches are
  * counted whether or not timing is on. */
 int aao_profile_enable(aao_ctx *ctx, int on);
@@ -245,7 +255,9 @@ int64_t aao_kernel_launches(const aao_ctx *ctx);
  *     reads), but two calls whose kernels overlap on the GPU (different
  *     streams, or different host threads) race on the array: serialise them.
  *   - The context itself still comes from aao_create, which allocates its
- *     constant tables once; no workspace is needed for this call. */
+ *     constant tables once; no workspace is needed for this call.
+ *   - AAO_PREC_FP32_REFINED needs scratch vectors beyond the array: in that
+ *     mode this call returns AAO_EINVAL. */
 int aao_precond_apply_static(aao_ctx *ctx, const double *x, double *y, int transpose,
                              void *stream);
 

@@ -20,11 +20,11 @@ import torch
 
 from . import _build
 from ._capi import (AAO_ECUDA, AAO_EINVAL, AAO_ENOCONV, AAO_ENUMERIC, AAO_EUNSUPPORTED,
-                    AAO_HEAT, AAO_HEAT_LITERAL, AAO_OK, AAO_PREC_FP32, AAO_PREC_FP64,
+                    AAO_HEAT, AAO_HEAT_LITERAL, AAO_OK, AAO_PREC_FP32, AAO_PREC_FP32_REFINED, AAO_PREC_FP64,
                     AAO_WAVE_BD2, AAOError, SolveInfo, check, lib)
 
 __all__ = ["AllAtOnce", "AAOSolve", "SolveInfo", "AAOError", "lib", "build",
-           "AAO_HEAT", "AAO_WAVE_BD2", "AAO_HEAT_LITERAL", "AAO_PREC_FP32", "AAO_PREC_FP64",
+           "AAO_HEAT", "AAO_WAVE_BD2", "AAO_HEAT_LITERAL", "AAO_PREC_FP32", "AAO_PREC_FP32_REFINED", "AAO_PREC_FP64",
            "AAO_OK", "AAO_ENOCONV", "AAO_EINVAL", "AAO_ECUDA", "AAO_ENUMERIC",
            "AAO_EUNSUPPORTED"]
 
@@ -54,7 +54,8 @@ class AllAtOnce:
 
     equation: "heat" (implicit Euler, A0 = M + tau kappa K, A1 = -M),
     "wave_bd2" (A0 = M + tau^2 K, A1 = -2M, A2 = M) or "heat_literal" (the
-    printed A0 = K + tau M).  precision: "fp32" or "fp64" for the
+    printed A0 = K + tau M).  precision: "fp32", "fp32_refined" (FP32 with
+    one refinement sweep, FP64-like accuracy) or "fp64" for the
     preconditioner; the outer GMRES is FP64 either way.
     """
 
@@ -100,7 +101,8 @@ class AllAtOnce:
         check(self.lib.aao_set_steps(self._ctx, arr.ctypes.data), "aao_set_steps", self._ctx)
 
     def set_precision(self, precision: str):
-        p = {"fp32": AAO_PREC_FP32, "fp64": AAO_PREC_FP64}[precision]
+        p = {"fp32": AAO_PREC_FP32, "fp64": AAO_PREC_FP64,
+             "fp32_refined": AAO_PREC_FP32_REFINED}[precision]
         check(self.lib.aao_set_precision(self._ctx, p), "aao_set_precision", self._ctx)
         self.precision = precision
 
@@ -227,8 +229,8 @@ class AllAtOnce:
     def profile_read(self, reset: bool = False):
         """{class: (milliseconds, launches)} since the last reset."""
         from ._capi import KERNEL_CLASSES
-        ms = (C.c_double * 8)()
-        nl = (C.c_int64 * 8)()
+        ms = (C.c_double * len(KERNEL_CLASSES))()
+        nl = (C.c_int64 * len(KERNEL_CLASSES))()
         check(self.lib.aao_profile_read(self._ctx, ms, nl, int(bool(reset))),
               "aao_profile_read", self._ctx)
         return {k: (ms[i], nl[i]) for i, k in enumerate(KERNEL_CLASSES)}

@@ -245,6 +245,8 @@ struct Ctx {
   cx<float> *tw32 = nullptr;      // exp(-2 pi i m/ell), m < ell
   cx<double> *tw64 = nullptr;
   double *beta = nullptr;         // per-step K coefficient tau_t kappa / h (ell)
+  double *beta_p = nullptr;       // K coefficient of the circulant P (constant step) (ell)
+  bool refine = false;            // FP32 preconditioner with one refinement sweep
   double *mv_d0 = nullptr;        // per-step diagonal of A0^t (ell)
   double *mv_o0 = nullptr;        // per-step off-diagonal of A0^t (ell)
   double mv_d1 = 0, mv_o1 = 0, mv_d2 = 0, mv_o2 = 0;   // A1, A2 (diag, off)
@@ -281,6 +283,8 @@ struct WsLayout {
   size_t spec = 0, spec_bytes = 0;
   size_t inter = 0, inter_bytes = 0;   // two-kernel forward FFT scratch (0: none)
   size_t red = 0, red_bytes = 0;
+  size_t rf32 = 0;        // refined apply: z0 (N floats)
+  size_t rf64 = 0;        // refined apply: residual, Neumann right-hand side (2 x N doubles)
   size_t vecs = 0;        // first FP64 vector (V_0 ...)
   size_t vec_bytes = 0;   // bytes per vector (rounded)
   size_t total = 0;
@@ -302,7 +306,7 @@ cudaError_t kernel_setup(const void *kern, int threads, size_t smem, int *reside
 cudaError_t fft_forward_f32(const Ctx &c, const double *x, const double *yprev, void *spec,
                             cudaStream_t s, void *inter = nullptr);
 cudaError_t fft_inverse_f32(const Ctx &c, const void *spec, double *y, cudaStream_t s,
-                            void *inter = nullptr);
+                            void *inter = nullptr, const float *base = nullptr);
 cudaError_t fft_forward_f64(const Ctx &c, const double *x, const double *yprev, void *spec,
                             cudaStream_t s, void *inter = nullptr);
 size_t fft_inter_bytes_f32(const Ctx &c);
@@ -322,6 +326,13 @@ cudaError_t launch_matvec(const Ctx &c, const double *x, double *y, int transpos
                           cudaStream_t s, const double *sub = nullptr);
 cudaError_t launch_matvec(const Ctx &c, const float *x, double *y, int transpose,
                           cudaStream_t s, const double *sub = nullptr);
+// y = P z - sub (or P^T z - sub) for an FP32 z: the residual of the refined
+// FP32 preconditioner, P the block circulant of Section 3 (constant step).
+cudaError_t launch_circ_residual(const Ctx &c, const float *z, double *y, int transpose,
+                                 cudaStream_t s, const double *sub);
+// u = x - E y, the right-hand side of a Neumann term (Section 2), in FP64.
+cudaError_t launch_neumann_rhs(const Ctx &c, const double *x, const double *y, double *u,
+                               cudaStream_t s);
 cudaError_t launch_rhs(const Ctx &c, const double *u0, const double *v0, double *b,
                        cudaStream_t s);
 

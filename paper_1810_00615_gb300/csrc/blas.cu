@@ -86,7 +86,7 @@ constexpr int kMvRows = 32;    // time steps per thread
 __device__ __forceinline__ double wide(double v) { return v; }
 __device__ __forceinline__ double wide(float v) { return to_f64(v); }
 
-template <int NB, bool TR, bool SUB, typename XT>
+template <int NB, bool TR, bool SUB, typename XT, bool CIRC>
 __global__ void __launch_bounds__(kMvCols)
 k_matvec(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
          const double *__restrict__ d0, const double *__restrict__ o0,
@@ -106,7 +106,11 @@ k_matvec(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
   double xp1 = 0.0, sp1 = 0.0, xp2 = 0.0, sp2 = 0.0;
   const int first = TR ? c1 - 1 : c0;
   const int step = TR ? -1 : 1;
-  const int tp1 = first - step, tp2 = first - 2 * step;
+  int tp1 = first - step, tp2 = first - 2 * step;
+  if (CIRC) {                       // the block circulant P: lags wrap around in time
+    tp1 = ((tp1 % ell) + ell) % ell;
+    tp2 = ((tp2 % ell) + ell) % ell;
+  }
   if (tp1 >= 0 && tp1 < ell) row_vals(tp1, xp1, sp1);
   if (NB > 2 && tp2 >= 0 && tp2 < ell) row_vals(tp2, xp2, sp2);
   for (int k = 0; k < c1 - c0; k++) {
@@ -211,7 +215,7 @@ __device__ __forceinline__ double fx_to_f64(long long S, int unit) {
 #ifndef AAO_MVFX_MINB
 #define AAO_MVFX_MINB 1
 #endif
-template <int NB, bool TR, bool SUB, typename XT>
+template <int NB, bool TR, bool SUB, typename XT, bool CIRC>
 __global__ void __launch_bounds__(kMvCols, AAO_MVFX_MINB)
 k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell, double mh,
             const double *__restrict__ beta, const double *__restrict__ sub) {
@@ -233,10 +237,18 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell, do
   const int ic = col_ok ? i : iw;               // a valid column for every lane
   const XT *px0 = x + (int64_t)t0 * n + ic;     // dereferenced only on valid steps
   auto t_ok = [&](int t) { return (unsigned)t < (unsigned)ell; };
+  // CIRC (the block circulant P): steps outside [0, ell) wrap around; the
+  // walk pointer is replaced by the wrapped row's address there
+  auto wrap = [&](int t) { return ((t % ell) + ell) % ell; };
+  auto z_ok = [&](int t) { return col_ok && (CIRC || t_ok(t)); };
+  auto zaddr = [&](int t, const XT *pw) -> const XT * {
+    return (CIRC && !t_ok(t)) ? x + (int64_t)wrap(t) * n + ic : pw;
+  };
 
   // pass 1: the tile's largest exponent (the values land in L1 for pass 2)
   auto halo = [&](int col, int k) -> XT {
-    const int t = t0 + k * dir;
+    int t = t0 + k * dir;
+    if (CIRC) t = wrap(t);
     return (k < IN && col >= 0 && col < n && t_ok(t)) ? __ldg(&x[(int64_t)t * n + col]) : (XT)0;
   };
   const XT hl0 = halo(iw - 1, lane), hr0 = halo(iw + 32, lane);
@@ -248,7 +260,7 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell, do
     int t = t0;
 #pragma unroll 4
     for (int k = 0; k < IN; k++, p += step, t += dir)
-      if (col_ok && t_ok(t)) em = max(em, F::exp(__ldg(p)));
+      if (z_ok(t)) em = max(em, F::exp(__ldg(zaddr(t, p))));
   }
   em = (int)__reduce_max_sync(0xffffffffu, (unsigned)em);
   if (em == F::kNonFinite) {                    // an inf or NaN in the tile
@@ -277,9 +289,8 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell, do
 #pragma unroll
   for (int k = 0; k < kPre; k++) {
     const int t = t0 + k * dir;
-    const bool ok = col_ok && t_ok(t);
-    zpre[k] = ok ? __ldg(px0 + k * step) : (XT)0;
-    vpre[k] = (SUB && ok && k >= NB - 1) ? __ldg(pv0 + k * step) : 0.0;
+    zpre[k] = z_ok(t) ? __ldg(zaddr(t, px0 + k * step)) : (XT)0;
+    vpre[k] = (SUB && col_ok && t_ok(t) && k >= NB - 1) ? __ldg(pv0 + k * step) : 0.0;
   }
   const XT *pz = px0 + kPre * step;
   const double *pv = SUB ? pv0 + kPre * step : nullptr;
@@ -295,9 +306,9 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell, do
       const double vk = vpre[u];
       {
         const int tn = t + kPre * dir;
-        const bool okn = col_ok && t_ok(tn) && k + kPre < IN;
-        zpre[u] = okn ? __ldg(pz) : (XT)0;
-        if (SUB) vpre[u] = okn ? __ldg(pv) : 0.0;
+        const bool inb = k + kPre < IN;
+        zpre[u] = (inb && z_ok(tn)) ? __ldg(zaddr(tn, pz)) : (XT)0;
+        if (SUB) vpre[u] = (inb && col_ok && t_ok(tn)) ? __ldg(pv) : 0.0;
         pz += step;
         if (SUB) pv += step;
       }
@@ -323,57 +334,93 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell, do
   }
 }
 
-template <int NB, bool TR, typename XT>
+template <int NB, bool TR, typename XT, bool CIRC>
 static void mv_sub(const Ctx &c, dim3 grid, const XT *x, double *y, const double *sub,
                    cudaStream_t s) {
   const int n = (int)c.n, ell = (int)c.ell;
   if (sub)
-    k_matvec<NB, TR, true, XT><<<grid, kMvCols, 0, s>>>(x, y, n, ell, c.mv_d0, c.mv_o0, c.mv_d1,
-                                                        c.mv_o1, c.mv_d2, c.mv_o2, sub);
+    k_matvec<NB, TR, true, XT, CIRC><<<grid, kMvCols, 0, s>>>(x, y, n, ell, c.mv_d0, c.mv_o0,
+                                                              c.mv_d1, c.mv_o1, c.mv_d2, c.mv_o2,
+                                                              sub);
   else
-    k_matvec<NB, TR, false, XT><<<grid, kMvCols, 0, s>>>(x, y, n, ell, c.mv_d0, c.mv_o0,
-                                                         c.mv_d1, c.mv_o1, c.mv_d2, c.mv_o2,
-                                                         nullptr);
+    k_matvec<NB, TR, false, XT, CIRC><<<grid, kMvCols, 0, s>>>(x, y, n, ell, c.mv_d0, c.mv_o0,
+                                                               c.mv_d1, c.mv_o1, c.mv_d2,
+                                                               c.mv_o2, nullptr);
 }
 
-template <typename XT>
+template <typename XT, bool CIRC = false>
 static cudaError_t matvec_any(const Ctx &c, const XT *x, double *y, int transpose,
                               cudaStream_t s, const double *sub) {
   const int n = (int)c.n, ell = (int)c.ell;
   const dim3 grid((unsigned)((n + kMvCols - 1) / kMvCols),
                   (unsigned)((ell + kMvRows - 1) / kMvRows));
   const bool bd2 = c.equation == AAO_WAVE_BD2;
-  if (bd2 && transpose) mv_sub<3, true>(c, grid, x, y, sub, s);
-  else if (bd2) mv_sub<3, false>(c, grid, x, y, sub, s);
-  else if (transpose) mv_sub<2, true>(c, grid, x, y, sub, s);
-  else mv_sub<2, false>(c, grid, x, y, sub, s);
+  if (bd2 && transpose) mv_sub<3, true, XT, CIRC>(c, grid, x, y, sub, s);
+  else if (bd2) mv_sub<3, false, XT, CIRC>(c, grid, x, y, sub, s);
+  else if (transpose) mv_sub<2, true, XT, CIRC>(c, grid, x, y, sub, s);
+  else mv_sub<2, false, XT, CIRC>(c, grid, x, y, sub, s);
   note_launch();
   return cudaGetLastError();
 }
 
-template <int NB, bool TR, typename XT>
+template <int NB, bool TR, typename XT, bool CIRC>
 static void mv_fx(const Ctx &c, dim3 grid, const XT *x, double *y, const double *sub,
                   cudaStream_t s) {
   const int n = (int)c.n, ell = (int)c.ell;
   const double mh = c.h / 6.0;
-  if (sub) k_matvec_fx<NB, TR, true, XT><<<grid, kMvCols, 0, s>>>(x, y, n, ell, mh, c.beta, sub);
-  else k_matvec_fx<NB, TR, false, XT><<<grid, kMvCols, 0, s>>>(x, y, n, ell, mh, c.beta, nullptr);
+  const double *beta = CIRC ? c.beta_p : c.beta;
+  if (sub)
+    k_matvec_fx<NB, TR, true, XT, CIRC><<<grid, kMvCols, 0, s>>>(x, y, n, ell, mh, beta, sub);
+  else
+    k_matvec_fx<NB, TR, false, XT, CIRC><<<grid, kMvCols, 0, s>>>(x, y, n, ell, mh, beta,
+                                                                  nullptr);
 }
 
 // Heat and BD2 take the fixed-point kernel; the literal heat form (whose M
-// coefficients differ between A0 and A1) the FP64 stencil.
-template <typename XT>
+// coefficients differ between A0 and A1) the FP64 stencil.  CIRC: the block
+// circulant P of Section 3 (constant step, time wrapped around) instead of A.
+template <typename XT, bool CIRC = false>
 static cudaError_t matvec_dispatch(const Ctx &c, const XT *x, double *y, int transpose,
                                    cudaStream_t s, const double *sub) {
-  if (c.equation == AAO_HEAT_LITERAL) return matvec_any(c, x, y, transpose, s, sub);
+  if (c.equation == AAO_HEAT_LITERAL) return matvec_any<XT, CIRC>(c, x, y, transpose, s, sub);
   const int n = (int)c.n, ell = (int)c.ell;
   const dim3 grid((unsigned)((n + kMvCols - 1) / kMvCols),
                   (unsigned)((ell + kFxRows - 1) / kFxRows));
   const bool bd2 = c.equation == AAO_WAVE_BD2;
-  if (bd2 && transpose) mv_fx<3, true>(c, grid, x, y, sub, s);
-  else if (bd2) mv_fx<3, false>(c, grid, x, y, sub, s);
-  else if (transpose) mv_fx<2, true>(c, grid, x, y, sub, s);
-  else mv_fx<2, false>(c, grid, x, y, sub, s);
+  if (bd2 && transpose) mv_fx<3, true, XT, CIRC>(c, grid, x, y, sub, s);
+  else if (bd2) mv_fx<3, false, XT, CIRC>(c, grid, x, y, sub, s);
+  else if (transpose) mv_fx<2, true, XT, CIRC>(c, grid, x, y, sub, s);
+  else mv_fx<2, false, XT, CIRC>(c, grid, x, y, sub, s);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_circ_residual(const Ctx &c, const float *z, double *y, int transpose,
+                                 cudaStream_t s, const double *sub) {
+  return matvec_dispatch<float, true>(c, z, y, transpose, s, sub);
+}
+
+// u = x - E y with (E y)_t = sigk_t (2 y_i - y_{i-1} - y_{i+1}), sigk_t =
+// (tau_t - tau) kappa / h (Section 2): the right-hand side of a Neumann term,
+// formed in FP64 for the refined FP32 preconditioner.
+__global__ void k_neumann_rhs(const double *__restrict__ x, const double *__restrict__ y,
+                              const double *__restrict__ sigk, double *__restrict__ u, int n,
+                              int64_t N) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(g / n);
+    const int i = (int)(g - (int64_t)t * n);
+    const double yc = y[g];
+    const double s = ((i > 0) ? y[g - 1] : 0.0) + ((i + 1 < n) ? y[g + 1] : 0.0);
+    u[g] = fma(-__ldg(&sigk[t]), fma(2.0, yc, -s), x[g]);
+  }
+}
+
+cudaError_t launch_neumann_rhs(const Ctx &c, const double *x, const double *y, double *u,
+                               cudaStream_t s) {
+  int64_t blocks = (c.N + kThreads - 1) / kThreads;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_neumann_rhs<<<(unsigned)blocks, kThreads, 0, s>>>(x, y, c.sigk, u, (int)c.n, c.N);
   note_launch();
   return cudaGetLastError();
 }

@@ -372,6 +372,12 @@ int refresh_constants(Ctx &c) {
     }
   }
   AAO_CK(c, upload((void **)&c.beta, beta));
+  // K coefficient of the circulant P (Section 3): the constant-step blocks
+  std::vector<double> beta_p((size_t)c.ell,
+                             c.equation == AAO_WAVE_BD2      ? c.tau * c.tau / c.h
+                             : c.equation == AAO_HEAT_LITERAL ? 1.0 / c.h
+                                                              : c.tau * c.kappa / c.h);
+  AAO_CK(c, upload((void **)&c.beta_p, beta_p));
   AAO_CK(c, upload((void **)&c.mv_d0, d0));
   AAO_CK(c, upload((void **)&c.mv_o0, o0));
   // A1 = -M (heat) or -2M (BD2), A2 = M (BD2)
@@ -440,7 +446,9 @@ WsLayout ws_layout(const Ctx &c, int restart) {
   L.inter_bytes = round_up(std::max(fft_inter_bytes_f32(c), fft_inter_bytes_f64(c)), kAlign);
   L.red = L.inter + L.inter_bytes;
   L.red_bytes = round_up((size_t)(kPartials + kSmall) * sizeof(double), kAlign);
-  L.vecs = L.red + L.red_bytes;
+  L.rf32 = L.red + L.red_bytes;
+  L.rf64 = L.rf32 + round_up((size_t)c.N * sizeof(float), kAlign);
+  L.vecs = L.rf64 + 2 * round_up((size_t)c.N * sizeof(double), kAlign);
   L.vec_bytes = round_up((size_t)c.N * sizeof(double), kAlign);
   const int nvec = restart > 0 ? (restart + 1) + restart + 2 : 0;
   L.total = L.vecs + (size_t)nvec * L.vec_bytes;
@@ -462,10 +470,11 @@ int check_ws(const Ctx &c, int restart) {
 
 // One application of P^{-1} (or P^{-T}); with yprev, of P^{-1}(x - E yprev).
 // YT = float stores an FP32 result (FP32 preconditioner only): the values
-// the FP32 inverse transform produces are then kept as they are.
+// the FP32 inverse transform produces are then kept as they are.  With base
+// (FP32 preconditioner, FP64 result) the result is base - P^{-1} x.
 template <typename YT>
 cudaError_t precond_once(Ctx &c, const double *x, const YT *yprev, YT *y, int tr,
-                         cudaStream_t s) {
+                         cudaStream_t s, const float *base = nullptr) {
   const aao::WsLayout L = aao::ws_layout(c, 0);
   void *spec = c.ws + L.spec;
   void *inter = L.inter_bytes ? c.ws + L.inter : nullptr;
@@ -480,14 +489,49 @@ cudaError_t precond_once(Ctx &c, const double *x, const YT *yprev, YT *y, int tr
   if (e != cudaSuccess) return e;
   return run(c, AAO_K_FFT_INVERSE, s, [&] {
     if constexpr (sizeof(YT) == 4) return aao::fft_inverse_f32_to_f32(c, spec, y, s, inter);
-    else return f32 ? aao::fft_inverse_f32(c, spec, y, s, inter)
+    else return f32 ? aao::fft_inverse_f32(c, spec, y, s, inter, base)
                     : aao::fft_inverse_f64(c, spec, y, s, inter);
   });
+}
+
+// Refined FP32 apply: z0 = P32^{-1} x, r = P z0 - x (exact fixed-point
+// circulant product), y = z0 - P32^{-1} r.  The error of y is the product of
+// two FP32 apply errors.  x and y may not overlap the refinement scratch.
+cudaError_t precond_refined(Ctx &c, const double *x, double *y, int tr, cudaStream_t s) {
+  const aao::WsLayout L = aao::ws_layout(c, 0);
+  float *z0 = reinterpret_cast<float *>(c.ws + L.rf32);
+  double *r = reinterpret_cast<double *>(c.ws + L.rf64);
+  cudaError_t e = precond_once<float>(c, x, nullptr, z0, tr, s);
+  if (e != cudaSuccess) return e;
+  e = run(c, AAO_K_REFINE, s, [&] { return aao::launch_circ_residual(c, z0, r, tr, s, x); });
+  if (e != cudaSuccess) return e;
+  return precond_once<double>(c, r, nullptr, y, tr, s, z0);
+}
+
+// P^{-1} x into an FP64 y in the context's precision mode.
+cudaError_t precond_apply64(Ctx &c, const double *x, double *y, int tr, cudaStream_t s) {
+  if (c.refine) return precond_refined(c, x, y, tr, s);
+  return precond_once<double>(c, x, nullptr, y, tr, s);
 }
 
 // Q_i^{-1} x (or Q_i^{-T} x) by y_0 = P^{-1} x, y_m = P^{-1}(x - E y_{m-1}).
 template <typename YT>
 cudaError_t neumann(Ctx &c, int terms, const double *x, YT *y, int tr, cudaStream_t s) {
+  if constexpr (sizeof(YT) == 8) {
+    if (c.refine) {
+      // refined terms: the right-hand side x - E y_{m-1} is formed in FP64
+      double *u = reinterpret_cast<double *>(c.ws + aao::ws_layout(c, 0).rf64) +
+                  round_up((size_t)c.N * sizeof(double), kAlign) / sizeof(double);
+      cudaError_t e = precond_refined(c, x, y, tr, s);
+      if (e != cudaSuccess || !c.variable_steps) return e;
+      for (int m = 1; m < terms; m++) {
+        e = run(c, AAO_K_REFINE, s, [&] { return aao::launch_neumann_rhs(c, x, y, u, s); });
+        if (e != cudaSuccess) return e;
+        if ((e = precond_refined(c, u, y, tr, s)) != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    }
+  }
   cudaError_t e = precond_once<YT>(c, x, nullptr, y, tr, s);
   if (e != cudaSuccess) return e;
   if (!c.variable_steps) return cudaSuccess;   // E = 0: every further term is P^{-1} x
@@ -527,7 +571,7 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
   // With the FP32 preconditioner the basis z_j = P^{-1} v_j is stored in FP32:
   // its values are FP32 numbers already, and flexible GMRES needs only that
   // A z_j is formed from the z_j that x is later built from.
-  const bool zf = precond >= 1 && c.prec == AAO_PREC_FP32;
+  const bool zf = precond >= 1 && c.prec == AAO_PREC_FP32 && !c.refine;
   std::vector<float *> Zf((size_t)m);
   for (int j = 0; j < m; j++) Zf[(size_t)j] = reinterpret_cast<float *>(Z[(size_t)j]);
   for (auto *v : V)
@@ -589,7 +633,7 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
           AAO_CK(c, precond_once<float>(c, V[(size_t)j], nullptr, Zf[(size_t)j], tr, s));
         else AAO_CK(c, neumann<float>(c, precond, V[(size_t)j], Zf[(size_t)j], tr, s));
       } else if (precond == 1) {
-        AAO_CK(c, precond_once<double>(c, V[(size_t)j], nullptr, Z[(size_t)j], tr, s));
+        AAO_CK(c, precond_apply64(c, V[(size_t)j], Z[(size_t)j], tr, s));
       } else if (precond >= 2) {
         AAO_CK(c, neumann<double>(c, precond, V[(size_t)j], Z[(size_t)j], tr, s));
       }
@@ -760,7 +804,8 @@ int aao_create(int64_t n, int64_t ell, double tau, int equation, aao_ctx **out) 
 void aao_destroy(aao_ctx *ctx) {
   if (!ctx) return;
   Ctx &c = ctx->c;
-  void *ptrs[] = {c.tab32, c.tab64, c.rec32, c.rec64, c.tw32, c.tw64, c.beta, c.mv_d0, c.mv_o0,
+  void *ptrs[] = {c.tab32, c.tab64, c.rec32, c.rec64, c.tw32, c.tw64, c.beta, c.beta_p,
+                  c.mv_d0, c.mv_o0,
                   c.sigk, c.sigk32};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -797,8 +842,10 @@ int aao_set_steps(aao_ctx *ctx, const double *tau_steps_host) {
 }
 
 int aao_set_precision(aao_ctx *ctx, int prec) {
-  if (!ctx || (prec != AAO_PREC_FP32 && prec != AAO_PREC_FP64)) return AAO_EINVAL;
-  ctx->c.prec = prec;
+  if (!ctx || (prec != AAO_PREC_FP32 && prec != AAO_PREC_FP64 && prec != AAO_PREC_FP32_REFINED))
+    return AAO_EINVAL;
+  ctx->c.refine = prec == AAO_PREC_FP32_REFINED;
+  ctx->c.prec = ctx->c.refine ? AAO_PREC_FP32 : prec;
   return AAO_OK;
 }
 
@@ -819,7 +866,7 @@ int aao_precond_apply(aao_ctx *ctx, const double *x, double *y, int transpose, v
   if (!ctx || !x || !y) return AAO_EINVAL;
   Ctx &c = ctx->c;
   if (overlap(x, y, (size_t)c.N * sizeof(double)) || check_ws(c, 0) != AAO_OK) return AAO_EINVAL;
-  AAO_CK(c, precond_once<double>(c, x, nullptr, y, transpose ? 1 : 0, as_stream(stream)));
+  AAO_CK(c, precond_apply64(c, x, y, transpose ? 1 : 0, as_stream(stream)));
   return AAO_OK;
 }
 

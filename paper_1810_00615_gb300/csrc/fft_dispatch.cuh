@@ -68,7 +68,8 @@ static cudaError_t run_forward(int64_t n, int64_t n_pad, const double *x, const 
 
 template <typename R, int L, typename OT>
 static cudaError_t run_inverse(int64_t n, int64_t n_pad, const cx<R> *spec, OT *y,
-                               const cx<R> *tw, cudaStream_t s, void *inter) {
+                               const cx<R> *tw, cudaStream_t s, void *inter,
+                               const float *base) {
   using S = Shape<R, L>;
   const int W = 2 * S::C;
   const int np = (int)((n + W - 1) / W);
@@ -82,7 +83,7 @@ static cudaError_t run_inverse(int64_t n, int64_t n_pad, const cx<R> *spec, OT *
       note_launch();
       const int ncx = np * S::C;
       const dim3 g2((unsigned)((ncx + kRowThreads - 1) / kRowThreads), (unsigned)(L / 16));
-      k_fft_inverse_rows<R, L, OT><<<g2, kRowThreads, 0, s>>>(ip, y, (int)n, ncx, tw);
+      k_fft_inverse_rows<R, L, OT><<<g2, kRowThreads, 0, s>>>(ip, y, (int)n, ncx, tw, base);
       note_launch();
       return cudaGetLastError();
     }
@@ -90,7 +91,7 @@ static cudaError_t run_inverse(int64_t n, int64_t n_pad, const cx<R> *spec, OT *
   auto kern = k_fft_inverse<R, L, OT>;
   const int g = persistent_grid(kern, S::T, S::SMEM, np);
   if (g <= 0) return cudaErrorInvalidConfiguration;
-  kern<<<g, S::T, S::SMEM, s>>>(spec, y, (int)n, n_pad, tw, np);
+  kern<<<g, S::T, S::SMEM, s>>>(spec, y, (int)n, n_pad, tw, np, base);
   note_launch();
   return cudaGetLastError();
 }
@@ -122,9 +123,10 @@ size_t inter_bytes_any(int64_t ell, int64_t n) {
 
 template <typename R, typename OT>
 cudaError_t inverse_any(int64_t ell, int64_t n, int64_t n_pad, const cx<R> *spec, OT *y,
-                        const cx<R> *tw, cudaStream_t s, void *inter) {
+                        const cx<R> *tw, cudaStream_t s, void *inter,
+                        const float *base = nullptr) {
   switch (ell) {
-#define AAO_I(L) case L: return run_inverse<R, L, OT>(n, n_pad, spec, y, tw, s, inter);
+#define AAO_I(L) case L: return run_inverse<R, L, OT>(n, n_pad, spec, y, tw, s, inter, base);
     AAO_FFT_CASES(AAO_I)
 #undef AAO_I
     default: return cudaErrorInvalidValue;

@@ -8,9 +8,10 @@ cudaError_t fft_forward_f32(const Ctx &c, const double *x, const double *y, void
                                          static_cast<cx<float> *>(spec), c.tw32, s, inter);
 }
 cudaError_t fft_inverse_f32(const Ctx &c, const void *spec, double *y, cudaStream_t s,
-                            void *inter) {
+                            void *inter, const float *base) {
   return fft::inverse_any<float, double>(c.ell, c.n, c.n_pad,
-                                         static_cast<const cx<float> *>(spec), y, c.tw32, s, inter);
+                                         static_cast<const cx<float> *>(spec), y, c.tw32, s, inter,
+                                         base);
 }
 cudaError_t fft_forward_f32_yf(const Ctx &c, const double *x, const float *y, void *spec,
                                cudaStream_t s, void *inter) {

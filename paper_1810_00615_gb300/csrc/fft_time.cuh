@@ -506,10 +506,12 @@ k_fft_inverse_panels(const cx<R> *__restrict__ spec, cx<R> *__restrict__ inter, 
   }
 }
 
+// With base (FP64 output only): y = base - (the transform), the correction
+// step of the refined FP32 preconditioner.
 template <typename R, int L, typename OT>
 __global__ void __launch_bounds__(kRowThreads)
 k_fft_inverse_rows(const cx<R> *__restrict__ inter, OT *__restrict__ y, int n, int ncx,
-                   const cx<R> *__restrict__ tw) {
+                   const cx<R> *__restrict__ tw, const float *__restrict__ base) {
   using S = Shape<R, L>;
   using P = Split<R, L>;
   constexpr int C = S::C, NS = L / 16;                        // last pass: radix 16, Ns = L/16
@@ -530,6 +532,13 @@ k_fft_inverse_rows(const cx<R> *__restrict__ inter, OT *__restrict__ y, int n, i
 #pragma unroll
   for (int r = 0; r < 16; r++) {
     const size_t o = (size_t)(j + r * NS) * n + i;
+    if constexpr (sizeof(OT) == 8) {
+      if (base) {
+        if (i < n) y[o] = to_f64(__ldg(&base[o])) - to_out<R, OT>(scale * v[r].re);
+        if (i + 1 < n) y[o + 1] = to_f64(__ldg(&base[o + 1])) - to_out<R, OT>(scale * v[r].im);
+        continue;
+      }
+    }
     if (i < n) y[o] = to_out<R, OT>(scale * v[r].re);
     if (i + 1 < n) y[o + 1] = to_out<R, OT>(scale * v[r].im);
   }
@@ -556,7 +565,7 @@ __device__ __forceinline__ void prefetch_spec(const CXT *__restrict__ spec, int 
 template <typename R, int L, typename OT>
 __global__ void __launch_bounds__(Shape<R, L>::T)
 k_fft_inverse(const cx<R> *__restrict__ spec, OT *__restrict__ y, int n, int64_t n_pad,
-              const cx<R> *__restrict__ tw, int npanels) {
+              const cx<R> *__restrict__ tw, int npanels, const float *__restrict__ base) {
   using S = Shape<R, L>;
   using PL = Passes<L>;
   constexpr int C = S::C, T = S::T, E = S::E, W = 2 * C;
@@ -592,7 +601,12 @@ k_fft_inverse(const cx<R> *__restrict__ spec, OT *__restrict__ y, int n, int64_t
 #pragma unroll 8
     for (int idx = threadIdx.x; idx < L * W; idx += T) {
       const int t = idx / W, w = idx - t * W, i = i0 + w;
-      if (i < n) y[(size_t)t * n + i] = to_out<R, OT>(scale * smr[2 * phys<C>(t, w >> 1) + (w & 1)]);
+      if (i < n) {
+        const size_t o = (size_t)t * n + i;
+        const OT v = to_out<R, OT>(scale * smr[2 * phys<C>(t, w >> 1) + (w & 1)]);
+        if constexpr (sizeof(OT) == 8) y[o] = base ? to_f64(__ldg(&base[o])) - v : v;
+        else y[o] = v;
+      }
     }
     __syncthreads();   // the work buffer is reused by the next panel
   }

@@ -46,6 +46,10 @@ extern "C" int aao_precond_apply_static(aao_ctx *ctx, const double *x, double *y
     const char *px = reinterpret_cast<const char *>(x), *py = reinterpret_cast<const char *>(y);
     if (px < py + vb && py < px + vb) return AAO_EINVAL;
   }
+  if (c.refine) {
+    c.last_error = "aao_precond_apply_static: the refined FP32 mode needs the workspace";
+    return AAO_EINVAL;
+  }
   const size_t elem = c.prec == AAO_PREC_FP32 ? sizeof(aao::cx<float>) : sizeof(aao::cx<double>);
   const size_t need = (size_t)c.nk * (size_t)c.n_pad * elem;
   if (need > kStaticScratchBytes) {
