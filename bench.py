@@ -36,6 +36,12 @@ METRIC = "all-at-once solve s & precond-apply HBM GB/s, mixed vs FP64 at 1e-10 r
 N_SPACE, ELL = 4095, 4096
 RESTART, RTOL, MAXIT = 30, 1e-10, 300
 WORKLOAD = "heat1d_p1_implicit_euler_n4095_ell4096_8modes_fgmres30_rtol1e-10"
+# The timed solve: FP32 preconditioner with one refinement sweep (FP64 outer
+# flexible GMRES).  The plain FP32 and the all-FP64 preconditioner are timed
+# on the same solve beside it.
+HEADLINE_PREC = "fp32_refined"
+PREC_LABEL = {"fp32_refined": "fp32 circulant + one refinement sweep",
+              "fp32": "fp32 circulant", "fp64": "fp64 circulant"}
 L2_BYTES = 135528448
 
 
@@ -229,13 +235,15 @@ def extra_rows(device, hbm_peak):
     sv = AllAtOnce(n, ell, 1.0 / ell, precision="fp32", restart=RESTART, device=device)
     sv.set_steps(syn.time_steps(ell, 0.5, syn.rng(3)))
     bb = sv.build_rhs(torch.from_numpy(syn.heat_initial(n)).to(device))
-    for pc in (1, 2, 3):
-        sv.solve(bb, restart=RESTART, rtol=RTOL, precond=pc)
-        info = {}
-        ms = _timed(lambda i: info.update(sv.solve(bb, restart=RESTART, rtol=RTOL,
-                                                   precond=pc)[1]), 3, stream)
-        rows[f"solve_steps_delta0.5_precond{pc}"] = {"ms": round(ms, 3), "iters": info["iters"],
-                                                     "relres": info["relres_true"]}
+    for prec in ("fp32", "fp32_refined"):
+        sv.set_precision(prec)
+        for pc in (1, 2, 3):
+            sv.solve(bb, restart=RESTART, rtol=RTOL, precond=pc)
+            info = {}
+            ms = _timed(lambda i: info.update(sv.solve(bb, restart=RESTART, rtol=RTOL,
+                                                       precond=pc)[1]), 3, stream)
+            rows[f"solve_steps_delta0.5_{prec}_precond{pc}"] = {
+                "ms": round(ms, 3), "iters": info["iters"], "relres": info["relres_true"]}
     del sv, bb
     torch.cuda.empty_cache()
     # BD2 wave, n = 8191, ell = 2048, 16-mode displacement and velocity
@@ -244,11 +252,14 @@ def extra_rows(device, hbm_peak):
                    device=device)
     u0, v0 = syn.wave_initial(nw, modes=16)
     bw = sw.build_rhs(torch.from_numpy(u0).to(device), torch.from_numpy(v0).to(device))
-    sw.solve(bw, restart=40, rtol=RTOL)
-    info = {}
-    ms = _timed(lambda i: info.update(sw.solve(bw, restart=40, rtol=RTOL)[1]), 3, stream)
-    rows["wave_bd2_n8191_ell2048_solve"] = {"ms": round(ms, 3), "iters": info["iters"],
-                                            "relres": info["relres_true"]}
+    wave = {}
+    for prec in ("fp32", "fp32_refined", "fp64"):
+        sw.set_precision(prec)
+        sw.solve(bw, restart=40, rtol=RTOL)
+        info = {}
+        ms = _timed(lambda i: info.update(sw.solve(bw, restart=40, rtol=RTOL)[1]), 2, stream)
+        wave[prec] = {"ms": round(ms, 3), "iters": info["iters"], "relres": info["relres_true"]}
+    rows["wave_bd2_n8191_ell2048_gmres40"] = wave
     del sw, bw
     torch.cuda.empty_cache()
     # adjoint pass, n = 16383, ell = 1024: forward solve, adjoint solve, gradients
@@ -264,12 +275,14 @@ def extra_rows(device, hbm_peak):
         lam, i2 = sa.adjoint_solve(U - obs, restart=RESTART, rtol=5e-9)
         gu, gk = sa.adjoint_grads(lam, U)
         res.update(fwd=i1["iters"], adj=i2["iters"])
-    adj(0)
-    ms = _timed(adj, 2, stream)
-    rows["adjoint_n16383_ell1024_pass"] = {"ms": round(ms, 3), "fwd_iters": res["fwd"],
-                                           "adj_iters": res["adj"],
-                                           "note": "forward solve to 5e-10, adjoint solve to "
-                                                   "5e-9 (FP64 floors 2.7e-10 / 2.5e-9)"}
+    adjr = {"note": "forward solve to 5e-10, adjoint solve to 5e-9 (FP64 floors "
+                    "2.7e-10 / 2.5e-9)"}
+    for prec in ("fp32", "fp32_refined"):
+        sa.set_precision(prec)
+        adj(0)
+        ms = _timed(adj, 2, stream)
+        adjr[prec] = {"ms": round(ms, 3), "fwd_iters": res["fwd"], "adj_iters": res["adj"]}
+    rows["adjoint_n16383_ell1024_pass"] = adjr
     del sa
     torch.cuda.empty_cache()
     # large heat workload, n = 65535: sweep over ell, FGMRES(20), FP32 vs FP64
@@ -281,7 +294,7 @@ def extra_rows(device, hbm_peak):
         sl = AllAtOnce(nl_, ell_, 1.0 / ell_, precision="fp32", restart=20, device=device)
         bl = sl.build_rhs(torch.from_numpy(syn.heat_initial(nl_)).to(device))
         entry = {}
-        for prec in ("fp32", "fp64"):
+        for prec in ("fp32", "fp32_refined", "fp64"):
             sl.set_precision(prec)
             sl.solve(bl, restart=20, rtol=2e-8)
             info = {}
@@ -290,6 +303,7 @@ def extra_rows(device, hbm_peak):
                            "relres": info["relres_true"]}
         entry["unknowns"] = nl_ * ell_
         entry["speedup_fp32_vs_fp64"] = round(entry["fp64"]["ms"] / entry["fp32"]["ms"], 3)
+        entry["speedup_refined_vs_fp64"] = round(entry["fp64"]["ms"] / entry["fp32_refined"]["ms"], 3)
         sweep[f"ell{ell_}"] = entry
         del sl, bl
         torch.cuda.empty_cache()
@@ -349,7 +363,7 @@ def run_gpu(args):
     hbm_peak, peak_kind = _peaks()
 
     u0 = syn.heat_initial(N_SPACE, modes=8)
-    solver = AllAtOnce(N_SPACE, ELL, 1.0 / ELL, precision="fp32", restart=RESTART,
+    solver = AllAtOnce(N_SPACE, ELL, 1.0 / ELL, precision=HEADLINE_PREC, restart=RESTART,
                        device=device)
     u0_d = torch.from_numpy(u0).to(device)
     b = solver.build_rhs(u0_d)
@@ -362,7 +376,7 @@ def run_gpu(args):
         return x, info
 
     for _ in range(max(args.warmup, 1)):
-        step("fp32")
+        step(HEADLINE_PREC)
     torch.cuda.synchronize()
 
     # ---- timed region: K mixed-precision solves
@@ -380,7 +394,7 @@ def run_gpu(args):
     for k in range(args.steps):
         flush.fill_(float(k))                      # L2 flush outside the step's events
         ev[k][0].record(stream)
-        x, info = step("fp32")
+        x, info = step(HEADLINE_PREC)
         ev[k][1].record(stream)
         infos.append(info)
     torch.cuda.synchronize()
@@ -398,21 +412,24 @@ def run_gpu(args):
     r = b - solver.matvec(x)
     relres = float(torch.linalg.norm(r) / torch.linalg.norm(b))
 
-    # ---- the all-FP64 form (same solve, FP64 preconditioner)
-    step("fp64")
-    torch.cuda.synchronize()
-    t64 = []
-    it64 = None
-    for k in range(max(1, min(args.steps, 3))):
-        flush.fill_(float(k))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, inf64 = step("fp64")
-        e1.record(stream)
+    # ---- the same solve with the plain FP32 and with the FP64 preconditioner
+    def timed_solves(prec):
+        step(prec)
         torch.cuda.synchronize()
-        t64.append(e0.elapsed_time(e1))
-        it64 = inf64["iters"]
-    solver.set_precision("fp32")
+        ts, its = [], None
+        for k in range(max(1, min(args.steps, 3))):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, inf = step(prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            its = inf["iters"]
+        return float(np.mean(ts)), its
+    t32, it32 = timed_solves("fp32")
+    t64, it64 = timed_solves("fp64")
+    solver.set_precision(HEADLINE_PREC)
 
     # ---- per-kernel profile of K more mixed solves (events around each kernel)
     solver.profile_read(reset=True)
@@ -420,12 +437,13 @@ def run_gpu(args):
     nprof = max(1, min(args.steps, 3))
     for k in range(nprof):
         flush.fill_(float(k))
-        step("fp32")
+        step(HEADLINE_PREC)
     torch.cuda.synchronize()
     prof = solver.profile_read(reset=True)
     solver.profile(False)
 
-    # ---- preconditioner apply throughput (FP32), inputs larger than L2
+    # ---- preconditioner apply throughput (plain FP32), inputs larger than L2
+    solver.set_precision("fp32")
     xs = [torch.randn(ELL, N_SPACE, dtype=torch.float64, device=device) for _ in range(2)]
     ys = [torch.empty_like(xs[0]) for _ in range(2)]
     for i in range(3):
@@ -446,6 +464,18 @@ def run_gpu(args):
     torch.cuda.synchronize()
     app_prof = solver.profile_read(reset=True)
     solver.profile(False)
+    # the refined apply (two FP32 applies and the exact residual P z0 - x)
+    solver.set_precision("fp32_refined")
+    for i in range(3):
+        solver.precond_apply(xs[i % 2], out=ys[i % 2])
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(napp):
+        solver.precond_apply(xs[i % 2], out=ys[i % 2])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    refined_ms = e0.elapsed_time(e1) / napp
+    solver.set_precision(HEADLINE_PREC)
     nk = ELL // 2 + 1
     Nel = N_SPACE * ELL
     spec_bytes = 8 * N_SPACE * nk                       # complex64 half spectrum
@@ -479,33 +509,38 @@ def run_gpu(args):
                     "unit": "GB/s", "frac": pk["frac"], "traffic": _traffic(dom),
                     "peak_kind": peak_kind}
     elif dom == "matvec":
-        # Four of the six matvecs of a solve are the fixed-point product
-        # w = A z - v of the FP32 basis (the other two, the residuals, run the
-        # same kernel on FP64 x).  Integer-ALU bound: the GB300 ALU pipe issues
-        # 64 lanes per clock per SM; achieved = ALU-pipe instructions per
-        # launch (ncu, committed summary) / the launch's event time here.
-        z32 = xs[0].float()
-        mv_reps = 20
+        # The solve's matvecs are the fixed-point product w = A z - v (Arnoldi,
+        # z FP64 with the refined preconditioner, FP32 with the plain one) and
+        # the residual A x - b (x FP64): one kernel.  Integer-ALU bound: the
+        # GB300 ALU pipe issues 64 lanes per clock per SM; achieved = ALU-pipe
+        # instructions per launch (ncu, committed summary) / event time here.
+        f32_basis = HEADLINE_PREC == "fp32"
+        z = xs[0].float() if f32_basis else xs[0]
         ts = []
-        for k in range(mv_reps + 3):
+        for k in range(23):
             flush.fill_(float(k))
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a0.record(stream)
-            solver.matvec_f32(z32, sub=xs[1], out=ys[0])
+            if f32_basis:
+                solver.matvec_f32(z, sub=xs[1], out=ys[0])
+            else:
+                solver.matvec(z, sub=xs[1], out=ys[0])
             a1.record(stream)
             torch.cuda.synchronize()
             if k >= 3:
                 ts.append(a0.elapsed_time(a1) * 1e-3)
         mv_s = float(np.median(ts))
-        alu = _profile_value("alu_inst_per_launch", "matvec_f32")
+        key = "matvec_f32" if f32_basis else "matvec_f64"
+        alu = _profile_value("alu_inst_per_launch", key)
         alu_peak = 152 * 64 * sm_mhz * 1e6 / 1e9                 # Gop/s
-        mv_bytes = Nel * (4 + 8 + 8)                              # z (FP32), v, w
+        mv_bytes = Nel * ((4 if f32_basis else 8) + 8 + 8)        # z, v, w
         achieved = alu / mv_s / 1e9 if alu else None
-        roofline = {"bound": "alu", "kernel": "matvec_f32: w = A z - v, fixed point",
+        roofline = {"bound": "alu",
+                    "kernel": f"{key}: w = A z - v, fixed point",
                     "achieved": round(achieved, 1) if achieved else None,
                     "peak": round(alu_peak, 1), "unit": "Gop/s",
                     "frac": round(achieved / alu_peak, 4) if achieved else None,
-                    "traffic": _traffic("matvec_f32"), "us": round(mv_s * 1e6, 1),
+                    "traffic": _traffic(key), "us": round(mv_s * 1e6, 1),
                     "algorithmic_bytes": mv_bytes,
                     "hbm_GB_s": round(mv_bytes / mv_s / 1e9, 1),
                     "hbm_frac": round(mv_bytes / mv_s / 1e9 / hbm_peak, 3),
@@ -554,16 +589,20 @@ def run_gpu(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N_SPACE, "ell": ELL, "restart": RESTART,
-                       "rtol": RTOL, "preconditioner": "fp32 circulant",
+                       "rtol": RTOL, "preconditioner": PREC_LABEL[HEADLINE_PREC],
                        "parallelism": f"replicas{world}",
                        "l2": "256 MiB buffer written before every step, outside its events"},
             "iters": infos[-1]["iters"], "relres_true": relres,
-            "fp64_solve_s": float(np.mean(t64)) / 1e3, "fp64_iters": it64,
-            "speedup_mixed_vs_fp64": float(np.mean(t64)) / ms,
+            "fp32_plain_solve_s": t32 / 1e3, "fp32_plain_iters": it32,
+            "fp64_solve_s": t64 / 1e3, "fp64_iters": it64,
+            "speedup_mixed_vs_fp64": t64 / ms,
             "precond_apply": {"us": round(1e3 * apply_ms, 2), "GB_s": round(apply_gbs, 1),
                               "frac_of_hbm": round(apply_gbs / hbm_peak, 3),
                               "bytes": bytes_apply, "peak_GB_s": hbm_peak,
                               "peak_kind": peak_kind, "kernels": per_kernel},
+            "precond_apply_refined": {"us": round(1e3 * refined_ms, 2),
+                                      "note": "FP32 apply, exact circulant residual, FP32 "
+                                              "correction; FP64 output"},
             "kernel_share": shares, "solve_kernels": solve_kernels, "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_v, "unit": "s", "h2d_bytes_per_step": 8 * N_SPACE,

@@ -155,6 +155,13 @@ int aao_neumann_apply(aao_ctx *ctx, int terms, const double *x, double *y,
 int aao_matvec(aao_ctx *ctx, const double *x, double *y, int transpose,
                void *stream);
 
+/* y = A x - sub or A^T x - sub in FP64 (Section 2): the matvec of aao_matvec
+ * with the subtraction fused, as the solver forms its residual A x - b and,
+ * with the FP64 preconditioned basis, its shifted Arnoldi product
+ * A z_j - v_j.  x, sub, y: device, N doubles; y overlaps neither. */
+int aao_matvec_sub(aao_ctx *ctx, const double *x, const double *sub, double *y, int transpose,
+                   void *stream);
+
 /* y = A x - sub or A^T x - sub (sub may be NULL: y = A x) as aao_matvec, for
  * an FP32 x (Section 2).  With sub this is exactly the product the
  * mixed-precision solver forms with its FP32 preconditioned basis in the

@@ -146,10 +146,16 @@ class AllAtOnce:
               "aao_neumann_apply", self._ctx)
         return y
 
-    def matvec(self, x, transpose=False, out=None, stream=None):
-        """y = A x (or A^T x) in FP64."""
+    def matvec(self, x, transpose=False, out=None, sub=None, stream=None):
+        """y = A x (or A^T x) in FP64; with sub, y = A x - sub (fused)."""
         x = _dev_f64(x, self.N, "x")
         y = self._out(out)
+        if sub is not None:
+            sub = _dev_f64(sub, self.N, "sub")
+            check(self.lib.aao_matvec_sub(self._ctx, x.data_ptr(), sub.data_ptr(), y.data_ptr(),
+                                          int(bool(transpose)), _stream(stream)),
+                  "aao_matvec_sub", self._ctx)
+            return y
         check(self.lib.aao_matvec(self._ctx, x.data_ptr(), y.data_ptr(), int(bool(transpose)),
                                   _stream(stream)), "aao_matvec", self._ctx)
         return y

@@ -888,6 +888,19 @@ int aao_matvec(aao_ctx *ctx, const double *x, double *y, int transpose, void *st
   return AAO_OK;
 }
 
+int aao_matvec_sub(aao_ctx *ctx, const double *x, const double *sub, double *y, int transpose,
+                   void *stream) {
+  if (!ctx || !x || !sub || !y) return AAO_EINVAL;
+  Ctx &c = ctx->c;
+  const size_t vb = (size_t)c.N * sizeof(double);
+  if (overlap(x, y, vb) || overlap(sub, y, vb)) return AAO_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] {
+    return aao::launch_matvec(c, x, y, transpose ? 1 : 0, s, sub);
+  }));
+  return AAO_OK;
+}
+
 int aao_matvec_f32(aao_ctx *ctx, const float *x, const double *sub, double *y, int transpose,
                    void *stream) {
   if (!ctx || !x || !y) return AAO_EINVAL;

@@ -4,8 +4,9 @@ profilers (ncu) and quick timing.
     python -m paper_1810_00615_gb300.profile_case --op precond --n 4095 --ell 4096 \\
         --prec fp32 --reps 3
 
---op precond | neumann | matvec | matvec_f32 | solve (matvec_f32: the product
-w = A z - v of an FP32 z, as the mixed solver forms it in its Arnoldi step).  Prints one line with the mean CUDA-
+--op precond | neumann | matvec | matvec_sub | matvec_f32 | solve (matvec_sub,
+matvec_f32: the fused product w = A z - v of an FP64 or FP32 z, as the solver
+forms it in its Arnoldi step).  Prints one line with the mean CUDA-
 event time per call.  Inputs are seeded standard-normal block vectors (or the
 8-mode heat initial data for `solve`).
 """
@@ -24,10 +25,10 @@ if ROOT not in sys.path:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", default="precond", choices=["precond", "neumann", "matvec", "matvec_f32", "solve"])
+    ap.add_argument("--op", default="precond", choices=["precond", "neumann", "matvec", "matvec_sub", "matvec_f32", "solve"])
     ap.add_argument("--n", type=int, default=4095)
     ap.add_argument("--ell", type=int, default=4096)
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp32_refined", "fp64"])
     ap.add_argument("--equation", default="heat")
     ap.add_argument("--terms", type=int, default=2)
     ap.add_argument("--reps", type=int, default=3)
@@ -46,6 +47,7 @@ def main(argv=None):
     x = torch.randn(a.ell, a.n, dtype=torch.float64, device="cuda", generator=g)
     y = torch.empty_like(x)
     x32 = x.float() if a.op == "matvec_f32" else None
+    x2 = torch.randn_like(x) if a.op == "matvec_sub" else None
     if a.op == "solve":
         b = s.build_rhs(torch.from_numpy(syn.heat_initial(a.n)).cuda())
 
@@ -56,6 +58,8 @@ def main(argv=None):
             s.neumann_apply(x, a.terms, out=y)
         elif a.op == "matvec":
             s.matvec(x, out=y)
+        elif a.op == "matvec_sub":
+            s.matvec(x, out=y, sub=x2)
         elif a.op == "matvec_f32":
             s.matvec_f32(x32, out=y, sub=x)
         else:

@@ -115,11 +115,14 @@ def test_matvec_f32_matches_oracle(n, ell, kind, transpose):
     # the FP64 entry point on the same values agrees as closely
     fp64 = to_host(a.matvec(torch.from_numpy(X).cuda(), transpose=transpose))
     assert rel_max(got, fp64) <= 1e-13
-    # the fused shifted-Arnoldi form y = A x - v
+    # the fused shifted-Arnoldi form y = A x - v, for FP32 and FP64 x
     V = rand_block(n, ell, 29 + n)
     fused = to_host(a.matvec_f32(_f32_dev(torch, X), transpose=transpose,
                                  sub=torch.from_numpy(V).cuda()))
     assert rel_max(fused, want - V) <= 1e-13
+    fused64 = to_host(a.matvec(torch.from_numpy(X).cuda(), transpose=transpose,
+                               sub=torch.from_numpy(V).cuda()))
+    assert rel_max(fused64, want - V) <= 1e-13
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
