@@ -144,6 +144,23 @@ __device__ __forceinline__ void st_hint(cx<R> *p, cx<R> v, unsigned long long po
   *p = v;
 #endif
 }
+// Two adjacent complex values (16 bytes for FP32, 32 for FP64) in one access;
+// p must be aligned to their combined size.
+template <typename R>
+__device__ __forceinline__ void st_hint2(cx<R> *p, cx<R> a, cx<R> b, unsigned long long pol) {
+  if constexpr (sizeof(R) == 4) {
+#if AAO_L2_HINTS
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
+                 ::"l"(p), "f"((float)a.re), "f"((float)a.im), "f"((float)b.re), "f"((float)b.im),
+                 "l"(pol) : "memory");
+#else
+    *reinterpret_cast<float4 *>(p) = make_float4(a.re, a.im, b.re, b.im);
+#endif
+  } else {
+    st_hint(p, a, pol);
+    st_hint(p + 1, b, pol);
+  }
+}
 template <typename R>
 __device__ __forceinline__ cx<R> ld_hintc(const cx<R> *p, unsigned long long pol) {
 #if AAO_L2_HINTS
@@ -161,6 +178,24 @@ __device__ __forceinline__ cx<R> ld_hintc(const cx<R> *p, unsigned long long pol
 #else
   return *p;
 #endif
+}
+template <typename R>
+__device__ __forceinline__ void ld_hint2(const cx<R> *p, cx<R> &a, cx<R> &b,
+                                         unsigned long long pol) {
+  if constexpr (sizeof(R) == 4) {
+#if AAO_L2_HINTS
+    float w, x, y, z;
+    asm("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(w), "=f"(x), "=f"(y), "=f"(z) : "l"(p), "l"(pol));
+#else
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    const float w = v.x, x = v.y, y = v.z, z = v.w;
+#endif
+    a.re = w; a.im = x; b.re = y; b.im = z;
+  } else {
+    a = ld_hintc(p, pol);
+    b = ld_hintc(p + 1, pol);
+  }
 }
 
 template <typename R> __device__ __forceinline__ R from_f64(double x);
@@ -341,6 +376,8 @@ cudaError_t launch_rhs(const Ctx &c, const double *u0, const double *v0, double 
 // Uses `red` (device scratch of at least red_bytes) for block partials and
 // writes the final sums to out (device).
 int  red_blocks(int64_t N);
+cudaError_t launch_norms2(const double *a, const double *b, int64_t N, double *partials,
+                          double *out, cudaStream_t s);
 cudaError_t launch_multidot(const double *const *V, int nv, const double *w, int64_t N,
                             bool with_norm, double *partials, double *out, cudaStream_t s);
 // w -= sum_j hf[j] h[j] V_j (h on device, hf host factors, NULL = 1);

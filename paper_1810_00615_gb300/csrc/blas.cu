@@ -502,6 +502,28 @@ static void run_multidot(const Ptrs8 &P, const double *w, int64_t N, int nb, dou
   k_multidot<NV, NORM><<<nb, kThreads, 0, s>>>(P, w, N, partials); note_launch();
 }
 
+// out[0] = <a, a>, out[1] = <b, b> in one pass over both vectors.
+__global__ void __launch_bounds__(kThreads)
+k_norms2(const double *__restrict__ a, const double *__restrict__ b, int64_t N,
+         double *__restrict__ partials) {
+  double acc[2] = {0.0, 0.0};
+  for (int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x; g < N;
+       g += (int64_t)gridDim.x * kThreads) {
+    const double av = a[g], bv = b[g];
+    acc[0] = fma(av, av, acc[0]);
+    acc[1] = fma(bv, bv, acc[1]);
+  }
+  block_store<2>(acc, partials);
+}
+
+cudaError_t launch_norms2(const double *a, const double *b, int64_t N, double *partials,
+                          double *out, cudaStream_t s) {
+  const int nb = red_blocks(N);
+  k_norms2<<<nb, kThreads, 0, s>>>(a, b, N, partials); note_launch();
+  k_finish<<<2, 32, 0, s>>>(partials, nb, 2, out); note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_multidot(const double *const *V, int nv, const double *w, int64_t N,
                             bool with_norm, double *partials, double *out, cudaStream_t s) {
   const int nb = red_blocks(N);

@@ -590,8 +590,14 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
     if ((e = fetch(d_nr, 1)) != cudaSuccess) return e;
     return cudaStreamSynchronize(s);
   };
-  AAO_CK(c, norm2(b));
+  // ||b||^2 and ||x0||^2 in one pass: a zero initial guess makes the first
+  // residual -b, so the first cycle needs no matvec (V_0 aliases b, the sign
+  // goes into its lazy scale)
+  AAO_CK(c, run(c, AAO_K_DOTS, s, [&] { return aao::launch_norms2(b, x, N, red, d_nr, s); }));
+  AAO_CK(c, fetch(d_nr, 2));
+  AAO_CK(c, cudaStreamSynchronize(s));
   const double bnorm = std::sqrt(hs[320]);
+  bool x0_zero = hs[321] == 0.0;
   if (!std::isfinite(bnorm)) return AAO_ENUMERIC;
   if (bnorm == 0.0) {
     AAO_CK(c, cudaMemsetAsync(x, 0, vb, s));
@@ -604,11 +610,24 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
   auto Hij = [&](int i, int j) -> double & { return H[(size_t)i * m + j]; };
   int iters = 0, restarts = 0, status = AAO_ENOCONV, stalled = 0;
   double relres_true = 1.0, est = 1.0, best = INFINITY;
+  double *const v0_slot = V[0];
   for (;;) {
-    // V_0 = A x - b = -r (one fused pass); v_0 = -V_0 / beta
-    AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] { return aao::launch_matvec(c, x, V[0], tr, s, b); }));
-    AAO_CK(c, norm2(V[0]));
-    const double beta = std::sqrt(hs[320]);
+    double beta;
+    double v0_sign;
+    if (x0_zero) {
+      // x = 0: r = b; V_0 = b read in place, v_0 = V_0 / beta
+      V[0] = const_cast<double *>(b);
+      beta = bnorm;
+      v0_sign = 1.0;
+      x0_zero = false;
+    } else {
+      // V_0 = A x - b = -r (one fused pass); v_0 = -V_0 / beta
+      V[0] = v0_slot;
+      AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] { return aao::launch_matvec(c, x, V[0], tr, s, b); }));
+      AAO_CK(c, norm2(V[0]));
+      beta = std::sqrt(hs[320]);
+      v0_sign = -1.0;
+    }
     relres_true = beta / bnorm;
     if (!std::isfinite(beta)) { status = AAO_ENUMERIC; break; }
     if (relres_true <= rtol) { status = AAO_OK; break; }
@@ -622,7 +641,7 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
       stalled = 0;
     }
     if (relres_true < best) best = relres_true;
-    sc[0] = -1.0 / beta;
+    sc[0] = v0_sign / beta;
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int jd = 0;

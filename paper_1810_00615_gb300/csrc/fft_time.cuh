@@ -345,8 +345,7 @@ k_fft_forward(const double *__restrict__ x, const YT *__restrict__ y,
       const int i = i0 + 2 * c;
       cx<R> *dst = spec + (size_t)k * n_pad + i;
       if (i + 1 < n) {
-        st_hint(dst, X, pol_keep);
-        st_hint(dst + 1, Y, pol_keep);
+        st_hint2(dst, X, Y, pol_keep);        // i even: the pair is 16/32-byte aligned
       } else if (i < n) {
         st_hint(dst, X, pol_keep);
       }
@@ -447,8 +446,7 @@ k_fft_forward_panels(const cx<R> *__restrict__ inter, cx<R> *__restrict__ spec, 
       const int i = i0 + 2 * c;
       cx<R> *dst = spec + (size_t)k * n_pad + i;
       if (i + 1 < n) {
-        st_hint(dst, X, pol_keep);
-        st_hint(dst + 1, Y, pol_keep);
+        st_hint2(dst, X, Y, pol_keep);        // i even: the pair is 16/32-byte aligned
       } else if (i < n) {
         st_hint(dst, X, pol_keep);
       }
@@ -484,8 +482,8 @@ k_fft_inverse_panels(const cx<R> *__restrict__ spec, cx<R> *__restrict__ inter, 
       const int i = i0 + 2 * c;
       const cx<R> *src = spec + (size_t)k * n_pad + i;
       cx<R> A = mk((R)0, (R)0), B = mk((R)0, (R)0);
-      if (i < n) A = ld_hintc(src, pol_done);
-      if (i + 1 < n) B = ld_hintc(src + 1, pol_done);
+      if (i + 1 < n) ld_hint2(src, A, B, pol_done);   // i even: aligned pair
+      else if (i < n) A = ld_hintc(src, pol_done);
       if (k == 0 || 2 * k == L) { A.im = (R)0; B.im = (R)0; }
       sm[phys<C>(k, c)] = mk(A.re - B.im, A.im + B.re);
       if (k > 0 && 2 * k < L) sm[phys<C>(L - k, c)] = mk(A.re + B.im, B.re - A.im);
@@ -588,8 +586,8 @@ k_fft_inverse(const cx<R> *__restrict__ spec, OT *__restrict__ y, int n, int64_t
       const int i = i0 + 2 * c;
       const cx<R> *src = spec + (size_t)k * n_pad + i;
       cx<R> A = mk((R)0, (R)0), B = mk((R)0, (R)0);
-      if (i < n) A = ld_hintc(src, pol_done);
-      if (i + 1 < n) B = ld_hintc(src + 1, pol_done);
+      if (i + 1 < n) ld_hint2(src, A, B, pol_done);   // i even: aligned pair
+      else if (i < n) A = ld_hintc(src, pol_done);
       if (k == 0 || 2 * k == L) { A.im = (R)0; B.im = (R)0; }
       // Z = A + i B for the pair of real outputs; Hermitian extension for L-k
       sm[phys<C>(k, c)] = mk(A.re - B.im, A.im + B.re);
