@@ -281,6 +281,8 @@ struct Ctx {
   cx<double> *tw64 = nullptr;
   double *beta = nullptr;         // per-step K coefficient tau_t kappa / h (ell)
   double *beta_p = nullptr;       // K coefficient of the circulant P (constant step) (ell)
+  struct MvRow *mv_rows = nullptr;     // fixed-point matvec: per-step combination of A
+  struct MvRow *mv_rows_p = nullptr;   // the same for the circulant P
   bool refine = false;            // FP32 preconditioner with one refinement sweep
   double *mv_d0 = nullptr;        // per-step diagonal of A0^t (ell)
   double *mv_o0 = nullptr;        // per-step off-diagonal of A0^t (ell)
@@ -314,6 +316,19 @@ struct aao_ctx {
 namespace aao {
 
 // Workspace layout (offsets in bytes from ws, each 256-byte aligned).
+// Output stage of the fixed-point matvec for one time step: with the exact
+// integer sums S_M = q_t - q_{t-1} (...) and S_K = s_t,
+//   (A x)_t = mh S_M + beta_t S_K = coef * (S_main + frac 2^-64 * S_other),
+// main = K when beta_t > mh (coef = beta_t, frac = mh / beta_t), else M
+// (coef = mh, frac = beta_t / mh), so 0 < frac <= 1 and the sum stays exact
+// up to the truncation of the product (< 1 unit).
+struct MvRow {
+  double coef;
+  unsigned long long frac;
+  int main_k;
+  int pad;
+};
+
 struct WsLayout {
   size_t spec = 0, spec_bytes = 0;
   size_t inter = 0, inter_bytes = 0;   // two-kernel forward FFT scratch (0: none)

@@ -144,10 +144,12 @@ k_matvec(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
 // (transpose: t+1, t+2 instead of t-1, t-2).  Each warp converts its tile of
 // x (its 32 columns, one halo column each side, the time steps it needs) to
 // 64-bit fixed point at the tile's largest exponent, forms both sums exactly
-// in integers (no cancellation error however much the terms cancel), rounds
-// them once to FP64 and finishes with two FMAs.  GB300 issues integer
-// operations at 64 per clock per SM and FP64 at 2, so this replaces five of
-// the seven FP64 operations per element of the FP64 form with integer work.
+// in integers (no cancellation error however much the terms cancel), joins
+// them into one integer with the ratio of their coefficients (a 64-bit
+// fixed-point fraction <= 1, one high multiply), rounds that once to FP64
+// and finishes with one FMA.  GB300 issues integer operations at 64 per
+// clock per SM and FP64 at 2, so this replaces six of the seven FP64
+// operations per element of the FP64 form with integer work.
 // The largest element of a tile keeps 58 bits (FP32 input: 34 binades below
 // it are exact, FP64 input: 5); anything smaller is truncated at 2^-57 of
 // the tile maximum.  x is FP64 (the solution, the public matvec) or FP32
@@ -217,8 +219,8 @@ __device__ __forceinline__ double fx_to_f64(long long S, int unit) {
 #endif
 template <int NB, bool TR, bool SUB, typename XT, bool CIRC>
 __global__ void __launch_bounds__(kMvCols, AAO_MVFX_MINB)
-k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell, double mh,
-            const double *__restrict__ beta, const double *__restrict__ sub) {
+k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
+            const MvRow *__restrict__ rows, const double *__restrict__ sub) {
   constexpr int R = kFxRows, IN = R + NB - 1;   // input time steps per tile
   constexpr int kWarps = kMvCols / 32;
   using F = Fx<XT>;
@@ -322,11 +324,17 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell, do
       if (k >= NB - 1 && k < IN && col_ok && t_ok(t)) {
         const long long sm = (NB == 2) ? q - q1 : q - 2 * q1 + q2;
         const long long sk = 2 * X - P;
-        const double bt = __ldg(&beta[t]);
+        // T = S_main + frac S_other, exact up to the truncated product; one
+        // rounding to FP64 and one FMA
+        const MvRow rw = rows[t];
+        const long long s_main = rw.main_k ? sk : sm, s_oth = rw.main_k ? sm : sk;
+        const unsigned long long so_neg = (unsigned long long)(s_oth >> 63);
+        const unsigned long long so_abs = ((unsigned long long)s_oth ^ so_neg) - so_neg;
+        const long long prod = (long long)__umul64hi(so_abs, rw.frac);
+        const long long T = s_main + (so_neg ? -prod : prod);
         constexpr bool RANGE = sizeof(XT) == 8;
-        const double skd = fx_to_f64<RANGE>(sk, unit), smd = fx_to_f64<RANGE>(sm, unit);
-        const double acc = SUB ? fma(bt, skd, -vk) : bt * skd;
-        py[(int64_t)k * step] = fma(mh, smd, acc);
+        const double td = fx_to_f64<RANGE>(T, unit);
+        py[(int64_t)k * step] = SUB ? fma(rw.coef, td, -vk) : rw.coef * td;
       }
       q2 = q1;
       q1 = q;
@@ -367,13 +375,11 @@ template <int NB, bool TR, typename XT, bool CIRC>
 static void mv_fx(const Ctx &c, dim3 grid, const XT *x, double *y, const double *sub,
                   cudaStream_t s) {
   const int n = (int)c.n, ell = (int)c.ell;
-  const double mh = c.h / 6.0;
-  const double *beta = CIRC ? c.beta_p : c.beta;
+  const MvRow *rows = CIRC ? c.mv_rows_p : c.mv_rows;
   if (sub)
-    k_matvec_fx<NB, TR, true, XT, CIRC><<<grid, kMvCols, 0, s>>>(x, y, n, ell, mh, beta, sub);
+    k_matvec_fx<NB, TR, true, XT, CIRC><<<grid, kMvCols, 0, s>>>(x, y, n, ell, rows, sub);
   else
-    k_matvec_fx<NB, TR, false, XT, CIRC><<<grid, kMvCols, 0, s>>>(x, y, n, ell, mh, beta,
-                                                                  nullptr);
+    k_matvec_fx<NB, TR, false, XT, CIRC><<<grid, kMvCols, 0, s>>>(x, y, n, ell, rows, nullptr);
 }
 
 // Heat and BD2 take the fixed-point kernel; the literal heat form (whose M

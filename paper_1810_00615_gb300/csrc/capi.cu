@@ -378,6 +378,24 @@ int refresh_constants(Ctx &c) {
                              : c.equation == AAO_HEAT_LITERAL ? 1.0 / c.h
                                                               : c.tau * c.kappa / c.h);
   AAO_CK(c, upload((void **)&c.beta_p, beta_p));
+  // fixed-point matvec output stages for A (per step) and P (constant step)
+  auto mvrow = [&](double b) {
+    aao::MvRow r{};
+    const bool k_main = b > mh;
+    r.coef = k_main ? b : mh;
+    const double frac = k_main ? mh / b : b / mh;          // in (0, 1]
+    const double scaled = std::ldexp(frac, 64);              // frac 2^64, exact for frac >= 2^-11
+    r.frac = scaled >= 18446744073709551616.0 ? ~0ull : (unsigned long long)std::nearbyint(scaled);
+    r.main_k = k_main ? 1 : 0;
+    return r;
+  };
+  std::vector<aao::MvRow> rows_a((size_t)c.ell), rows_p((size_t)c.ell);
+  for (int64_t t = 0; t < c.ell; t++) {
+    rows_a[(size_t)t] = mvrow(beta[(size_t)t]);
+    rows_p[(size_t)t] = mvrow(beta_p[(size_t)t]);
+  }
+  AAO_CK(c, upload((void **)&c.mv_rows, rows_a));
+  AAO_CK(c, upload((void **)&c.mv_rows_p, rows_p));
   AAO_CK(c, upload((void **)&c.mv_d0, d0));
   AAO_CK(c, upload((void **)&c.mv_o0, o0));
   // A1 = -M (heat) or -2M (BD2), A2 = M (BD2)
@@ -824,7 +842,7 @@ void aao_destroy(aao_ctx *ctx) {
   if (!ctx) return;
   Ctx &c = ctx->c;
   void *ptrs[] = {c.tab32, c.tab64, c.rec32, c.rec64, c.tw32, c.tw64, c.beta, c.beta_p,
-                  c.mv_d0, c.mv_o0,
+                  c.mv_rows, c.mv_rows_p, c.mv_d0, c.mv_o0,
                   c.sigk, c.sigk32};
   for (void *p : ptrs)
     if (p) cudaFree(p);

@@ -90,6 +90,16 @@ def block_vector(n: int, ell: int, gen: np.random.Generator) -> np.ndarray:
     return gen.standard_normal((ell, n))
 
 
+def parabola_load(n: int) -> np.ndarray:
+    """Load vector (u0, phi_i) of the paper's Table 1/2 initial condition
+    u0(x) = x(1 - x) against the P1 hats on the uniform grid, in closed form:
+    h x_i (1 - x_i) - h^3 / 6.  It is M times the L2 projection of u0, i.e.
+    the first block of the heat right-hand side."""
+    h = 1.0 / (n + 1)
+    x = grid(n)
+    return h * x * (1.0 - x) - h ** 3 / 6.0
+
+
 def heat_initial(n: int, modes: int = 8, seed: int = DEFAULT_SEED) -> np.ndarray:
     """Projected u0 for the heat workloads (seeded sine modes)."""
     g = rng(seed)

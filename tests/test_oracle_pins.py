@@ -55,6 +55,16 @@ def test_p1_mass_row_sums_and_stiffness_nullspace():
     np.testing.assert_allclose((K @ x)[1:-1], 0.0, atol=1e-12)
 
 
+def test_parabola_load_matches_quadrature_projection():
+    """The closed-form load vector of u0 = x(1 - x) (the paper's Table 1/2
+    initial data) equals M times the oracle's quadrature L2 projection."""
+    for n in (1, 5, 63, 320):
+        u = fem.l2_projection(lambda x: x * (1.0 - x), n)
+        M, _ = fem.p1_matrices(n)
+        f = syn.parabola_load(n)
+        assert np.max(np.abs(M @ u - f)) <= 1e-13 * np.max(np.abs(f))
+
+
 def test_l2_projection_quadrature_matches_sine_closed_form():
     n = 33
     c = np.array([0.7, -0.2, 0.05])
