@@ -155,6 +155,14 @@ k_matvec(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
 // the tile maximum.  x is FP64 (the solution, the public matvec) or FP32
 // (the preconditioned basis of the mixed solver).
 constexpr int kFxRows = 32;   // output time steps per warp tile
+#ifndef AAO_MVFX_U1
+#define AAO_MVFX_U1 16     // unroll of the exponent pass (loads in flight)
+#endif
+#ifndef AAO_MVFX_PRE
+#define AAO_MVFX_PRE 2     // steps of prefetch in the walk
+#endif
+constexpr int kFxU1 = AAO_MVFX_U1;
+
 
 template <typename XT> struct Fx;
 template <> struct Fx<float> {
@@ -260,7 +268,7 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
   {
     const XT *p = px0;
     int t = t0;
-#pragma unroll 4
+#pragma unroll kFxU1
     for (int k = 0; k < IN; k++, p += step, t += dir)
       if (z_ok(t)) em = max(em, F::exp(__ldg(zaddr(t, p))));
   }
@@ -284,7 +292,7 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
 
   // pass 2: walk the steps; x and the subtrahend come kPre steps ahead so
   // their latency hides behind the integer work of the steps in between
-  constexpr int kPre = 4;
+  constexpr int kPre = AAO_MVFX_PRE;
   const double *pv0 = SUB ? sub + (int64_t)t0 * n + ic : nullptr;
   XT zpre[kPre];
   double vpre[kPre];
