@@ -286,7 +286,7 @@ def extra_rows(device, hbm_peak):
     del sa
     torch.cuda.empty_cache()
     # the paper's Table 1 (uniform steps) and Table 2 (Neumann on the perturbed
-    # grid) problems with ell = 1024: u0 = x(1 - x), tolerance 1e-5, FP64
+    # grid) problems, ell = 768, 1024, 1440: u0 = x(1 - x), tolerance 1e-5, FP64
     # preconditioner as in the paper (Table 2's grids are seeded draws of the
     # same law, not the paper's).  Paper times: Table 1, 32 processes.
     def parabola_rhs(n_, ell_):
@@ -294,11 +294,14 @@ def extra_rows(device, hbm_peak):
         B[0] = torch.from_numpy(syn.parabola_load(n_)).to(device)
         return B
     t1 = {}
-    paper_t1 = {320: 6.07, 512: 11.75, 768: 16.12}
-    for n_ in (320, 512, 768):
-        s1 = AllAtOnce(n_, 1024, 1.0 / 1024, precision="fp64", restart=RESTART, device=device)
-        b1 = parabola_rhs(n_, 1024)
-        entry = {"paper_s_32_processes": paper_t1[n_]}
+    paper_t1 = {(768, 320): 3.34, (768, 512): 6.69, (768, 768): 9.65,
+                (1024, 320): 6.07, (1024, 512): 11.75, (1024, 768): 16.12,
+                (1440, 320): 13.06, (1440, 512): 22.50, (1440, 768): 32.41,
+                (1440, 1568): 63.30}
+    for (ell_, n_), paper_s in paper_t1.items():
+        s1 = AllAtOnce(n_, ell_, 1.0 / ell_, precision="fp64", restart=RESTART, device=device)
+        b1 = parabola_rhs(n_, ell_)
+        entry = {"paper_s_32_processes": paper_s}
         for prec in ("fp64", "fp32_refined"):
             s1.set_precision(prec)
             s1.solve(b1, restart=RESTART, rtol=1e-5)
@@ -306,16 +309,17 @@ def extra_rows(device, hbm_peak):
             ms = _timed(lambda i: info.update(s1.solve(b1, restart=RESTART, rtol=1e-5)[1]), 3,
                         stream)
             entry[prec] = {"ms": round(ms, 3), "iters": info["iters"]}
-        t1[f"n{n_}"] = entry
+        t1[f"ell{ell_}_n{n_}"] = entry
         del s1
-    rows["paper_table1_ell1024_tol1e-5"] = t1
+    rows["paper_table1_tol1e-5"] = t1
     t2 = {}
-    for tag, n_ in (("d", 512), ("e", 768), ("f", 1024)):
-        s2 = AllAtOnce(n_, 1024, 1.0 / 1024, precision="fp64", restart=RESTART, device=device)
-        b2 = parabola_rhs(n_, 1024)
+    for tag, n_, ell_ in (("a", 320, 768), ("b", 512, 768), ("c", 768, 768), ("d", 512, 1024),
+                          ("e", 768, 1024), ("f", 1024, 1024)):
+        s2 = AllAtOnce(n_, ell_, 1.0 / ell_, precision="fp64", restart=RESTART, device=device)
+        b2 = parabola_rhs(n_, ell_)
         tab = {}
         for delta in (0.9, 0.7, 0.5, 0.3, 0.1):
-            s2.set_steps(syn.time_steps(1024, delta, syn.rng(7)))
+            s2.set_steps(syn.time_steps(ell_, delta, syn.rng(7)))
             its, tms = [], []
             for terms in (1, 2, 3):
                 s2.solve(b2, restart=RESTART, rtol=1e-5, precond=terms)
@@ -326,9 +330,9 @@ def extra_rows(device, hbm_peak):
                 tms.append(ms)
             tab[f"delta{delta}"] = {"iters_i123": its, "delta21_ms": round(tms[1] - tms[0], 3),
                                     "ms_i1": round(tms[0], 3)}
-        t2[f"({tag}) n{n_}"] = tab
+        t2[f"({tag}) n{n_} ell{ell_}"] = tab
         del s2
-    rows["paper_table2_ell1024_tol1e-5_fp64"] = t2
+    rows["paper_table2_tol1e-5_fp64"] = t2
     torch.cuda.empty_cache()
     # large heat workload, n = 65535: sweep over ell, FGMRES(20), FP32 vs FP64
     # preconditioner.  The FP64 representation floor of the solution is up to

@@ -80,8 +80,9 @@ typedef struct {
 } aao_solve_info;
 
 /* Create a context for an n x ell all-at-once system with constant step tau
- * (Section 2; tau = T/ell with T = 1 in the paper).  ell must be a power of
- * two, 1 <= ell <= 4096; 1 <= n <= 16383.  Computes the per-frequency
+ * (Section 2; tau = T/ell with T = 1 in the paper).  ell = 2^a 3^b 5^c,
+ * 1 <= ell <= 4096 (powers of two use radix-16 time FFTs, the other lengths,
+ * e.g. the paper's 768 and 1440, mixed-radix ones); 1 <= n <= 16383.  Computes the per-frequency
  * tridiagonal symbols A0 + w_k A1 (+ w_k^2 A2), w_k = exp(-2 pi i k/ell),
  * k = 0..ell/2 (Section 3, Fourier diagonalisation of P), in FP64 on the
  * host and uploads them; the context owns that device memory.

@@ -763,6 +763,14 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
   return status;
 }
 
+// ell = 2^a 3^b 5^c: powers of two run the radix-16 kernels, the rest the
+// mixed-radix kernels.
+bool fft_length_ok(int64_t ell) {
+  for (int64_t r : {2, 3, 5})
+    while (ell % r == 0) ell /= r;
+  return ell == 1;
+}
+
 }  // namespace
 
 extern "C" {
@@ -790,7 +798,7 @@ int aao_create(int64_t n, int64_t ell, double tau, int equation, aao_ctx **out) 
   if (n < 1 || !(tau > 0.0) || !std::isfinite(tau)) return AAO_EINVAL;
   if (equation != AAO_HEAT && equation != AAO_WAVE_BD2 && equation != AAO_HEAT_LITERAL)
     return AAO_EINVAL;
-  if (ell < 1 || ell > kMaxEll || (ell & (ell - 1)) != 0 || n > kMaxN) return AAO_EUNSUPPORTED;
+  if (ell < 1 || ell > kMaxEll || !fft_length_ok(ell) || n > kMaxN) return AAO_EUNSUPPORTED;
   aao_ctx *h = new (std::nothrow) aao_ctx();
   if (!h) return AAO_ENOMEM;
   Ctx &c = h->c;

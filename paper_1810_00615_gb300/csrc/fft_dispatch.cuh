@@ -1,6 +1,7 @@
 // Instantiation and dispatch of the time-axis FFT kernels for one real type.
 #pragma once
 #include "fft_time.cuh"
+#include "fft_mixed.cuh"
 
 namespace aao {
 namespace fft {
@@ -107,7 +108,7 @@ cudaError_t forward_any(int64_t ell, int64_t n, int64_t n_pad, const double *x, 
 #define AAO_F(L) case L: return run_forward<R, L, YT>(n, n_pad, x, y, sigk, spec, tw, s, inter);
     AAO_FFT_CASES(AAO_F)
 #undef AAO_F
-    default: return cudaErrorInvalidValue;
+    default: return run_forward_mixed<R, YT>(ell, n, n_pad, x, y, sigk, spec, tw, s);
   }
 }
 
@@ -129,7 +130,7 @@ cudaError_t inverse_any(int64_t ell, int64_t n, int64_t n_pad, const cx<R> *spec
 #define AAO_I(L) case L: return run_inverse<R, L, OT>(n, n_pad, spec, y, tw, s, inter, base);
     AAO_FFT_CASES(AAO_I)
 #undef AAO_I
-    default: return cudaErrorInvalidValue;
+    default: return run_inverse_mixed<R, OT>(ell, n, n_pad, spec, y, tw, s, base);
   }
 }
 

@@ -47,7 +47,8 @@ def test_create_rejects_bad_arguments_without_a_device(lib):
     assert lib.aao_create(63, 64, 0.0, K.AAO_HEAT, C.byref(ctx)) == K.AAO_EINVAL
     assert lib.aao_create(63, 64, -1.0, K.AAO_HEAT, C.byref(ctx)) == K.AAO_EINVAL
     assert lib.aao_create(63, 64, 1 / 64, 7, C.byref(ctx)) == K.AAO_EINVAL
-    assert lib.aao_create(63, 48, 1 / 48, K.AAO_HEAT, C.byref(ctx)) == K.AAO_EUNSUPPORTED
+    assert lib.aao_create(63, 49, 1 / 49, K.AAO_HEAT, C.byref(ctx)) == K.AAO_EUNSUPPORTED  # 7^2
+    assert lib.aao_create(63, 14, 1 / 14, K.AAO_HEAT, C.byref(ctx)) == K.AAO_EUNSUPPORTED
     assert lib.aao_create(63, 8192, 1 / 8192, K.AAO_HEAT, C.byref(ctx)) == K.AAO_EUNSUPPORTED
     assert lib.aao_create(1 << 20, 64, 1 / 64, K.AAO_HEAT, C.byref(ctx)) == K.AAO_EUNSUPPORTED
     assert lib.aao_create(63, 64, 1 / 64, K.AAO_HEAT, None) == K.AAO_EINVAL
