@@ -566,7 +566,8 @@ cudaError_t neumann(Ctx &c, int terms, const double *x, YT *y, int tr, cudaStrea
 // subtraction is fused into the matvec), which spans the same Krylov space;
 // the Hessenberg matrix of A P^{-1} is that of w~ plus the identity.  One
 // classical Gram-Schmidt pass is followed by a second one only when the
-// norm drops below 1/sqrt(2) of its value (the DGKS criterion).
+// norm drops below 1/sqrt(2) of its value (the DGKS criterion) and the
+// iteration goes on after this step.
 //
 // Lazy normalisation: basis vectors are stored unscaled, v_j = sc[j] * V_j,
 // and the scales are folded into the coefficients the kernels receive (the
@@ -695,7 +696,26 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
       const double before = hs[nv];          // ||w~||^2 before the projection (unscaled)
       double after = hs[320 + nv];           // after
       for (int i = 0; i < nv; i++) Hij(i, j) = sc[(size_t)i] * sc[(size_t)j] * hs[i];
-      if (after < 0.5 * before) {
+      // The residual estimate this column would give as it stands: the second
+      // Gram-Schmidt pass only matters if the iteration continues, so it is
+      // skipped when this step already meets the tolerance (the true residual
+      // is checked before returning in any case).
+      auto trial_est = [&](double after_sq) {
+        std::vector<double> col((size_t)j + 2);
+        for (int i = 0; i <= j; i++) col[(size_t)i] = Hij(i, j);
+        col[(size_t)j] += 1.0;
+        col[(size_t)j + 1] = std::fabs(sc[(size_t)j]) * std::sqrt(after_sq);
+        for (int i = 0; i < j; i++) {
+          const double t = cs[(size_t)i] * col[(size_t)i] + sn[(size_t)i] * col[(size_t)i + 1];
+          col[(size_t)i + 1] = -sn[(size_t)i] * col[(size_t)i] + cs[(size_t)i] * col[(size_t)i + 1];
+          col[(size_t)i] = t;
+        }
+        const double rr = std::hypot(col[(size_t)j], col[(size_t)j + 1]);
+        const double snj = (rr == 0.0) ? 0.0 : col[(size_t)j + 1] / rr;
+        return std::fabs(snj * g[(size_t)j]) / bnorm;
+      };
+      const bool last_step = trial_est(after) <= rtol || iters + 1 >= maxit || j + 1 == m;
+      if (after < 0.5 * before && !last_step) {
         // DGKS: lost more than half the norm, orthogonalise once more
         AAO_CK(c, run(c, AAO_K_DOTS, s, [&] {
           return aao::launch_multidot(V.data(), nv, w, N, false, red, d_h2, s);

@@ -197,8 +197,13 @@ k_tridiag(cx<R> *__restrict__ spec, int n, int64_t n_pad, const TriTab<R, CH> *_
 template <int CH>
 __device__ __forceinline__ int rpos(int e) { return e + e / CH; }
 
-template <typename R, int CH>
-__global__ void __launch_bounds__(1024)
+// SMALL: at most 256 threads (rows up to 4096), compiled for AAO_TRI_MINB
+// resident CTAs per SM so that the ell/2 + 1 frequencies take fewer waves.
+#ifndef AAO_TRI_MINB
+#define AAO_TRI_MINB 3
+#endif
+template <typename R, int CH, bool SMALL>
+__global__ void __launch_bounds__(SMALL ? 256 : 1024, SMALL ? AAO_TRI_MINB : 1)
 k_tridiag_rec(cx<R> *__restrict__ spec, int n, int64_t n_pad,
               const RecTab<R, CH> *__restrict__ tabs, int conj_sym, int levels, int4 lsz_lo,
               int2 lsz_hi) {
@@ -588,7 +593,7 @@ static cudaError_t run_tridiag_rec(const Ctx &c, void *spec, const void *tab, in
   for (int l = 1; l < levels; l++) off += (size_t)(lsz[l] + lsz[l] / CH) + 1;
   off += (size_t)P;
   const size_t smem = ((off * sizeof(cx<R>) + 15) & ~(size_t)15) + (size_t)P * CH * sizeof(cx<R>);
-  auto kern = k_tridiag_rec<R, CH>;
+  auto kern = P <= 256 ? k_tridiag_rec<R, CH, true> : k_tridiag_rec<R, CH, false>;
   cudaError_t e = kernel_setup((const void *)kern, P, smem);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
   const int4 lo = make_int4(lsz[0], lsz[1], lsz[2], lsz[3]);
