@@ -477,16 +477,31 @@ k_fft_inverse_panels(const cx<R> *__restrict__ spec, cx<R> *__restrict__ inter, 
   const unsigned long long pol_done = l2_evict_first(), pol_keep = l2_evict_last();
   for (int panel = blockIdx.x; panel < npanels; panel += gridDim.x) {
     const int i0 = panel * W;
-    for (int idx = threadIdx.x; idx < NK * C; idx += T) {
+    // all of a thread's spectrum loads are issued before any is used
+    constexpr int IT = (NK * C + T - 1) / T;
+    cx<R> A[IT], B[IT];
+#pragma unroll
+    for (int q = 0; q < IT; q++) {
+      const int idx = threadIdx.x + q * T;
       const int k = idx / C, c = idx - k * C;
       const int i = i0 + 2 * c;
       const cx<R> *src = spec + (size_t)k * n_pad + i;
-      cx<R> A = mk((R)0, (R)0), B = mk((R)0, (R)0);
-      if (i + 1 < n) ld_hint2(src, A, B, pol_done);   // i even: aligned pair
-      else if (i < n) A = ld_hintc(src, pol_done);
-      if (k == 0 || 2 * k == L) { A.im = (R)0; B.im = (R)0; }
-      sm[phys<C>(k, c)] = mk(A.re - B.im, A.im + B.re);
-      if (k > 0 && 2 * k < L) sm[phys<C>(L - k, c)] = mk(A.re + B.im, B.re - A.im);
+      A[q] = mk((R)0, (R)0);
+      B[q] = mk((R)0, (R)0);
+      if (idx < NK * C) {
+        if (i + 1 < n) ld_hint2(src, A[q], B[q], pol_done);   // i even: aligned pair
+        else if (i < n) A[q] = ld_hintc(src, pol_done);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < IT; q++) {
+      const int idx = threadIdx.x + q * T;
+      if (idx >= NK * C) break;
+      const int k = idx / C, c = idx - k * C;
+      cx<R> a = A[q], b = B[q];
+      if (k == 0 || 2 * k == L) { a.im = (R)0; b.im = (R)0; }
+      sm[phys<C>(k, c)] = mk(a.re - b.im, a.im + b.re);
+      if (k > 0 && 2 * k < L) sm[phys<C>(L - k, c)] = mk(a.re + b.im, b.re - a.im);
     }
     __syncthreads();
     pass<R, L, C, P::R1, +1, T>(sm, 1, tw);
