@@ -243,7 +243,13 @@ k_tridiag_rec(cx<R> *__restrict__ spec, int n, int64_t n_pad,
   cx<R> v[CH];
   {
     const float4 *g = reinterpret_cast<const float4 *>(row);
-    for (int q = p; q < nchunks; q += P) s_row[swz(q)] = ld_hint4(&g[q], pol_keep);
+    // nchunks = P * CH / EPC: every thread copies CH / EPC chunks, all loads
+    // issued before the first store
+    float4 ch[CH / EPC];
+#pragma unroll
+    for (int j = 0; j < CH / EPC; j++) ch[j] = ld_hint4(&g[p + j * P], pol_keep);
+#pragma unroll
+    for (int j = 0; j < CH / EPC; j++) s_row[swz(p + j * P)] = ch[j];
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < CH / EPC; j++) {
