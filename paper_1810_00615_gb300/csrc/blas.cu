@@ -250,9 +250,13 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
   // CIRC (the block circulant P): steps outside [0, ell) wrap around; the
   // walk pointer is replaced by the wrapped row's address there
   auto wrap = [&](int t) { return ((t % ell) + ell) % ell; };
-  auto z_ok = [&](int t) { return col_ok && (CIRC || t_ok(t)); };
+  // only the first (last) tile of a column walks past the ends in time
+  const int t_min = TR ? t0 - (IN - 1) : t0, t_max = TR ? t0 : t0 + IN - 1;
+  const bool wrap_tile = CIRC && (t_min < 0 || t_max >= ell);
+  auto z_ok = [&](int t) { return col_ok && (wrap_tile || t_ok(t)); };
   auto zaddr = [&](int t, const XT *pw) -> const XT * {
-    return (CIRC && !t_ok(t)) ? x + (int64_t)wrap(t) * n + ic : pw;
+    if (wrap_tile && !t_ok(t)) return x + (int64_t)wrap(t) * n + ic;
+    return pw;
   };
 
   // pass 1: the tile's largest exponent (the values land in L1 for pass 2)

@@ -386,16 +386,45 @@ k_fft_forward_rows(const double *__restrict__ x, const YT *__restrict__ y,
   constexpr int C = S::C, R1 = P::R1;
   const int j = blockIdx.y;                                   // butterfly (time offset)
   const int cg = blockIdx.x * kRowThreads + threadIdx.x;      // complex column
-  if (cg >= ncx) return;
+  const bool act = cg < ncx;        // every thread stays for the barriers below
   const int i = 2 * cg;
   const unsigned long long pol_stream = l2_evict_first(), pol_keep = l2_evict_last();
   cx<R> v[R1];
+  if constexpr (!NEUMANN) {
+    // The CTA's rows (512 real columns each) come in through shared memory,
+    // up to 8 at a time, so that every warp load is one contiguous segment
+    // instead of two interleaved 8-byte streams.
+    constexpr int H = R1 < 8 ? R1 : 8;
+    __shared__ __align__(16) double s_in[H][2 * kRowThreads];
+    const int i0 = 2 * blockIdx.x * kRowThreads;
 #pragma unroll
-  for (int r = 0; r < R1; r++) {
-    const int t = j + r * P::LR;
-    v[r] = mk(load_real<R, L, NEUMANN, YT>(x, y, sigk, n, t, i, pol_stream),
-              load_real<R, L, NEUMANN, YT>(x, y, sigk, n, t, i + 1, pol_stream));
+    for (int h = 0; h < R1; h += H) {
+#pragma unroll
+      for (int rr = 0; rr < H; rr++) {
+        const size_t row = (size_t)(j + (h + rr) * P::LR) * n;
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+          const int col = u * kRowThreads + threadIdx.x, ic = i0 + col;
+          s_in[rr][col] = (ic < n) ? ld_hint(&x[row + ic], pol_stream) : 0.0;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int rr = 0; rr < H; rr++) {
+        const double2 d = reinterpret_cast<const double2 *>(s_in[rr])[threadIdx.x];
+        v[h + rr] = mk(from_f64<R>(d.x), from_f64<R>(d.y));
+      }
+      __syncthreads();
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < R1; r++) {
+      const int t = j + r * P::LR;
+      v[r] = mk(load_real<R, L, NEUMANN, YT>(x, y, sigk, n, t, i, pol_stream),
+                load_real<R, L, NEUMANN, YT>(x, y, sigk, n, t, i + 1, pol_stream));
+    }
   }
+  if (!act) return;
   dft<R, -1, R1>(v);
   cx<R> *dst = reinterpret_cast<cx<R> *>(reinterpret_cast<unsigned char *>(inter) +
                                          (size_t)(cg / C) * P::PANEL) + (cg % C);
@@ -530,30 +559,61 @@ k_fft_inverse_rows(const cx<R> *__restrict__ inter, OT *__restrict__ y, int n, i
   constexpr int C = S::C, NS = L / 16;                        // last pass: radix 16, Ns = L/16
   const int j = blockIdx.y;                                   // butterfly = first time step
   const int cg = blockIdx.x * kRowThreads + threadIdx.x;
-  if (cg >= ncx) return;
+  const bool act = cg < ncx;        // every thread stays for the barriers below
   const unsigned long long pol_done = l2_evict_first();
   const cx<R> *src = reinterpret_cast<const cx<R> *>(reinterpret_cast<const unsigned char *>(inter) +
-                                                     (size_t)(cg / C) * P::PANEL) + (cg % C);
+                                                     (size_t)(act ? cg / C : 0) * P::PANEL) + (cg % C);
   cx<R> v[16];
 #pragma unroll
-  for (int r = 0; r < 16; r++) v[r] = ld_hintc(src + phys<C>(j + r * NS, 0), pol_done);
+  for (int r = 0; r < 16; r++)
+    v[r] = act ? ld_hintc(src + phys<C>(j + r * NS, 0), pol_done) : mk((R)0, (R)0);
 #pragma unroll
   for (int r = 1; r < 16; r++) v[r] = twiddle<R, +1>(v[r], tw[j * r]);
   dft<R, +1, 16>(v);
   const R scale = (R)1 / (R)L;
-  const int i = 2 * cg;
+  // The CTA's rows (16 time steps x 512 real columns) go out through shared
+  // memory in two halves, so that every warp store (and base load) is one
+  // contiguous segment instead of two interleaved 8-byte streams.
+  __shared__ __align__(16) OT s_out[8][2 * kRowThreads];
+  const int i0 = 2 * blockIdx.x * kRowThreads;                // first real column of the CTA
 #pragma unroll
-  for (int r = 0; r < 16; r++) {
-    const size_t o = (size_t)(j + r * NS) * n + i;
+  for (int h = 0; h < 2; h++) {
+    // the base values of this half are requested before the barrier
+    float bv[8][2];
     if constexpr (sizeof(OT) == 8) {
       if (base) {
-        if (i < n) y[o] = to_f64(__ldg(&base[o])) - to_out<R, OT>(scale * v[r].re);
-        if (i + 1 < n) y[o + 1] = to_f64(__ldg(&base[o + 1])) - to_out<R, OT>(scale * v[r].im);
-        continue;
+#pragma unroll
+        for (int rr = 0; rr < 8; rr++) {
+          const size_t row = (size_t)(j + (h * 8 + rr) * NS) * n;
+#pragma unroll
+          for (int u = 0; u < 2; u++) {
+            const int i = i0 + u * kRowThreads + threadIdx.x;
+            bv[rr][u] = (i < n) ? __ldg(&base[row + i]) : 0.0f;
+          }
+        }
       }
     }
-    if (i < n) y[o] = to_out<R, OT>(scale * v[r].re);
-    if (i + 1 < n) y[o + 1] = to_out<R, OT>(scale * v[r].im);
+#pragma unroll
+    for (int rr = 0; rr < 8; rr++)   // one 8/16-byte store of the pair: no bank conflicts
+      reinterpret_cast<cx<OT> *>(s_out[rr])[threadIdx.x] =
+          mk(to_out<R, OT>(scale * v[h * 8 + rr].re), to_out<R, OT>(scale * v[h * 8 + rr].im));
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < 8; rr++) {
+      const size_t row = (size_t)(j + (h * 8 + rr) * NS) * n;
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        const int col = u * kRowThreads + threadIdx.x, i = i0 + col;
+        if (i >= n) continue;
+        const OT val = s_out[rr][col];
+        if constexpr (sizeof(OT) == 8) {
+          y[row + i] = base ? to_f64(bv[rr][u]) - val : val;
+        } else {
+          y[row + i] = val;
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
