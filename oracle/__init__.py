@@ -10,11 +10,12 @@ Contents (each function cites the passage it follows):
 
 * ``fem``      P1 mass/stiffness matrices and the L2 projection (Section 2).
 * ``system``   time-stepping blocks for the heat equation (uniform and
-               variable steps) and the BD2 wave scheme; the monolithic
+               variable steps) and the BD2 and BD4 wave schemes (BD4 with
+               its BD2 start-up rows); the monolithic
                operators, their transposes, exact solves by forward and
                backward substitution, right-hand sides, and dense assembly
                of every block matrix for tiny sizes (Section 2).
-* ``precond``  the block-circulant preconditioners P, Q, R_BD2 applied
+* ``precond``  the block-circulant preconditioners P, Q, R_BD2, R_BD4 applied
                through the Fourier diagonalisation with a dense DFT (Section
                3, method 1) and per-frequency tridiagonal solves; the
                Neumann-series approximation Q_i^{-1} (Section 2).

@@ -1,7 +1,8 @@
 """Block-circulant preconditioners and the Neumann series (Sections 2 and 3).
 
-P (heat) and R_BD2 (wave) are block circulant: P = I (x) A0 + Sigma (x) A1
-(+ Sigma^2 (x) A2 for BD2), the Kronecker form of Section 3, with Sigma the ell x ell cyclic
+P (heat), R_BD2 and R_BD4 (wave) are block circulant: P = I (x) A0 +
+Sigma (x) A1 (+ Sigma^2 (x) A2 for BD2, + Sigma^3 (x) A3 for BD4), the
+Kronecker form of Section 3, with Sigma the ell x ell cyclic
 down-shift, (Sigma x)_t = x_{t-1 mod ell} (the paper writes Sigma in
 R^{n x n}; its size is ell).  Sigma = U Lambda U^* with U the unitary DFT of
 size ell, U_{tk} = exp(+2 pi i t k / ell)/sqrt(ell), and Lambda_kk = w_k =
@@ -85,7 +86,7 @@ def shift_eigenvalues(ell: int) -> np.ndarray:
 
 
 def frequency_block(S: BlockSystem, w: complex):
-    """I (x) A0 + Lambda (x) A1 (+ Lambda^2 (x) A2) restricted to frequency w."""
+    """I (x) A0 + sum_j Lambda^j (x) A_j restricted to frequency w."""
     B = constant_A0(S).astype(np.complex128)
     for j, Aj in enumerate(S.lower, start=1):
         B = B + (w ** j) * Aj

@@ -1,4 +1,5 @@
-"""All-at-once block systems of Section 2 (heat, variable-step heat, BD2 wave).
+"""All-at-once block systems of Section 2 (heat, variable-step heat, BD2 and
+BD4 wave).
 
 A block vector is an array of shape (ell, n); row t holds u_{t+1}.
 
@@ -13,9 +14,15 @@ Time-stepping blocks:
 * Heat with steps tau_1..tau_ell (system B of Section 2): A0^t = M +
   tau_t*kappa*K on the block diagonal, A1 = -M below it.
 * Wave, BD2 (Section 2, C_BD2): A0 = M + tau^2 K, A1 = -2M, A2 = M.
+* Wave, BD4 (Section 2, C_BD4): the four-step formula gives A0 = 2M +
+  tau^2 K, A1 = -5M, A2 = 4M, A3 = -M; its first two rows are BD2 steps
+  (diagonal B = M + tau^2 K, and C = -2M below the second one), so the
+  matrix is Toeplitz only from the third block row on.
 
-The monolithic matrix is block lower-triangular Toeplitz (block-diagonal
-part per step for B):  (A U)_t = A0^t u_t + sum_{j>=1} A_j u_{t-j}.
+The monolithic matrix is block lower-triangular (block-diagonal part per
+step for B and for the BD4 start-up rows):
+(A U)_t = A0^t u_t + sum_{j>=1} A_j^t u_{t-j}, with A_j^t = A_j except where
+``startup`` names another block for row t.
 """
 from __future__ import annotations
 
@@ -57,6 +64,12 @@ class BlockSystem:
     taus: Optional[np.ndarray] = None  # per-step tau_t (system B), else None
     kappa: float = 1.0
     extra: dict = field(default_factory=dict)
+    startup: dict = field(default_factory=dict)  # (t, j) -> block at row t, lag j
+
+
+def lag_block(S: BlockSystem, t: int, j: int):
+    """The block multiplying u_{t-j} in block row t (j >= 1)."""
+    return S.startup.get((t, j), S.lower[j - 1])
 
 
 def heat(n: int, ell: int, tau: float, kappa: float = 1.0,
@@ -96,26 +109,39 @@ def bd2(n: int, ell: int, tau: float) -> BlockSystem:
                        M, K, "bd2", tau)
 
 
+def bd4(n: int, ell: int, tau: float) -> BlockSystem:
+    """C_BD4 of Section 2.  Rows t >= 2 (0-based) apply the four-step formula
+    (2M + tau^2 K) u_t - 5M u_{t-1} + 4M u_{t-2} - M u_{t-3}; rows 0 and 1
+    are BD2 steps, B u_1 and C u_1 + B u_2 with B = M + tau^2 K, C = -2M."""
+    M, K = p1_matrices(n)
+    B = (M + tau * tau * K).tocsr()
+    A0 = (2.0 * M + tau * tau * K).tocsr()
+    diag = [B if t < 2 else A0 for t in range(ell)]
+    lower = [(-5.0 * M).tocsr(), (4.0 * M).tocsr(), (-M).tocsr()]
+    startup = {(1, 1): (-2.0 * M).tocsr()}
+    return BlockSystem(n, ell, diag, lower, M, K, "bd4", tau, startup=startup)
+
+
 def matvec(S: BlockSystem, X: np.ndarray) -> np.ndarray:
-    """Y = A X with (A X)_t = A0^t x_t + sum_j A_j x_{t-j} (x_{<0} = 0)."""
+    """Y = A X with (A X)_t = A0^t x_t + sum_j A_j^t x_{t-j} (x_{<0} = 0)."""
     Y = np.empty_like(X, dtype=np.result_type(X, np.float64))
     for t in range(S.ell):
         y = S.diag[t] @ X[t]
-        for j, Aj in enumerate(S.lower, start=1):
+        for j in range(1, len(S.lower) + 1):
             if t - j >= 0:
-                y = y + Aj @ X[t - j]
+                y = y + lag_block(S, t, j) @ X[t - j]
         Y[t] = y
     return Y
 
 
 def matvec_T(S: BlockSystem, X: np.ndarray) -> np.ndarray:
-    """Y = A^T X: (A^T X)_t = (A0^t)^T x_t + sum_j A_j^T x_{t+j}."""
+    """Y = A^T X: (A^T X)_t = (A0^t)^T x_t + sum_j (A_j^{t+j})^T x_{t+j}."""
     Y = np.empty_like(X, dtype=np.result_type(X, np.float64))
     for t in range(S.ell):
         y = S.diag[t].T @ X[t]
-        for j, Aj in enumerate(S.lower, start=1):
+        for j in range(1, len(S.lower) + 1):
             if t + j < S.ell:
-                y = y + Aj.T @ X[t + j]
+                y = y + lag_block(S, t + j, j).T @ X[t + j]
         Y[t] = y
     return Y
 
@@ -128,9 +154,9 @@ def forward_substitution(S: BlockSystem, B: np.ndarray) -> np.ndarray:
     U = np.zeros_like(B, dtype=np.float64)
     for t in range(S.ell):
         r = B[t].copy()
-        for j, Aj in enumerate(S.lower, start=1):
+        for j in range(1, len(S.lower) + 1):
             if t - j >= 0:
-                r = r - Aj @ U[t - j]
+                r = r - lag_block(S, t, j) @ U[t - j]
         U[t] = solve_tridiag(S.diag[t], r)
     return U
 
@@ -140,9 +166,9 @@ def backward_substitution(S: BlockSystem, G: np.ndarray) -> np.ndarray:
     L = np.zeros_like(G, dtype=np.float64)
     for t in range(S.ell - 1, -1, -1):
         r = G[t].copy()
-        for j, Aj in enumerate(S.lower, start=1):
+        for j in range(1, len(S.lower) + 1):
             if t + j < S.ell:
-                r = r - Aj.T @ L[t + j]
+                r = r - lag_block(S, t + j, j).T @ L[t + j]
         L[t] = solve_tridiag(S.diag[t].T, r)
     return L
 
@@ -170,6 +196,22 @@ def rhs_bd2(S: BlockSystem, u0: np.ndarray,
     return B
 
 
+def rhs_bd4(S: BlockSystem, u0: np.ndarray,
+            v0: Optional[np.ndarray] = None) -> np.ndarray:
+    """b_BD4 = [B u0; -M u0; M u0; 0; ...] (Section 2): the BD2 start-up rows
+    as in rhs_bd2 (B = M + tau^2 K, the first row B (u0 + tau v0) with an
+    initial velocity), and the third row carries the -M u_0 term of the
+    first four-step equation to the right-hand side."""
+    B = np.zeros((S.ell, S.n))
+    first = u0 if v0 is None else u0 + S.tau * v0
+    B[0] = S.diag[0] @ first
+    if S.ell > 1:
+        B[1] = -(S.M @ u0)
+    if S.ell > 2:
+        B[2] = S.M @ u0
+    return B
+
+
 # ---------------------------------------------------------------- dense forms
 def dense_monolithic(S: BlockSystem) -> np.ndarray:
     """Dense n*ell x n*ell matrix of A (tiny sizes only)."""
@@ -177,18 +219,20 @@ def dense_monolithic(S: BlockSystem) -> np.ndarray:
     A = np.zeros((n * ell, n * ell))
     for t in range(ell):
         A[t * n:(t + 1) * n, t * n:(t + 1) * n] = S.diag[t].toarray()
-        for j, Aj in enumerate(S.lower, start=1):
+        for j in range(1, len(S.lower) + 1):
             if t - j >= 0:
-                A[t * n:(t + 1) * n, (t - j) * n:(t - j + 1) * n] = Aj.toarray()
+                A[t * n:(t + 1) * n, (t - j) * n:(t - j + 1) * n] = lag_block(S, t, j).toarray()
     return A
 
 
 def dense_circulant(S: BlockSystem, per_step: bool = False) -> np.ndarray:
     """Dense block circulant built entry by entry (tiny sizes only).
 
-    per_step=False: P (heat, Section 2) or R_BD2 (wave): every diagonal block
-    is the constant-step A0 = M + tau kappa K (heat) or M + tau^2 K (BD2),
-    and block A_j sits at block column (t - j) mod ell.
+    per_step=False: P (heat, Section 2), R_BD2 or R_BD4 (wave): every
+    diagonal block is the constant-step A0 (M + tau kappa K for heat,
+    M + tau^2 K for BD2, 2M + tau^2 K for BD4), and block A_j sits at block
+    column (t - j) mod ell in every row.  R_BD4 is the circulant of the
+    Toeplitz part of C_BD4; the start-up rows do not enter it.
     per_step=True: Q of Section 2, the diagonal blocks A0^t of system B.
     """
     n, ell = S.n, S.ell
@@ -213,6 +257,8 @@ def constant_A0(S: BlockSystem) -> sp.csr_matrix:
         return (S.K + S.tau * S.M).tocsr()
     if S.kind == "bd2":
         return (S.M + S.tau * S.tau * S.K).tocsr()
+    if S.kind == "bd4":
+        return (2.0 * S.M + S.tau * S.tau * S.K).tocsr()
     raise ValueError(S.kind)
 
 

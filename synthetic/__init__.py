@@ -21,6 +21,9 @@ Recipe (numpy PCG64, seed 1810615 unless a caller passes another seed):
   eigenvector of the P1 mass matrix, so the projection stays in that mode.
 * Non-uniform time grids follow Section 4: ``t_0 = 0``, ``t_ell = 1`` and
   ``t_j = (j + delta (R_j - 0.5)) / ell`` with ``R_j`` uniform on [0, 1).
+* The non-smooth wave initial condition of Section 4 (Tables 3 and 4):
+  ``u0(x) = cos^2(4 pi (x - 1/2))`` on (3/8, 5/8), zero elsewhere, sampled
+  at the interior nodes (the paper does not say how it is discretised).
 * Random block vectors (parity inputs) are standard normal, shape
   ``(ell, n)``, row ``t`` holding time block ``t+1``.
 """
@@ -112,3 +115,10 @@ def wave_initial(n: int, modes: int = 16, seed: int = DEFAULT_SEED):
     a = sine_coefficients(modes, g)
     b = sine_coefficients(modes, g)
     return sine_l2_projection(a, n), sine_l2_projection(b, n)
+
+
+def wave_nonsmooth(n: int) -> np.ndarray:
+    """Nodal samples of the non-smooth wave initial condition of Section 4:
+    cos^2(4 pi (x - 1/2)) for 3/8 < x < 5/8, zero elsewhere."""
+    x = grid(n)
+    return np.where((x > 0.375) & (x < 0.625), np.cos(4.0 * np.pi * (x - 0.5)) ** 2, 0.0)
