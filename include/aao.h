@@ -8,9 +8,12 @@
  *     time (block lower-bidiagonal A with A0 = M + tau*kappa*K, A1 = -M, or
  *     per-step A0^t = M + tau_t*kappa*K for the variable-step system B), and
  *   - the 1D wave equation with the BD2 scheme (three block bands,
- *     A0 = M + tau^2 K, A1 = -2M, A2 = M),
+ *     A0 = M + tau^2 K, A1 = -2M, A2 = M) or the BD4 scheme (four block
+ *     bands A0 = 2M + tau^2 K, A1 = -5M, A2 = 4M, A3 = -M after two BD2
+ *     start-up rows),
  * by flexible GMRES preconditioned with the McDonald-Pestana-Wathen block
- * circulant P (Section 2; R_BD2 for the wave equation) or its Neumann-series
+ * circulant P (Section 2; R_BD2 or R_BD4 for the wave equation) or its
+ * Neumann-series
  * extension Q_i^{-1} (Section 2).  P^{-1} is applied through its Fourier
  * diagonalisation (Section 3): a real FFT along the time axis, one complex
  * tridiagonal solve per frequency, an inverse FFT.
@@ -49,8 +52,15 @@ typedef struct aao_ctx aao_ctx;
  *                   Q = P + sigma (x) K, so the time step multiplies K here.
  * AAO_WAVE_BD2      BD2 for M u'' = -K u: A0 = M + tau^2 K, A1 = -2M, A2 = M.
  * AAO_HEAT_LITERAL  the printed blocks A0 = K + tau*M, A1 = -M (kept to show
- *                   the difference; kappa is ignored). */
-enum { AAO_HEAT = 0, AAO_WAVE_BD2 = 1, AAO_HEAT_LITERAL = 2 };
+ *                   the difference; kappa is ignored).
+ * AAO_WAVE_BD4      C_BD4 for M u'' = -K u: block rows t >= 3 (1-based) are
+ *                   A3 u_{t-3} + A2 u_{t-2} + A1 u_{t-1} + A0 u_t with
+ *                   A0 = 2M + tau^2 K, A1 = -5M, A2 = 4M, A3 = -M; rows 1
+ *                   and 2 are the BD2 steps B u_1 and C u_1 + B u_2 with
+ *                   B = M + tau^2 K, C = -2M.  Its preconditioner is R_BD4,
+ *                   the block circulant of (A0, A1, A2, A3).  Uniform steps
+ *                   only, like BD2; kappa is ignored by both wave forms. */
+enum { AAO_HEAT = 0, AAO_WAVE_BD2 = 1, AAO_HEAT_LITERAL = 2, AAO_WAVE_BD4 = 3 };
 
 /* Arithmetic of the preconditioner (FFTs and tridiagonal solves).  The outer
  * GMRES, the matvec and the true residual are FP64 in both cases. */
@@ -130,7 +140,8 @@ int aao_set_workspace(aao_ctx *ctx, void *dev_ptr, size_t bytes);
  * P^{-1} = (U (x) I)[I (x) A0 + Lambda (x) A1]^{-1}(U^* (x) I).  P^T is
  * diagonalised by the same DFT with conj(w_k).  Runs a real FFT along the
  * time axis, ell/2+1 complex tridiagonal solves and the inverse FFT, in the
- * context's precision.  For the wave equation P is R_BD2.  Needs the
+ * context's precision.  For the wave equations P is R_BD2 or R_BD4 (block k
+ * A0 + w_k A1 + w_k^2 A2 (+ w_k^3 A3)).  Needs the
  * workspace.  x, y: device, N doubles, no overlap. */
 int aao_precond_apply(aao_ctx *ctx, const double *x, double *y, int transpose,
                       void *stream);
@@ -147,10 +158,13 @@ int aao_neumann_apply(aao_ctx *ctx, int terms, const double *x, double *y,
 /* y = A x (transpose = 0) or A^T x (transpose = 1) in FP64 (Section 2; the
  * monolithic matrix is never formed).  Heat: y_t = M(x_t - x_{t-1}) +
  * tau_t kappa K x_t; BD2: y_t = M(x_t - 2x_{t-1} + x_{t-2}) + tau^2 K x_t;
- * the transpose shifts the other way.  For these two forms the stencil sums
+ * BD4: y_t = M(2x_t - 5x_{t-1} + 4x_{t-2} - x_{t-3}) + tau^2 K x_t, with the
+ * BD2 rows B x_1 and C x_1 + B x_2 first;
+ * the transpose shifts the other way.  For these forms the stencil sums
  * are formed exactly in 64-bit fixed point per 32-column, 32-step tile and
  * rounded once (elements more than 2^5 below their tile's largest enter with
- * an absolute error under 2^-57 of it); the literal heat form runs the FP64
+ * an absolute error under 2^-57 of it; BD4, whose larger weights need two
+ * more guard bits: 2^3 and 2^-55); the literal heat form runs the FP64
  * stencil.  An inf or NaN in a tile makes that tile's outputs NaN.  No
  * workspace needed. */
 int aao_matvec(aao_ctx *ctx, const double *x, double *y, int transpose,
@@ -178,14 +192,15 @@ int aao_matvec_f32(aao_ctx *ctx, const float *x, const double *sub, double *y, i
 
 /* Right-hand side from initial data (Section 2): heat b = [M u0; 0; ...];
  * BD2 b = [A0 (u0 + tau v0); -M u0; 0; ...] (v0 may be NULL = at rest, which
- * is the paper's b_BD2).  u0, v0: device, n doubles; b: device, N doubles. */
+ * is the paper's b_BD2); BD4 b = [B (u0 + tau v0); -M u0; M u0; 0; ...]
+ * (b_BD4 at rest).  u0, v0: device, n doubles; b: device, N doubles. */
 int aao_build_rhs(aao_ctx *ctx, const double *u0, const double *v0, double *b,
                   void *stream);
 
 /* Solve A x = b by flexible GMRES(restart), right-preconditioned, FP64
  * Arnoldi with classical Gram-Schmidt and re-orthogonalisation, Givens
  * rotations on the host, the true residual recomputed in FP64 at every
- * restart.  precond: 0 none, 1 the circulant P (R_BD2), i >= 2 the Neumann
+ * restart.  precond: 0 none, 1 the circulant P (R_BD2, R_BD4), i >= 2 the Neumann
  * series Q_i^{-1}.  Stops when ||b - A x|| <= rtol ||b|| (true residual), or
  * with AAO_ENOCONV (x holds the last iterate) after maxit Arnoldi steps or
  * when three restart cycles in a row lower the true residual by less than

@@ -21,14 +21,15 @@ import torch
 from . import _build
 from ._capi import (AAO_ECUDA, AAO_EINVAL, AAO_ENOCONV, AAO_ENUMERIC, AAO_EUNSUPPORTED,
                     AAO_HEAT, AAO_HEAT_LITERAL, AAO_OK, AAO_PREC_FP32, AAO_PREC_FP32_REFINED, AAO_PREC_FP64,
-                    AAO_WAVE_BD2, AAOError, SolveInfo, check, lib)
+                    AAO_WAVE_BD2, AAO_WAVE_BD4, AAOError, SolveInfo, check, lib)
 
 __all__ = ["AllAtOnce", "AAOSolve", "SolveInfo", "AAOError", "lib", "build",
-           "AAO_HEAT", "AAO_WAVE_BD2", "AAO_HEAT_LITERAL", "AAO_PREC_FP32", "AAO_PREC_FP32_REFINED", "AAO_PREC_FP64",
+           "AAO_HEAT", "AAO_WAVE_BD2", "AAO_WAVE_BD4", "AAO_HEAT_LITERAL", "AAO_PREC_FP32", "AAO_PREC_FP32_REFINED", "AAO_PREC_FP64",
            "AAO_OK", "AAO_ENOCONV", "AAO_EINVAL", "AAO_ECUDA", "AAO_ENUMERIC",
            "AAO_EUNSUPPORTED"]
 
-EQUATIONS = {"heat": AAO_HEAT, "wave_bd2": AAO_WAVE_BD2, "heat_literal": AAO_HEAT_LITERAL}
+EQUATIONS = {"heat": AAO_HEAT, "wave_bd2": AAO_WAVE_BD2, "heat_literal": AAO_HEAT_LITERAL,
+             "wave_bd4": AAO_WAVE_BD4}
 
 
 def build(force: bool = False) -> str:
@@ -53,8 +54,9 @@ class AllAtOnce:
     """One all-at-once system (n spatial nodes, ell time steps) on one GPU.
 
     equation: "heat" (implicit Euler, A0 = M + tau kappa K, A1 = -M),
-    "wave_bd2" (A0 = M + tau^2 K, A1 = -2M, A2 = M) or "heat_literal" (the
-    printed A0 = K + tau M).  precision: "fp32", "fp32_refined" (FP32 with
+    "wave_bd2" (A0 = M + tau^2 K, A1 = -2M, A2 = M), "wave_bd4" (A0 = 2M +
+    tau^2 K, A1 = -5M, A2 = 4M, A3 = -M after two BD2 start-up rows;
+    preconditioned by R_BD4) or "heat_literal" (the printed A0 = K + tau M).  precision: "fp32", "fp32_refined" (FP32 with
     one refinement sweep, FP64-like accuracy) or "fp64" for the
     preconditioner; the outer GMRES is FP64 either way.
     """

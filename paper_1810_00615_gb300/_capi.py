@@ -12,7 +12,7 @@ import threading
 
 from . import _build
 
-AAO_HEAT, AAO_WAVE_BD2, AAO_HEAT_LITERAL = 0, 1, 2
+AAO_HEAT, AAO_WAVE_BD2, AAO_HEAT_LITERAL, AAO_WAVE_BD4 = 0, 1, 2, 3
 AAO_PREC_FP64, AAO_PREC_FP32, AAO_PREC_FP32_REFINED = 0, 1, 2
 AAO_OK, AAO_ENOCONV = 0, 1
 AAO_EINVAL, AAO_ENOMEM, AAO_ECUDA, AAO_ENUMERIC, AAO_EUNSUPPORTED = -1, -2, -3, -4, -5

@@ -135,13 +135,15 @@ k_matvec(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
 }
 
 // ------------------------------------------------ fixed-point matvec
-// For the standard heat equation (any steps) and BD2 every block is
+// For the standard heat equation (any steps), BD2 and BD4 every block is
 // a M + b K with M = (h/6) tridiag(1,4,1), K = (1/h) tridiag(-1,2,-1)
 // (Section 2).  With q_t = 4 x_t + x_{t,i-1} + x_{t,i+1} and
 // s_t = 2 x_t - x_{t,i-1} - x_{t,i+1}:
 //   heat  (A x)_t = (h/6)(q_t - q_{t-1})            + beta_t s_t
 //   BD2   (A x)_t = (h/6)(q_t - 2 q_{t-1} + q_{t-2}) + beta   s_t
-// (transpose: t+1, t+2 instead of t-1, t-2).  Each warp converts its tile of
+//   BD4   (A x)_t = (h/6)(2 q_t - 5 q_{t-1} + 4 q_{t-2} - q_{t-3}) + beta s_t,
+//         except the two BD2 start-up rows of C_BD4 (weights 1 and 1, -2)
+// (transpose: t+1, t+2, t+3 instead of t-1, t-2, t-3).  Each warp converts its tile of
 // x (its 32 columns, one halo column each side, the time steps it needs) to
 // 64-bit fixed point at the tile's largest exponent, forms both sums exactly
 // in integers (no cancellation error however much the terms cancel), joins
@@ -152,7 +154,8 @@ k_matvec(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
 // operations per element of the FP64 form with integer work.
 // The largest element of a tile keeps 58 bits (FP32 input: 34 binades below
 // it are exact, FP64 input: 5); anything smaller is truncated at 2^-57 of
-// the tile maximum.  x is FP64 (the solution, the public matvec) or FP32
+// the tile maximum.  BD4's weights (sum of magnitudes 12) need two guard
+// bits more: 56 bits, truncation at 2^-55.  x is FP64 (the solution, the public matvec) or FP32
 // (the preconditioned basis of the mixed solver).
 constexpr int kFxRows = 32;   // output time steps per warp tile
 #ifndef AAO_MVFX_U1
@@ -171,16 +174,19 @@ template <> struct Fx<float> {
     const int e = (int)((__float_as_uint(v) >> 23) & 0xffu);
     return e ? e : 1;                       // subnormals scale like exponent 1
   }
-  // v * 2^(184 - emax) as an integer (|.| < 2^58), emax >= exp(v)
+  // v * 2^(184 - G - emax) as an integer (|.| < 2^(58 - G)), emax >= exp(v);
+  // G guard bits leave room for larger integer weights in the sums
+  template <int G>
   __device__ static long long fixed(float v, int emax) {
     const unsigned b = __float_as_uint(v);
     const unsigned e = (b >> 23) & 0xffu;
     const unsigned long long mant = (b & 0x7fffffu) | (e ? 0x800000u : 0u);
     const int sh = min(emax - (e ? (int)e : 1), 63);
-    const unsigned long long u = (mant << 34) >> sh;
+    const unsigned long long u = (mant << (34 - G)) >> sh;
     return (b >> 31) ? -(long long)u : (long long)u;
   }
-  __device__ static int unit(int emax) { return emax - 184; }   // log2 of one unit
+  template <int G>
+  __device__ static int unit(int emax) { return emax - 184 + G; }   // log2 of one unit
 };
 template <> struct Fx<double> {
   static constexpr int kNonFinite = 2047;
@@ -188,16 +194,18 @@ template <> struct Fx<double> {
     const int e = (int)(((unsigned)__double2hiint(v) >> 20) & 0x7ffu);
     return e ? e : 1;
   }
-  // v * 2^(1080 - emax) as an integer (|.| < 2^58), emax >= exp(v)
+  // v * 2^(1080 - G - emax) as an integer (|.| < 2^(58 - G)), emax >= exp(v)
+  template <int G>
   __device__ static long long fixed(double v, int emax) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int e = (int)((b >> 52) & 0x7ffu);
     const unsigned long long mant = (b & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
     const int sh = min(emax - (e ? e : 1), 63);
-    const unsigned long long u = (mant << 5) >> sh;
+    const unsigned long long u = (mant << (5 - G)) >> sh;
     return (b >> 63) ? -(long long)u : (long long)u;
   }
-  __device__ static int unit(int emax) { return emax - 1080; }
+  template <int G>
+  __device__ static int unit(int emax) { return emax - 1080 + G; }
 };
 
 // S * 2^unit rounded to nearest even (|S| < 2^63).  With RANGE, results
@@ -231,6 +239,7 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
             const MvRow *__restrict__ rows, const double *__restrict__ sub) {
   constexpr int R = kFxRows, IN = R + NB - 1;   // input time steps per tile
   constexpr int kWarps = kMvCols / 32;
+  constexpr int G = NB == 4 ? 2 : 0;            // guard bits (sums below 2^63)
   using F = Fx<XT>;
   __shared__ long long s_halo[kWarps][2][IN];   // converted halo columns, walk order
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -283,14 +292,14 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
         y[(int64_t)t * n + i] = __longlong_as_double(0x7ff8000000000000ll);
     return;
   }
-  const int unit = F::unit(em);
+  const int unit = F::template unit<G>(em);
   if (lane < IN) {
-    s_halo[warp][0][lane] = F::fixed(hl0, em);
-    s_halo[warp][1][lane] = F::fixed(hr0, em);
+    s_halo[warp][0][lane] = F::template fixed<G>(hl0, em);
+    s_halo[warp][1][lane] = F::template fixed<G>(hr0, em);
   }
   if (IN > 32 && lane + 32 < IN) {
-    s_halo[warp][0][lane + 32] = F::fixed(hl1, em);
-    s_halo[warp][1][lane + 32] = F::fixed(hr1, em);
+    s_halo[warp][0][lane + 32] = F::template fixed<G>(hl1, em);
+    s_halo[warp][1][lane + 32] = F::template fixed<G>(hr1, em);
   }
   __syncwarp();
 
@@ -309,7 +318,7 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
   const XT *pz = px0 + kPre * step;
   const double *pv = SUB ? pv0 + kPre * step : nullptr;
   double *py = y + (int64_t)t0 * n + ic;
-  long long q1 = 0, q2 = 0;                     // q of the previous one or two steps walked
+  long long q1 = 0, q2 = 0, q3 = 0;             // q of the previous steps walked
 #pragma unroll 1
   for (int kb = 0; kb < IN; kb += kPre) {
 #pragma unroll
@@ -326,7 +335,7 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
         pz += step;
         if (SUB) pv += step;
       }
-      const long long X = F::fixed(zk, em);
+      const long long X = F::template fixed<G>(zk, em);
       long long Xl = __shfl_up_sync(0xffffffffu, X, 1);
       long long Xr = __shfl_down_sync(0xffffffffu, X, 1);
       if (lane == 0) Xl = s_halo[warp][0][k < IN ? k : 0];
@@ -334,7 +343,18 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
       const long long P = Xl + Xr;
       const long long q = 4 * X + P;
       if (k >= NB - 1 && k < IN && col_ok && t_ok(t)) {
-        const long long sm = (NB == 2) ? q - q1 : q - 2 * q1 + q2;
+        long long sm;
+        if (NB == 2) {
+          sm = q - q1;
+        } else if (NB == 3) {
+          sm = q - 2 * q1 + q2;
+        } else {
+          sm = 2 * q - 5 * q1 + 4 * q2 - q3;
+          if (!CIRC && t < 2) {   // the BD2 start-up rows of C_BD4 (and their columns)
+            if (!TR) sm = t == 0 ? q : q - 2 * q1;
+            else sm = t == 0 ? q - 2 * q1 + 4 * q2 - q3 : q - 5 * q1 + 4 * q2 - q3;
+          }
+        }
         const long long sk = 2 * X - P;
         // T = S_main + frac S_other, exact up to the truncated product; one
         // rounding to FP64 and one FMA
@@ -348,6 +368,7 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
         const double td = fx_to_f64<RANGE>(T, unit);
         py[(int64_t)k * step] = SUB ? fma(rw.coef, td, -vk) : rw.coef * td;
       }
+      q3 = q2;
       q2 = q1;
       q1 = q;
     }
@@ -394,7 +415,7 @@ static void mv_fx(const Ctx &c, dim3 grid, const XT *x, double *y, const double 
     k_matvec_fx<NB, TR, false, XT, CIRC><<<grid, kMvCols, 0, s>>>(x, y, n, ell, rows, nullptr);
 }
 
-// Heat and BD2 take the fixed-point kernel; the literal heat form (whose M
+// Heat, BD2 and BD4 take the fixed-point kernel; the literal heat form (whose M
 // coefficients differ between A0 and A1) the FP64 stencil.  CIRC: the block
 // circulant P of Section 3 (constant step, time wrapped around) instead of A.
 template <typename XT, bool CIRC = false>
@@ -404,8 +425,10 @@ static cudaError_t matvec_dispatch(const Ctx &c, const XT *x, double *y, int tra
   const int n = (int)c.n, ell = (int)c.ell;
   const dim3 grid((unsigned)((n + kMvCols - 1) / kMvCols),
                   (unsigned)((ell + kFxRows - 1) / kFxRows));
-  const bool bd2 = c.equation == AAO_WAVE_BD2;
-  if (bd2 && transpose) mv_fx<3, true, XT, CIRC>(c, grid, x, y, sub, s);
+  const bool bd2 = c.equation == AAO_WAVE_BD2, bd4 = c.equation == AAO_WAVE_BD4;
+  if (bd4 && transpose) mv_fx<4, true, XT, CIRC>(c, grid, x, y, sub, s);
+  else if (bd4) mv_fx<4, false, XT, CIRC>(c, grid, x, y, sub, s);
+  else if (bd2 && transpose) mv_fx<3, true, XT, CIRC>(c, grid, x, y, sub, s);
   else if (bd2) mv_fx<3, false, XT, CIRC>(c, grid, x, y, sub, s);
   else if (transpose) mv_fx<2, true, XT, CIRC>(c, grid, x, y, sub, s);
   else mv_fx<2, false, XT, CIRC>(c, grid, x, y, sub, s);
@@ -455,9 +478,11 @@ cudaError_t launch_matvec(const Ctx &c, const float *x, double *y, int transpose
 
 // --------------------------------------------------------------------- rhs
 // Heat: b_0 = M u0.  BD2: b_0 = A0 (u0 + tau v0) = M w + tau^2 K w,
-// b_1 = -M u0.  Literal heat: b_0 = M u0.  Other blocks zero.
+// b_1 = -M u0.  BD4: b_0 = B (u0 + tau v0) (B = M + tau^2 K, the BD2
+// block), b_1 = -M u0, b_2 = M u0.  Literal heat: b_0 = M u0.  Other
+// blocks zero.  wave: 0 heat, 2 BD2, 3 BD4 (the number of start-up rows).
 __global__ void k_rhs(const double *__restrict__ u0, const double *__restrict__ v0,
-                      double *__restrict__ b, int n, int ell, int bd2, double tau,
+                      double *__restrict__ b, int n, int ell, int wave, double tau,
                       double mh, double kh) {
   const int64_t N = (int64_t)n * ell;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N;
@@ -465,21 +490,21 @@ __global__ void k_rhs(const double *__restrict__ u0, const double *__restrict__ 
     const int t = (int)(g / n);
     const int i = (int)(g - (int64_t)t * n);
     double out = 0.0;
-    if (t <= 1) {
+    if (t <= 2) {
       auto at = [&](const double *v, int j) { return (j >= 0 && j < n) ? v[j] : 0.0; };
       auto w = [&](int j) {
         double r = at(u0, j);
-        if (bd2 && v0 && t == 0) r = fma(tau, at(v0, j), r);
+        if (wave && v0 && t == 0) r = fma(tau, at(v0, j), r);
         return r;
       };
       const double wc = w(i), wl = w(i - 1), wr = w(i + 1);
       const double m = mh * fma(4.0, wc, wl + wr);
       if (t == 0) {
         out = m;
-        if (bd2) out = fma(tau * tau * kh, (wc - wl) - (wr - wc), out);
-      } else if (bd2) {
-        const double uc = at(u0, i), ul = at(u0, i - 1), ur = at(u0, i + 1);
-        out = -mh * fma(4.0, uc, ul + ur);
+        if (wave) out = fma(tau * tau * kh, (wc - wl) - (wr - wc), out);
+      } else if (t < wave) {
+        // w = u0 on these rows: -M u0 (second row), +M u0 (third, BD4)
+        out = t == 1 ? -m : m;
       }
     }
     b[g] = out;
@@ -491,7 +516,10 @@ cudaError_t launch_rhs(const Ctx &c, const double *u0, const double *v0, double 
   int64_t blocks = (c.N + kThreads - 1) / kThreads;
   if (blocks > 152 * 32) blocks = 152 * 32;
   k_rhs<<<(unsigned)blocks, kThreads, 0, s>>>(u0, v0, b, (int)c.n, (int)c.ell,
-                                              c.equation == AAO_WAVE_BD2, c.tau, c.h / 6.0,
+                                              c.equation == AAO_WAVE_BD2   ? 2
+                                              : c.equation == AAO_WAVE_BD4 ? 3
+                                                                           : 0,
+                                              c.tau, c.h / 6.0,
                                               1.0 / c.h); note_launch();
   return cudaGetLastError();
 }

@@ -53,12 +53,16 @@ cd one_minus_w(int64_t k, int64_t ell) {
   return cd(2.0 * s * s, sinpi_q(2 * k, ell));
 }
 
-// Frequency block A0 + w A1 (+ w^2 A2) = cM(k) M + cK K (Section 3).
+// Frequency block A0 + w A1 (+ w^2 A2 + w^3 A3) = cM(k) M + cK K (Section 3).
 void block_symbol(const Ctx &c, int64_t k, cd &cM, double &cK) {
   const cd om = one_minus_w(k, c.ell);
   switch (c.equation) {
     case AAO_WAVE_BD2:  // (M + tau^2 K) - 2 w M + w^2 M = (1 - w)^2 M + tau^2 K
       cM = om * om;
+      cK = c.tau * c.tau;
+      break;
+    case AAO_WAVE_BD4:  // 2 - 5w + 4w^2 - w^3 = (1 - w)^2 (2 - w), 2 - w = 1 + (1 - w)
+      cM = om * om * (1.0 + om);
       cK = c.tau * c.tau;
       break;
     case AAO_HEAT_LITERAL:  // (K + tau M) - w M = (tau - 1 + (1 - w)) M + K
@@ -343,7 +347,8 @@ int refresh_constants(Ctx &c) {
   for (int64_t t = 0; t < c.ell; t++) {
     const double tt = c.variable_steps ? c.taus[(size_t)t] : c.tau;
     switch (c.equation) {
-      case AAO_WAVE_BD2: beta[(size_t)t] = c.tau * c.tau / c.h; break;
+      case AAO_WAVE_BD2:
+      case AAO_WAVE_BD4: beta[(size_t)t] = c.tau * c.tau / c.h; break;
       case AAO_HEAT_LITERAL: beta[(size_t)t] = 1.0 / c.h; break;
       default: beta[(size_t)t] = tt * c.kappa / c.h; break;
     }
@@ -353,6 +358,12 @@ int refresh_constants(Ctx &c) {
         const double q = c.tau * c.tau;
         d0[(size_t)t] = 4 * mh + 2 * q * kh;
         o0[(size_t)t] = mh - q * kh;
+        break;
+      }
+      case AAO_WAVE_BD4: {   // B = M + tau^2 K on the two start-up rows, then 2M + tau^2 K
+        const double q = c.tau * c.tau, a = t < 2 ? 1.0 : 2.0;
+        d0[(size_t)t] = 4 * a * mh + 2 * q * kh;
+        o0[(size_t)t] = a * mh - q * kh;
         break;
       }
       case AAO_HEAT_LITERAL:
@@ -374,7 +385,8 @@ int refresh_constants(Ctx &c) {
   AAO_CK(c, upload((void **)&c.beta, beta));
   // K coefficient of the circulant P (Section 3): the constant-step blocks
   std::vector<double> beta_p((size_t)c.ell,
-                             c.equation == AAO_WAVE_BD2      ? c.tau * c.tau / c.h
+                             c.equation == AAO_WAVE_BD2 || c.equation == AAO_WAVE_BD4
+                                                              ? c.tau * c.tau / c.h
                              : c.equation == AAO_HEAT_LITERAL ? 1.0 / c.h
                                                               : c.tau * c.kappa / c.h);
   AAO_CK(c, upload((void **)&c.beta_p, beta_p));
@@ -816,7 +828,8 @@ int aao_create(int64_t n, int64_t ell, double tau, int equation, aao_ctx **out) 
   if (!out) return AAO_EINVAL;
   *out = nullptr;
   if (n < 1 || !(tau > 0.0) || !std::isfinite(tau)) return AAO_EINVAL;
-  if (equation != AAO_HEAT && equation != AAO_WAVE_BD2 && equation != AAO_HEAT_LITERAL)
+  if (equation != AAO_HEAT && equation != AAO_WAVE_BD2 && equation != AAO_HEAT_LITERAL &&
+      equation != AAO_WAVE_BD4)
     return AAO_EINVAL;
   if (ell < 1 || ell > kMaxEll || !fft_length_ok(ell) || n > kMaxN) return AAO_EUNSUPPORTED;
   aao_ctx *h = new (std::nothrow) aao_ctx();

@@ -6,7 +6,7 @@ import pytest
 import synthetic as syn
 from oracle import system
 
-EQ = {"heat": 0, "wave_bd2": 1, "heat_literal": 2}
+EQ = {"heat": 0, "wave_bd2": 1, "heat_literal": 2, "wave_bd4": 3}
 
 
 def need_gpu():
@@ -24,6 +24,8 @@ def oracle_system(kind, n, ell, tau=None, kappa=1.0, taus=None):
         return system.heat(n, ell, tau, kappa)
     if kind == "heat_literal":
         return system.heat(n, ell, tau, literal=True)
+    if kind == "wave_bd4":
+        return system.bd4(n, ell, tau)
     return system.bd2(n, ell, tau)
 
 

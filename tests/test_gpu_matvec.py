@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("n,ell", [(1, 1), (2, 3), (5, 7), (33, 16), (255, 64), (1000, 9)])
-@pytest.mark.parametrize("kind", ["heat", "wave_bd2", "heat_literal", "steps"])
+@pytest.mark.parametrize("kind", ["heat", "wave_bd2", "heat_literal", "steps", "wave_bd4"])
 @pytest.mark.parametrize("transpose", [False, True])
 def test_matvec_matches_oracle(n, ell, kind, transpose):
     torch = need_gpu()
@@ -56,19 +56,22 @@ def test_matvec_full_size():
     assert rel_max(got, system.matvec_T(S, X)) <= 1e-13
 
 
-@pytest.mark.parametrize("kind", ["heat", "wave_bd2", "heat_literal"])
+@pytest.mark.parametrize("kind", ["heat", "wave_bd2", "heat_literal", "wave_bd4"])
 @pytest.mark.parametrize("with_v0", [False, True])
-def test_rhs_matches_oracle(kind, with_v0):
+@pytest.mark.parametrize("ell", [1, 2, 4, 16])
+def test_rhs_matches_oracle(kind, with_v0, ell):
     torch = need_gpu()
     from paper_1810_00615_gb300 import AllAtOnce
-    if with_v0 and kind != "wave_bd2":
+    if with_v0 and not kind.startswith("wave"):
         pytest.skip("initial velocity is a wave input")
-    n, ell = 63, 16
+    n = 63
     S = oracle_system(kind, n, ell)
     u0, v0 = syn.wave_initial(n, modes=16)
     a = AllAtOnce(n, ell, 1.0 / ell, equation=kind, restart=1)
     if kind == "wave_bd2":
         want = system.rhs_bd2(S, u0, v0 if with_v0 else None)
+    elif kind == "wave_bd4":
+        want = system.rhs_bd4(S, u0, v0 if with_v0 else None)
     else:
         want = system.rhs_heat(S, u0)
     got = to_host(a.build_rhs(to_dev(torch, u0), to_dev(torch, v0) if with_v0 else None))

@@ -39,6 +39,7 @@ def _abs_system(S):
     T.__dict__.update(S.__dict__)
     T.diag = [abs(D) for D in S.diag]
     T.lower = [abs(L) for L in S.lower]
+    T.startup = {k: abs(B) for k, B in S.startup.items()}
     return T
 
 
@@ -53,16 +54,16 @@ def _context(kind, n, ell):
     return S, a
 
 
-def _tile_max(X):
+def _tile_max(X, lags=2):
     """For each output (t, i): max |x| over the fixed-point tile that forms it
-    (its 32 columns with one halo column each side, its 32 steps with the two
-    lag steps on either side)."""
+    (its 32 columns with one halo column each side, its 32 steps with the
+    lag steps on either side: two, three for BD4)."""
     ell, n = X.shape
     A = np.abs(X)
     T = np.zeros_like(A)
     for t0 in range(0, ell, 32):
         for i0 in range(0, n, 32):
-            blk = A[max(0, t0 - 2):min(ell, t0 + 34), max(0, i0 - 1):min(n, i0 + 33)]
+            blk = A[max(0, t0 - lags):min(ell, t0 + 32 + lags), max(0, i0 - 1):min(n, i0 + 33)]
             T[t0:t0 + 32, i0:i0 + 32] = blk.max()
     return T
 
@@ -70,12 +71,15 @@ def _tile_max(X):
 def _bound(S, X, transpose):
     """8 FP64 roundings of (|A| |x|)_i plus the documented truncation: inputs
     far below their tile maximum enter with an absolute error under 2^-57 of
-    it (2^-56 here for margin), times the row sums of |A|."""
+    it (2^-55 for BD4, whose fixed point keeps two guard bits; here twice
+    that for margin), times the row sums of |A|."""
     absS = _abs_system(S)
     f = system.matvec_T if transpose else system.matvec
     mag = f(absS, np.abs(X))
     rows = f(absS, np.ones_like(X))
-    return 8 * EPS * mag + 2.0 ** -56 * rows * _tile_max(X)
+    bd4 = S.kind == "bd4"
+    trunc = 2.0 ** (-54 if bd4 else -56)
+    return 8 * EPS * mag + trunc * rows * _tile_max(X, 3 if bd4 else 2)
 
 
 def _exact(S, X, transpose):
@@ -93,9 +97,10 @@ def _exact(S, X, transpose):
     Y = np.zeros_like(Xl)
     for t in range(S.ell):
         y = apply(S.diag[t].T if transpose else S.diag[t], Xl[t])
-        for j, Aj in enumerate(S.lower, start=1):
+        for j in range(1, len(S.lower) + 1):
             s = t + j if transpose else t - j
             if 0 <= s < S.ell:
+                Aj = system.lag_block(S, s if transpose else t, j)
                 y = y + apply(Aj.T if transpose else Aj, Xl[s])
         Y[t] = y
     return Y
@@ -103,7 +108,7 @@ def _exact(S, X, transpose):
 
 @pytest.mark.parametrize("n,ell", [(1, 1), (2, 2), (5, 8), (33, 16), (65, 64), (255, 128),
                                    (1000, 32)])
-@pytest.mark.parametrize("kind", ["heat", "wave_bd2", "heat_literal", "steps"])
+@pytest.mark.parametrize("kind", ["heat", "wave_bd2", "heat_literal", "steps", "wave_bd4"])
 @pytest.mark.parametrize("transpose", [False, True])
 def test_matvec_f32_matches_oracle(n, ell, kind, transpose):
     torch = need_gpu()
@@ -126,7 +131,7 @@ def test_matvec_f32_matches_oracle(n, ell, kind, transpose):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
-@pytest.mark.parametrize("kind", ["heat", "wave_bd2", "steps"])
+@pytest.mark.parametrize("kind", ["heat", "wave_bd2", "steps", "wave_bd4"])
 @pytest.mark.parametrize("transpose", [False, True])
 def test_matvec_elementwise_rounding_bound(kind, transpose, dtype):
     """A near-cancelling input (the rounded time-stepping solution) and a
@@ -137,6 +142,9 @@ def test_matvec_elementwise_rounding_bound(kind, transpose, dtype):
     if kind == "wave_bd2":
         u0, v0 = syn.wave_initial(n, modes=16)
         B = system.rhs_bd2(S, u0, v0)
+    elif kind == "wave_bd4":
+        u0, v0 = syn.wave_initial(n, modes=16)
+        B = system.rhs_bd4(S, u0, v0)
     else:
         B = system.rhs_heat(S, syn.heat_initial(n, modes=8))
     U = system.forward_substitution(S, B)

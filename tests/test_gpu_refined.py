@@ -29,7 +29,7 @@ def kappa(S):
 
 def refined_tol(S, kind, n, ell):
     t = fp32_tol(n, ell)
-    if kind == "wave_bd2":
+    if kind.startswith("wave"):
         t = max(t, kappa(S) * 2.0 ** -24)
     return 32 * t * t + 4 * kappa(S) * 2.0 ** -53
 
@@ -39,7 +39,7 @@ SHAPES = [(1, 1), (2, 4), (15, 16), (17, 16), (33, 64), (100, 128), (255, 256), 
 
 
 @pytest.mark.parametrize("n,ell", SHAPES)
-@pytest.mark.parametrize("kind", ["heat", "wave_bd2", "heat_literal"])
+@pytest.mark.parametrize("kind", ["heat", "wave_bd2", "heat_literal", "wave_bd4"])
 @pytest.mark.parametrize("transpose", [False, True])
 def test_refined_apply_matches_oracle(n, ell, kind, transpose):
     torch = need_gpu()
