@@ -204,7 +204,8 @@ def _timed(fn, reps, stream):
 def extra_rows(device, hbm_peak):
     """The other rows of the hot path, each timed with CUDA events: the FP64
     preconditioner apply, Neumann applies and solves on the perturbed grid,
-    the BD2 wave solve (n = 8191, ell = 2048) and the adjoint pass
+    the BD2 wave solve (n = 8191, ell = 2048), BD4 wave solves and the
+    adjoint pass
     (n = 16383, ell = 1024)."""
     import torch
     import synthetic as syn
@@ -261,6 +262,27 @@ def extra_rows(device, hbm_peak):
         wave[prec] = {"ms": round(ms, 3), "iters": info["iters"], "relres": info["relres_true"]}
     rows["wave_bd2_n8191_ell2048_gmres40"] = wave
     del sw, bw
+    torch.cuda.empty_cache()
+    # BD4 wave (C_BD4 preconditioned by R_BD4) on the non-smooth bump of
+    # Table 3, tolerance 1e-5: the paper's largest Table 3 shape and n = 1023,
+    # ell = 1024 (larger BD4 systems stagnate even with the FP64 R_BD4)
+    bd4 = {}
+    for n4, l4, rs in ((96, 96, 50), (1023, 1024, 100)):
+        s4 = AllAtOnce(n4, l4, 1.0 / l4, equation="wave_bd4", precision="fp64", restart=rs,
+                       device=device)
+        b4 = s4.build_rhs(torch.from_numpy(syn.wave_nonsmooth(n4)).to(device))
+        entry = {}
+        for prec in ("fp64", "fp32_refined"):
+            s4.set_precision(prec)
+            s4.solve(b4, restart=rs, rtol=1e-5, maxit=1000)
+            info = {}
+            ms = _timed(lambda i: info.update(s4.solve(b4, restart=rs, rtol=1e-5,
+                                                       maxit=1000)[1]), 2, stream)
+            entry[prec] = {"ms": round(ms, 3), "iters": info["iters"],
+                           "relres": info["relres_true"]}
+        bd4[f"n{n4}_ell{l4}_gmres{rs}"] = entry
+        del s4, b4
+    rows["wave_bd4_bump_tol1e-5"] = bd4
     torch.cuda.empty_cache()
     # adjoint pass, n = 16383, ell = 1024: forward solve, adjoint solve, gradients
     na, la = 16383, 1024

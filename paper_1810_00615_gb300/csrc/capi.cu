@@ -748,6 +748,23 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
       const bool breakdown = !(hn > 1e-300);
       // v_{j+1} = w~ / hn = (sc_j / hn) W~
       sc[(size_t)j + 1] = breakdown ? 0.0 : sc[(size_t)j] / hn;
+      // The stored vectors' norms drift by the factor hn per step.  Where
+      // that product leaves [2^-60, 2^60] (long cycles of an ill-conditioned
+      // P, e.g. R_BD4), scale the stored vector to unit norm: the squared
+      // norms must stay finite and the FP32 preconditioner must see its input
+      // inside the FP32 range.
+      if (!breakdown) {
+        const double sa = std::fabs(sc[(size_t)j + 1]);
+        if (sa > 0x1p60 || sa < 0x1p-60) {
+          double *d_s = small + 950;
+          hs[950] = sc[(size_t)j + 1];
+          AAO_CK(c, cudaMemcpyAsync(d_s, hs + 950, sizeof(double), cudaMemcpyHostToDevice, s));
+          AAO_CK(c, run(c, AAO_K_UPDATE, s, [&] {
+            return aao::launch_scale(w, w, d_s, N, false, s);
+          }));
+          sc[(size_t)j + 1] = 1.0;
+        }
+      }
       for (int i = 0; i < j; i++) {
         const double t = cs[(size_t)i] * Hij(i, j) + sn[(size_t)i] * Hij(i + 1, j);
         Hij(i + 1, j) = -sn[(size_t)i] * Hij(i, j) + cs[(size_t)i] * Hij(i + 1, j);
