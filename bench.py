@@ -222,6 +222,27 @@ def extra_rows(device, hbm_peak):
     b64 = 8 * Nel + 2 * spec + 2 * (2 * spec) + 2 * spec + 8 * Nel
     rows["precond_apply_fp64"] = {"us": round(1e3 * ms, 1), "GB_s": round(b64 / ms / 1e6, 1),
                                   "bytes": b64, "note": "FP64 pipe bound (FFT and solves in FP64)"}
+    # the DST-in-space form of the frequency-block solves (same apply; the
+    # elimination kernel replaced by sine transforms in space), FP32 and FP64
+    dst = {}
+    for prec in ("fp32", "fp64"):
+        a.set_precision(prec)
+        a.set_space_solver("dst")
+        ms = _timed(lambda i: a.precond_apply(x[i % 2], out=y[i % 2]), 10, stream)
+        a.profile_read(reset=True)
+        a.profile(True)
+        for i in range(5):
+            a.precond_apply(x[i % 2], out=y[i % 2])
+        torch.cuda.synchronize()
+        pr = a.profile_read(reset=True)
+        a.profile(False)
+        kus = 1e3 * pr["tridiag"][0] / 5
+        esz = 8 if prec == "fp32" else 16
+        kb = 2 * esz * n * (ell // 2 + 1)
+        dst[prec] = {"apply_us": round(1e3 * ms, 1), "dst_kernel_us": round(kus, 1),
+                     "dst_kernel_GB_s": round(kb / kus / 1e3, 1)}
+        a.set_space_solver("tridiag")
+    rows["precond_apply_dst_in_space"] = dst
     # Neumann on the perturbed grid (delta = 0.5)
     a.set_precision("fp32")
     a.set_steps(syn.time_steps(ell, 0.5, syn.rng(3)))
@@ -246,6 +267,20 @@ def extra_rows(device, hbm_peak):
             rows[f"solve_steps_delta0.5_{prec}_precond{pc}"] = {
                 "ms": round(ms, 3), "iters": info["iters"], "relres": info["relres_true"]}
     del sv, bb
+    torch.cuda.empty_cache()
+    # the headline solve with the DST-in-space frequency-block solves
+    sd = AllAtOnce(n, ell, 1.0 / ell, precision="fp32_refined", restart=RESTART, device=device,
+                   space="dst")
+    bd = sd.build_rhs(torch.from_numpy(syn.heat_initial(n)).to(device))
+    dsol = {}
+    for prec in ("fp32_refined", "fp32"):
+        sd.set_precision(prec)
+        sd.solve(bd, restart=RESTART, rtol=RTOL)
+        info = {}
+        ms = _timed(lambda i: info.update(sd.solve(bd, restart=RESTART, rtol=RTOL)[1]), 3, stream)
+        dsol[prec] = {"ms": round(ms, 3), "iters": info["iters"], "relres": info["relres_true"]}
+    rows["solve_dst_in_space"] = dsol
+    del sd, bd
     torch.cuda.empty_cache()
     # BD2 wave, n = 8191, ell = 2048, 16-mode displacement and velocity
     nw, lw = 8191, 2048

@@ -126,6 +126,19 @@ int aao_set_steps(aao_ctx *ctx, const double *tau_steps_host);
  * choice of how to evaluate the Section 3 preconditioner on this hardware. */
 int aao_set_precision(aao_ctx *ctx, int prec);
 
+/* How the per-frequency blocks cM_k M + cK K of P are solved (Section 3).
+ * AAO_SPACE_TRIDIAG (default): elimination of the complex tridiagonal block
+ *   in row-excess form (any n).
+ * AAO_SPACE_DST: the spatial blocks diagonalised too, by sine transforms:
+ *   a DST-I of each frequency row, division by lambda_kj = cM_k m_j + cK k_j
+ *   (m_j, k_j the DST-I eigenvalues of M and K), the inverse DST-I.  Each
+ *   mode is then divided exactly once, so its relative accuracy is that of
+ *   the transforms whatever the block's condition number.  Needs n + 1 a
+ *   power of two with 16 <= n + 1 <= 4096 (AAO_EUNSUPPORTED otherwise).
+ * Applies to every apply entry point (P, Neumann, refined, the solves). */
+enum { AAO_SPACE_TRIDIAG = 0, AAO_SPACE_DST = 1 };
+int aao_set_space_solver(aao_ctx *ctx, int solver);
+
 /* Bytes of device workspace that the solve calls need for GMRES(restart)
  * (restart >= 1).  The apply calls need aao_workspace_bytes(ctx, 0). */
 size_t aao_workspace_bytes(const aao_ctx *ctx, int restart);

@@ -21,11 +21,12 @@ import torch
 from . import _build
 from ._capi import (AAO_ECUDA, AAO_EINVAL, AAO_ENOCONV, AAO_ENUMERIC, AAO_EUNSUPPORTED,
                     AAO_HEAT, AAO_HEAT_LITERAL, AAO_OK, AAO_PREC_FP32, AAO_PREC_FP32_REFINED, AAO_PREC_FP64,
+                    AAO_SPACE_DST, AAO_SPACE_TRIDIAG,
                     AAO_WAVE_BD2, AAO_WAVE_BD4, AAOError, SolveInfo, check, lib)
 
 __all__ = ["AllAtOnce", "AAOSolve", "SolveInfo", "AAOError", "lib", "build",
            "AAO_HEAT", "AAO_WAVE_BD2", "AAO_WAVE_BD4", "AAO_HEAT_LITERAL", "AAO_PREC_FP32", "AAO_PREC_FP32_REFINED", "AAO_PREC_FP64",
-           "AAO_OK", "AAO_ENOCONV", "AAO_EINVAL", "AAO_ECUDA", "AAO_ENUMERIC",
+           "AAO_SPACE_TRIDIAG", "AAO_SPACE_DST", "AAO_OK", "AAO_ENOCONV", "AAO_EINVAL", "AAO_ECUDA", "AAO_ENUMERIC",
            "AAO_EUNSUPPORTED"]
 
 EQUATIONS = {"heat": AAO_HEAT, "wave_bd2": AAO_WAVE_BD2, "heat_literal": AAO_HEAT_LITERAL,
@@ -63,7 +64,7 @@ class AllAtOnce:
 
     def __init__(self, n: int, ell: int, tau: Optional[float] = None, equation="heat",
                  kappa: float = 1.0, precision: str = "fp32", restart: int = 30,
-                 device=None):
+                 device=None, space: str = "tridiag"):
         self.lib = lib()
         self.n, self.ell = int(n), int(ell)
         self.N = self.n * self.ell
@@ -78,6 +79,9 @@ class AllAtOnce:
         if kappa != 1.0:
             self.set_kappa(kappa)
         self.set_precision(precision)
+        self.space = "tridiag"
+        if space != "tridiag":
+            self.set_space_solver(space)
         self._ws = None
         self._restart = 0
         self.ensure_workspace(restart)
@@ -107,6 +111,11 @@ class AllAtOnce:
              "fp32_refined": AAO_PREC_FP32_REFINED}[precision]
         check(self.lib.aao_set_precision(self._ctx, p), "aao_set_precision", self._ctx)
         self.precision = precision
+
+    def set_space_solver(self, space: str):
+        sv = {"tridiag": AAO_SPACE_TRIDIAG, "dst": AAO_SPACE_DST}[space]
+        check(self.lib.aao_set_space_solver(self._ctx, sv), "aao_set_space_solver", self._ctx)
+        self.space = space
 
     def workspace_bytes(self, restart: int) -> int:
         return int(self.lib.aao_workspace_bytes(self._ctx, int(restart)))

@@ -20,7 +20,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libaao.so")
 STAMP = os.path.join(PKG, "libaao.stamp")
-SOURCES = ["capi.cu", "blas.cu", "tridiag.cu", "fft_f32.cu", "fft_f64.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "blas.cu", "tridiag.cu", "fft_f32.cu", "fft_f64.cu", "noalloc.cu",
+           "dst.cu"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 

@@ -279,6 +279,13 @@ struct Ctx {
   int lsz32[kRecLevels] = {0}, lsz64[kRecLevels] = {0};   // unknowns per level
   cx<float> *tw32 = nullptr;      // exp(-2 pi i m/ell), m < ell
   cx<double> *tw64 = nullptr;
+  int space = AAO_SPACE_TRIDIAG;  // per-frequency solver
+  cx<float> *dtw32 = nullptr;     // DST form: exp(-2 pi i m/(2(n+1))), m < 2(n+1)
+  cx<double> *dtw64 = nullptr;
+  void *dst_cm32 = nullptr;       // cM_k per frequency (FP32: float4 hi/lo pairs; FP64: cx)
+  void *dst_cm64 = nullptr;
+  void *dst_mk32 = nullptr;       // (m_j, cK k_j) per mode j = 1..n (same forms)
+  void *dst_mk64 = nullptr;
   double *beta = nullptr;         // per-step K coefficient tau_t kappa / h (ell)
   double *beta_p = nullptr;       // K coefficient of the circulant P (constant step) (ell)
   struct MvRow *mv_rows = nullptr;     // fixed-point matvec: per-step combination of A
@@ -371,6 +378,10 @@ cudaError_t fft_inverse_f32_to_f32(const Ctx &c, const void *spec, float *y, cud
                                    void *inter = nullptr);
 cudaError_t launch_tridiag(const Ctx &c, void *spec, int prec, int transpose,
                            cudaStream_t s);
+// The same solves by DST-I in space (AAO_SPACE_DST), in place on the spectrum.
+constexpr int64_t kDstMaxL = 4096;   // n + 1 <= kDstMaxL, a power of two
+bool dst_supported(int64_t n);
+cudaError_t launch_dst_solve(const Ctx &c, void *spec, int prec, int transpose, cudaStream_t s);
 // y = A x (or A^T x); with `sub`, y = A x - sub (fused, for the shifted Arnoldi).
 cudaError_t launch_matvec(const Ctx &c, const double *x, double *y, int transpose,
                           cudaStream_t s, const double *sub = nullptr);

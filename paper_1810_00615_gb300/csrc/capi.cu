@@ -300,6 +300,51 @@ cudaError_t collect(Ctx &c) {
   return cudaSuccess;
 }
 
+// Tables of the DST-in-space solver: the twiddles of the length-2(n+1)
+// transform, cM_k (k < nk) and (m_j, cK k_j) for the sine modes j = 1..n
+// with m_j = (h/6)(4 + 2 cos th) = h (1 - (2/3) sin^2(th/2)) and k_j =
+// (2/h)(1 - cos th) = (4/h) sin^2(th/2), th = pi j/(n+1).
+cudaError_t upload_dst_tables(Ctx &c) {
+  const int64_t n = c.n, L2 = 2 * (n + 1);
+  std::vector<cx<float>> tw32((size_t)L2);
+  std::vector<float4> cm32((size_t)c.nk), mk32((size_t)n);   // hi + lo pairs
+  std::vector<cx<double>> tw64((size_t)L2), cm64((size_t)c.nk), mk64((size_t)n);
+  auto split = [](double v, float &hi, float &lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+  };
+  for (int64_t m = 0; m < L2; m++) {
+    const double co = sinpi_q(4 * m + L2, 2 * L2), si = sinpi_q(2 * m, L2);
+    tw64[(size_t)m] = aao::mk(co, -si);
+    tw32[(size_t)m] = aao::mk((float)co, (float)-si);
+  }
+  double cK = 0.0;
+  for (int64_t k = 0; k < c.nk; k++) {
+    cd cM;
+    block_symbol(c, k, cM, cK);
+    cm64[(size_t)k] = aao::mk(cM.real(), cM.imag());
+    float4 &q = cm32[(size_t)k];
+    split(cM.real(), q.x, q.y);
+    split(cM.imag(), q.z, q.w);
+  }
+  for (int64_t j = 1; j <= n; j++) {
+    const double sh = sinpi_q(j, L2);                // sin(th/2)
+    const double mj = c.h * (1.0 - (2.0 / 3.0) * sh * sh);
+    const double kj = (4.0 / c.h) * sh * sh;
+    mk64[(size_t)j - 1] = aao::mk(mj, cK * kj);
+    float4 &q = mk32[(size_t)j - 1];
+    split(mj, q.x, q.y);
+    split(cK * kj, q.z, q.w);
+  }
+  cudaError_t e = upload((void **)&c.dtw32, tw32);
+  if (e == cudaSuccess) e = upload((void **)&c.dtw64, tw64);
+  if (e == cudaSuccess) e = upload(&c.dst_cm32, cm32);
+  if (e == cudaSuccess) e = upload(&c.dst_cm64, cm64);
+  if (e == cudaSuccess) e = upload(&c.dst_mk32, mk32);
+  if (e == cudaSuccess) e = upload(&c.dst_mk64, mk64);
+  return e;
+}
+
 // (Re)compute everything that depends on kappa, the steps or tau.
 int refresh_constants(Ctx &c) {
   // per-frequency tridiagonal tables
@@ -339,6 +384,8 @@ int refresh_constants(Ctx &c) {
       AAO_CK(c, upload(&c.rec64, r64));
     }
   }
+  // DST-in-space form: cM_k per frequency, (m_j, cK k_j) per mode
+  if (c.space == AAO_SPACE_DST) AAO_CK(c, upload_dst_tables(c));
   // matvec K coefficients beta_t and Neumann coefficients (tau_t - tau) kappa / h
   std::vector<double> beta((size_t)c.ell), sk((size_t)c.ell, 0.0);
   std::vector<double> d0((size_t)c.ell), o0((size_t)c.ell);
@@ -901,7 +948,8 @@ void aao_destroy(aao_ctx *ctx) {
   Ctx &c = ctx->c;
   void *ptrs[] = {c.tab32, c.tab64, c.rec32, c.rec64, c.tw32, c.tw64, c.beta, c.beta_p,
                   c.mv_rows, c.mv_rows_p, c.mv_d0, c.mv_o0,
-                  c.sigk, c.sigk32};
+                  c.sigk, c.sigk32, c.dtw32, c.dtw64, c.dst_cm32, c.dst_cm64,
+                  c.dst_mk32, c.dst_mk64};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c.host_small) cudaFreeHost(c.host_small);
@@ -941,6 +989,16 @@ int aao_set_precision(aao_ctx *ctx, int prec) {
     return AAO_EINVAL;
   ctx->c.refine = prec == AAO_PREC_FP32_REFINED;
   ctx->c.prec = ctx->c.refine ? AAO_PREC_FP32 : prec;
+  return AAO_OK;
+}
+
+int aao_set_space_solver(aao_ctx *ctx, int solver) {
+  if (!ctx || (solver != AAO_SPACE_TRIDIAG && solver != AAO_SPACE_DST)) return AAO_EINVAL;
+  Ctx &c = ctx->c;
+  if (solver == AAO_SPACE_DST && !aao::dst_supported(c.n)) return AAO_EUNSUPPORTED;
+  if (solver == c.space) return AAO_OK;
+  c.space = solver;
+  if (solver == AAO_SPACE_DST) AAO_CK(c, upload_dst_tables(c));
   return AAO_OK;
 }
 

@@ -629,6 +629,7 @@ static cudaError_t run_tridiag(const Ctx &c, void *spec, const void *tab, int P,
 }
 
 cudaError_t launch_tridiag(const Ctx &c, void *spec, int prec, int transpose, cudaStream_t s) {
+  if (c.space == AAO_SPACE_DST) return launch_dst_solve(c, spec, prec, transpose, s);
   if (prec == AAO_PREC_FP32 && c.clu32 > 1)
     return run_tridiag_cluster<float, 16>(c, spec, c.rec32, c.cta32, c.clu32, transpose, c.lev32,
                                           c.lsz32, s);

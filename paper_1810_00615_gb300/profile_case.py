@@ -4,6 +4,7 @@ profilers (ncu) and quick timing.
     python -m paper_1810_00615_gb300.profile_case --op precond --n 4095 --ell 4096 \\
         --prec fp32 --reps 3
 
+--space tridiag | dst selects the frequency-block solver.
 --op precond | neumann | matvec | matvec_sub | matvec_f32 | solve (matvec_sub,
 matvec_f32: the fused product w = A z - v of an FP64 or FP32 z, as the solver
 forms it in its Arnoldi step).  Prints one line with the mean CUDA-
@@ -31,6 +32,7 @@ def main(argv=None):
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp32_refined", "fp64"])
     ap.add_argument("--equation", default="heat")
     ap.add_argument("--terms", type=int, default=2)
+    ap.add_argument("--space", default="tridiag", choices=["tridiag", "dst"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
     a = ap.parse_args(argv)
@@ -40,7 +42,7 @@ def main(argv=None):
     from paper_1810_00615_gb300 import AllAtOnce
 
     s = AllAtOnce(a.n, a.ell, 1.0 / a.ell, equation=a.equation, precision=a.prec,
-                  restart=30 if a.op == "solve" else 1)
+                  restart=30 if a.op == "solve" else 1, space=a.space)
     if a.op == "neumann":
         s.set_steps(syn.time_steps(a.ell, 0.5, syn.rng(3)))
     g = torch.Generator(device="cuda").manual_seed(1)
@@ -75,7 +77,7 @@ def main(argv=None):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / a.reps
-    print(f"op={a.op} n={a.n} ell={a.ell} prec={a.prec} ms_per_call={ms:.4f} "
+    print(f"op={a.op} n={a.n} ell={a.ell} prec={a.prec} space={a.space} ms_per_call={ms:.4f} "
           f"launches={s.kernel_launches()}")
     return 0
 
