@@ -481,14 +481,18 @@ def run_gpu(args):
         x, info = solver.solve(b, restart=RESTART, rtol=RTOL, maxit=MAXIT, precond=1)
         return x, info
 
+    # The clock sampler starts before the warm-up: nvidia-smi's start-up
+    # (driver queries for a fraction of a second) then overlaps the warm-up
+    # instead of the timed region.
+    clocks = ClockSampler(torch.cuda.current_device() if not os.environ.get(
+        "CUDA_VISIBLE_DEVICES") else int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local]))
+    clocks.start()
+    time.sleep(0.5)
     for _ in range(max(args.warmup, 1)):
         step(HEADLINE_PREC)
     torch.cuda.synchronize()
 
     # ---- timed region: K mixed-precision solves
-    clocks = ClockSampler(torch.cuda.current_device() if not os.environ.get(
-        "CUDA_VISIBLE_DEVICES") else int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local]))
-    clocks.start()
     launches0 = solver.kernel_launches()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]

@@ -139,6 +139,13 @@ int aao_set_precision(aao_ctx *ctx, int prec);
 enum { AAO_SPACE_TRIDIAG = 0, AAO_SPACE_DST = 1 };
 int aao_set_space_solver(aao_ctx *ctx, int solver);
 
+/* Initial guess of aao_gmres_solve and aao_adjoint_solve.  AAO_GUESS_GIVEN
+ * (default): x holds the initial guess on entry.  AAO_GUESS_ZERO: the solve
+ * starts from x0 = 0 and never reads x, which is then output only and need
+ * not be initialised (saves filling it and two passes over it). */
+enum { AAO_GUESS_GIVEN = 0, AAO_GUESS_ZERO = 1 };
+int aao_set_initial_guess(aao_ctx *ctx, int mode);
+
 /* Bytes of device workspace that the solve calls need for GMRES(restart)
  * (restart >= 1).  The apply calls need aao_workspace_bytes(ctx, 0). */
 size_t aao_workspace_bytes(const aao_ctx *ctx, int restart);
@@ -213,7 +220,7 @@ int aao_build_rhs(aao_ctx *ctx, const double *u0, const double *v0, double *b,
 /* Solve A x = b by flexible GMRES(restart), right-preconditioned, FP64
  * Arnoldi with classical Gram-Schmidt and re-orthogonalisation, Givens
  * rotations on the host, the true residual recomputed in FP64 at every
- * restart.  precond: 0 none, 1 the circulant P (R_BD2, R_BD4), i >= 2 the Neumann
+ * restart (x0 = 0 without reading x under AAO_GUESS_ZERO).  precond: 0 none, 1 the circulant P (R_BD2, R_BD4), i >= 2 the Neumann
  * series Q_i^{-1}.  Stops when ||b - A x|| <= rtol ||b|| (true residual), or
  * with AAO_ENOCONV (x holds the last iterate) after maxit Arnoldi steps or
  * when three restart cycles in a row lower the true residual by less than

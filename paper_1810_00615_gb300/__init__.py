@@ -196,9 +196,14 @@ class AllAtOnce:
         self.ensure_workspace(restart)
         b = _dev_f64(b, self.N, "b")
         if x0 is None:
-            x = torch.zeros(self.ell, self.n, dtype=torch.float64, device=self.device)
+            # x0 = 0 without a fill: the solver never reads x and writes it whole
+            x = torch.empty(self.ell, self.n, dtype=torch.float64, device=self.device)
+            guess = 1
         else:
             x = _dev_f64(x0, self.N, "x0").clone()
+            guess = 0
+        check(self.lib.aao_set_initial_guess(self._ctx, guess), "aao_set_initial_guess",
+              self._ctx)
         info = SolveInfo()
         hist = None
         if history:

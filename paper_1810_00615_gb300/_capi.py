@@ -15,6 +15,7 @@ from . import _build
 AAO_HEAT, AAO_WAVE_BD2, AAO_HEAT_LITERAL, AAO_WAVE_BD4 = 0, 1, 2, 3
 AAO_PREC_FP64, AAO_PREC_FP32, AAO_PREC_FP32_REFINED = 0, 1, 2
 AAO_SPACE_TRIDIAG, AAO_SPACE_DST = 0, 1
+AAO_GUESS_GIVEN, AAO_GUESS_ZERO = 0, 1
 AAO_OK, AAO_ENOCONV = 0, 1
 AAO_EINVAL, AAO_ENOMEM, AAO_ECUDA, AAO_ENUMERIC, AAO_EUNSUPPORTED = -1, -2, -3, -4, -5
 KERNEL_CLASSES = ["fft_forward", "tridiag", "fft_inverse", "matvec", "dots", "update",
@@ -41,6 +42,7 @@ SIGNATURES = {
     "aao_set_steps": (C.c_int, [C.c_void_p, C.c_void_p]),
     "aao_set_precision": (C.c_int, [C.c_void_p, C.c_int]),
     "aao_set_space_solver": (C.c_int, [C.c_void_p, C.c_int]),
+    "aao_set_initial_guess": (C.c_int, [C.c_void_p, C.c_int]),
     "aao_workspace_bytes": (C.c_size_t, [C.c_void_p, C.c_int]),
     "aao_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "aao_precond_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),

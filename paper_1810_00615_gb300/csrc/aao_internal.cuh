@@ -291,6 +291,7 @@ struct Ctx {
   struct MvRow *mv_rows = nullptr;     // fixed-point matvec: per-step combination of A
   struct MvRow *mv_rows_p = nullptr;   // the same for the circulant P
   bool refine = false;            // FP32 preconditioner with one refinement sweep
+  int guess = AAO_GUESS_GIVEN;    // solves read x as the initial guess, or start from 0
   double *mv_d0 = nullptr;        // per-step diagonal of A0^t (ell)
   double *mv_o0 = nullptr;        // per-step off-diagonal of A0^t (ell)
   double mv_d1 = 0, mv_o1 = 0, mv_d2 = 0, mv_o2 = 0;   // A1, A2 (diag, off)
@@ -413,10 +414,11 @@ cudaError_t launch_update_dots(const double *const *V, int nv, const double *h,
                                double *w, int64_t N, bool want_dots, double *partials,
                                double *out2, cudaStream_t s, const double *hf = nullptr);
 // x += sum_j y[j] Z_j (y on device)
+// x += Z y, or x = Z y (x not read) with assign
 cudaError_t launch_combine(const double *const *Z, int nv, const double *y, double *x,
-                           int64_t N, cudaStream_t s);
+                           int64_t N, cudaStream_t s, bool assign = false);
 cudaError_t launch_combine(const float *const *Z, int nv, const double *y, double *x,
-                           int64_t N, cudaStream_t s);
+                           int64_t N, cudaStream_t s, bool assign = false);
 // y = a*x (a on device, *a_scale of index)
 cudaError_t launch_scale(const double *x, double *y, const double *a, int64_t N,
                          bool invert, cudaStream_t s, bool negate = false);

@@ -689,13 +689,14 @@ cudaError_t launch_update_dots(const double *const *V, int nv, const double *h, 
 // ------------------------------------------------------------ x += Z y
 template <int NV, typename ZT>
 __global__ void __launch_bounds__(kThreads)
-k_combine(PtrsT<ZT> Z, const double *__restrict__ yv, double *__restrict__ x, int64_t N) {
+k_combine(PtrsT<ZT> Z, const double *__restrict__ yv, double *__restrict__ x, int64_t N,
+          int assign) {
   double c[NV];
 #pragma unroll
   for (int j = 0; j < NV; j++) c[j] = yv[j];
   for (int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x; g < N;
        g += (int64_t)gridDim.x * kThreads) {
-    double a = x[g];
+    double a = assign ? 0.0 : x[g];   // assign: x = Z y (x not read)
 #pragma unroll
     for (int j = 0; j < NV; j++) a = fma(c[j], wide(__ldg(&Z.p[j][g])), a);
     x[g] = a;
@@ -704,7 +705,7 @@ k_combine(PtrsT<ZT> Z, const double *__restrict__ yv, double *__restrict__ x, in
 
 template <typename ZT>
 static cudaError_t combine_any(const ZT *const *Z, int nv, const double *y, double *x, int64_t N,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool assign) {
   int64_t blocks = (N + kThreads - 1) / kThreads;
   if (blocks > 152 * 16) blocks = 152 * 16;
   int done = 0;
@@ -713,7 +714,7 @@ static cudaError_t combine_any(const ZT *const *Z, int nv, const double *y, doub
     PtrsT<ZT> P{};
     for (int j = 0; j < g; j++) P.p[j] = Z[done + j];
     switch (g) {
-#define AAO_CB(G) case G: k_combine<G, ZT><<<(unsigned)blocks, kThreads, 0, s>>>(P, y + done, x, N); note_launch(); break;
+#define AAO_CB(G) case G: k_combine<G, ZT><<<(unsigned)blocks, kThreads, 0, s>>>(P, y + done, x, N, (assign && done == 0) ? 1 : 0); note_launch(); break;
       AAO_CB(1) AAO_CB(2) AAO_CB(3) AAO_CB(4) AAO_CB(5) AAO_CB(6) AAO_CB(7) AAO_CB(8)
 #undef AAO_CB
     }
@@ -723,13 +724,13 @@ static cudaError_t combine_any(const ZT *const *Z, int nv, const double *y, doub
 }
 
 cudaError_t launch_combine(const double *const *Z, int nv, const double *y, double *x,
-                           int64_t N, cudaStream_t s) {
-  return combine_any(Z, nv, y, x, N, s);
+                           int64_t N, cudaStream_t s, bool assign) {
+  return combine_any(Z, nv, y, x, N, s, assign);
 }
 
 cudaError_t launch_combine(const float *const *Z, int nv, const double *y, double *x,
-                           int64_t N, cudaStream_t s) {
-  return combine_any(Z, nv, y, x, N, s);
+                           int64_t N, cudaStream_t s, bool assign) {
+  return combine_any(Z, nv, y, x, N, s, assign);
 }
 
 // ------------------------------------------------------------ misc

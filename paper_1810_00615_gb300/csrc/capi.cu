@@ -670,12 +670,22 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
   };
   // ||b||^2 and ||x0||^2 in one pass: a zero initial guess makes the first
   // residual -b, so the first cycle needs no matvec (V_0 aliases b, the sign
-  // goes into its lazy scale)
-  AAO_CK(c, run(c, AAO_K_DOTS, s, [&] { return aao::launch_norms2(b, x, N, red, d_nr, s); }));
-  AAO_CK(c, fetch(d_nr, 2));
+  // goes into its lazy scale).  Under AAO_GUESS_ZERO x is not read at all:
+  // only ||b||^2 is formed and the first update assigns x = Z y.
+  const bool guess_zero = c.guess == AAO_GUESS_ZERO;
+  if (guess_zero) {
+    AAO_CK(c, run(c, AAO_K_DOTS, s, [&] {
+      return aao::launch_multidot(nullptr, 0, b, N, true, red, d_nr, s);
+    }));
+    AAO_CK(c, fetch(d_nr, 1));
+  } else {
+    AAO_CK(c, run(c, AAO_K_DOTS, s, [&] { return aao::launch_norms2(b, x, N, red, d_nr, s); }));
+    AAO_CK(c, fetch(d_nr, 2));
+  }
   AAO_CK(c, cudaStreamSynchronize(s));
   const double bnorm = std::sqrt(hs[320]);
-  bool x0_zero = hs[321] == 0.0;
+  bool x0_zero = guess_zero || hs[321] == 0.0;
+  bool x_unset = guess_zero;   // x holds no value yet (written by the first update)
   if (!std::isfinite(bnorm)) return AAO_ENUMERIC;
   if (bnorm == 0.0) {
     AAO_CK(c, cudaMemsetAsync(x, 0, vb, s));
@@ -843,11 +853,13 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
     for (int i = 0; i < jd; i++) hs[480 + i] = y[(size_t)i] * sc[(size_t)i];   // z_i = sc_i Z_i
     AAO_CK(c, cudaMemcpyAsync(d_y, hs + 480, jd * sizeof(double), cudaMemcpyHostToDevice, s));
     AAO_CK(c, run(c, AAO_K_COMBINE, s, [&] {
-      return zf ? aao::launch_combine(Zf.data(), jd, d_y, x, N, s)
-                : aao::launch_combine(Z.data(), jd, d_y, x, N, s);
+      return zf ? aao::launch_combine(Zf.data(), jd, d_y, x, N, s, x_unset)
+                : aao::launch_combine(Z.data(), jd, d_y, x, N, s, x_unset);
     }));
+    if (jd > 0) x_unset = false;
     restarts++;
   }
+  if (x_unset) AAO_CK(c, cudaMemsetAsync(x, 0, vb, s));   // stopped before the first update
   AAO_CK(c, cudaStreamSynchronize(s));
   AAO_CK(c, collect(c));
   if (info) {
@@ -989,6 +1001,12 @@ int aao_set_precision(aao_ctx *ctx, int prec) {
     return AAO_EINVAL;
   ctx->c.refine = prec == AAO_PREC_FP32_REFINED;
   ctx->c.prec = ctx->c.refine ? AAO_PREC_FP32 : prec;
+  return AAO_OK;
+}
+
+int aao_set_initial_guess(aao_ctx *ctx, int mode) {
+  if (!ctx || (mode != AAO_GUESS_GIVEN && mode != AAO_GUESS_ZERO)) return AAO_EINVAL;
+  ctx->c.guess = mode;
   return AAO_OK;
 }
 
@@ -1146,14 +1164,17 @@ int aao_solve_host(aao_ctx *ctx, const double *u0_host, const double *v0_host, d
   cudaStream_t s = as_stream(stream);
   double *db = vec_at(c, L, 2 * restart + 1);
   double *dx = vec_at(c, L, 2 * restart + 2);
-  // u0 and v0 go to the x buffer (n and 2n doubles) before x is zeroed
+  // u0 and v0 go to the x buffer (n and 2n doubles); the solve starts from
+  // x0 = 0 without reading that buffer (AAO_GUESS_ZERO)
   const size_t nb = (size_t)c.n * sizeof(double);
   if ((size_t)c.N < 2 * (size_t)c.n && v0_host) return AAO_EUNSUPPORTED;
   AAO_CK(c, cudaMemcpyAsync(dx, u0_host, nb, cudaMemcpyHostToDevice, s));
   if (v0_host) AAO_CK(c, cudaMemcpyAsync(dx + c.n, v0_host, nb, cudaMemcpyHostToDevice, s));
   AAO_CK(c, run(c, AAO_K_OTHER, s, [&] { return aao::launch_rhs(c, dx, v0_host ? dx + c.n : nullptr, db, s); }));
-  AAO_CK(c, cudaMemsetAsync(dx, 0, (size_t)c.N * sizeof(double), s));
+  const int guess = c.guess;
+  c.guess = AAO_GUESS_ZERO;
   const int st = solve_core(c, 0, db, dx, restart, rtol, maxit, precond, info, s);
+  c.guess = guess;
   if (st < 0) return st;
   AAO_CK(c, cudaMemcpyAsync(U_host, dx, (size_t)c.N * sizeof(double), cudaMemcpyDeviceToHost, s));
   AAO_CK(c, cudaStreamSynchronize(s));

@@ -234,3 +234,31 @@ def test_heat_n65535_large_workload(ell):
     x, info = a.solve(a.build_rhs(to_dev(torch, u0)), restart=20, rtol=2e-8)
     assert info["converged"], info
     _check(S, system.rhs_heat(S, u0), to_host(x), rtol=2e-8, errtol=1e-6)
+
+
+def test_zero_initial_guess_never_reads_x():
+    """AAO_GUESS_ZERO: x is output only.  A NaN-filled x gives the same
+    solution as an explicit zero guess, and a solve stopped before its
+    first update (maxit = 0) returns x = 0."""
+    torch = need_gpu()
+    import ctypes as C
+    from paper_1810_00615_gb300 import AllAtOnce, _capi
+    lib = _capi.lib()
+    n, ell = 255, 256
+    a = AllAtOnce(n, ell, 1.0 / ell, precision="fp32_refined", restart=30)
+    b = a.build_rhs(torch.from_numpy(syn.heat_initial(n, modes=8)).cuda())
+    x_given, info_given = a.solve(b, x0=torch.zeros_like(b), rtol=1e-10)
+    stream = C.c_void_p(int(torch.cuda.current_stream().cuda_stream))
+    for maxit, want in ((300, x_given), (0, torch.zeros_like(b))):
+        x = torch.full_like(b, float("nan"))
+        assert lib.aao_set_initial_guess(a._ctx, _capi.AAO_GUESS_ZERO) == _capi.AAO_OK
+        info = _capi.SolveInfo()
+        st = lib.aao_gmres_solve(a._ctx, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), 30,
+                                 1e-10, maxit, 1, C.byref(info), stream)
+        assert st in (_capi.AAO_OK, _capi.AAO_ENOCONV)
+        assert torch.isfinite(x).all()
+        assert torch.equal(x, want)
+    assert lib.aao_set_initial_guess(a._ctx, 7) == _capi.AAO_EINVAL
+    # the Python wrapper's default (x0=None) takes the same path
+    x_none, info_none = a.solve(b, rtol=1e-10)
+    assert torch.equal(x_none, x_given) and info_none["iters"] == info_given["iters"]
