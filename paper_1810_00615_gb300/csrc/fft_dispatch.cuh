@@ -1,7 +1,9 @@
 // Instantiation and dispatch of the time-axis FFT kernels for one real type.
 #pragma once
+#include <type_traits>
 #include "fft_time.cuh"
 #include "fft_mixed.cuh"
+#include "fft_four.cuh"
 
 namespace aao {
 namespace fft {
@@ -19,6 +21,12 @@ static int persistent_grid(K kern, int threads, size_t smem, int npanels) {
 #ifndef AAO_FFT_SPLIT
 #define AAO_FFT_SPLIT 1
 #endif
+#ifndef AAO_FFT_FOUR
+#define AAO_FFT_FOUR 1
+#endif
+// The four-step kernels serve FP32, ell = 4096, without a Neumann iterate.
+template <typename R, int L>
+constexpr bool kUseFour = AAO_FFT_FOUR && std::is_same<R, float>::value && L == 4096;
 
 // Bytes of the panel-major intermediate of the two-kernel forward transform
 // (0 where the single kernel is used).
@@ -26,7 +34,9 @@ template <typename R, int L>
 static size_t inter_bytes_l(int64_t n) {
   if (!(AAO_FFT_SPLIT && Split<R, L>::OK)) return 0;
   const int W = 2 * Shape<R, L>::C;
-  return (size_t)((n + W - 1) / W) * Split<R, L>::PANEL;
+  const size_t split = (size_t)((n + W - 1) / W) * Split<R, L>::PANEL;
+  if constexpr (kUseFour<R, L>) return split > four_inter_bytes(n) ? split : four_inter_bytes(n);
+  return split;
 }
 
 template <typename R, int L, typename YT>
@@ -36,6 +46,9 @@ static cudaError_t run_forward(int64_t n, int64_t n_pad, const double *x, const 
   using S = Shape<R, L>;
   const int W = 2 * S::C;
   const int np = (int)((n + W - 1) / W);
+  if constexpr (kUseFour<R, L>) {
+    if (inter && !y) return four_forward(n, n_pad, x, spec, tw, s, inter);
+  }
   if constexpr (AAO_FFT_SPLIT && Split<R, L>::OK) {
     if (inter) {
       const int ncx = np * S::C;
@@ -74,6 +87,9 @@ static cudaError_t run_inverse(int64_t n, int64_t n_pad, const cx<R> *spec, OT *
   using S = Shape<R, L>;
   const int W = 2 * S::C;
   const int np = (int)((n + W - 1) / W);
+  if constexpr (kUseFour<R, L>) {
+    if (inter) return four_inverse<OT>(n, n_pad, spec, y, tw, s, inter, base);
+  }
   if constexpr (AAO_FFT_SPLIT && Split<R, L>::OK) {
     if (inter) {
       cx<R> *ip = static_cast<cx<R> *>(inter);

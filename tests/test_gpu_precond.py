@@ -196,3 +196,23 @@ def test_precond_long_rows_cluster_form(n, ell, prec, transpose):
     got = to_host(a.precond_apply(to_dev(torch, X), transpose=transpose))
     want = precond.circulant_inverse_spectral(S, X, transpose=transpose)
     assert rel_max(got, want) <= tol_for(S, "heat", prec, n, ell)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 64, 127, 128, 130, 255])
+@pytest.mark.parametrize("prec", ["fp32", "fp32_refined"])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_precond_ell4096_matches_oracle(n, prec, transpose):
+    """ell = 4096, the benchmark length (the four-step FP32 transforms), at
+    column counts that leave ragged 64-column blocks; the refined mode also
+    runs the inverse with its base (z0 - P^{-1} r)."""
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    ell = 4096
+    S = oracle_system("heat", n, ell)
+    X = rand_block(n, ell, 4000 + n)
+    want = precond.circulant_inverse_spectral(S, X, transpose=transpose)
+    a = AllAtOnce(n, ell, 1.0 / ell, precision=prec, restart=1)
+    got = to_host(a.precond_apply(to_dev(torch, X), transpose=transpose))
+    t = fp32_tol(n, ell)
+    tol = t if prec == "fp32" else 32 * t * t + 4 * kappa(S) * 2.0 ** -53
+    assert rel_max(got, want) <= tol
