@@ -24,9 +24,10 @@ static int persistent_grid(K kern, int threads, size_t smem, int npanels) {
 #ifndef AAO_FFT_FOUR
 #define AAO_FFT_FOUR 1
 #endif
-// The four-step kernels serve FP32, ell = 4096, without a Neumann iterate.
+// The four-step kernels serve FP32, ell = 256 ... 4096, without a Neumann
+// iterate.
 template <typename R, int L>
-constexpr bool kUseFour = AAO_FFT_FOUR && std::is_same<R, float>::value && L == 4096;
+constexpr bool kUseFour = AAO_FFT_FOUR && std::is_same<R, float>::value && Four<L>::OK;
 
 // Bytes of the panel-major intermediate of the two-kernel forward transform
 // (0 where the single kernel is used).
@@ -35,7 +36,10 @@ static size_t inter_bytes_l(int64_t n) {
   if (!(AAO_FFT_SPLIT && Split<R, L>::OK)) return 0;
   const int W = 2 * Shape<R, L>::C;
   const size_t split = (size_t)((n + W - 1) / W) * Split<R, L>::PANEL;
-  if constexpr (kUseFour<R, L>) return split > four_inter_bytes(n) ? split : four_inter_bytes(n);
+  if constexpr (kUseFour<R, L>) {
+    const size_t four = four_inter_bytes(L, n);
+    return split > four ? split : four;
+  }
   return split;
 }
 
@@ -47,7 +51,7 @@ static cudaError_t run_forward(int64_t n, int64_t n_pad, const double *x, const 
   const int W = 2 * S::C;
   const int np = (int)((n + W - 1) / W);
   if constexpr (kUseFour<R, L>) {
-    if (inter && !y) return four_forward(n, n_pad, x, spec, tw, s, inter);
+    if (inter && !y) return four_forward<L>(n, n_pad, x, spec, tw, s, inter);
   }
   if constexpr (AAO_FFT_SPLIT && Split<R, L>::OK) {
     if (inter) {
@@ -88,7 +92,7 @@ static cudaError_t run_inverse(int64_t n, int64_t n_pad, const cx<R> *spec, OT *
   const int W = 2 * S::C;
   const int np = (int)((n + W - 1) / W);
   if constexpr (kUseFour<R, L>) {
-    if (inter) return four_inverse<OT>(n, n_pad, spec, y, tw, s, inter, base);
+    if (inter) return four_inverse<L, OT>(n, n_pad, spec, y, tw, s, inter, base);
   }
   if constexpr (AAO_FFT_SPLIT && Split<R, L>::OK) {
     if (inter) {

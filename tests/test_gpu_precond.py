@@ -198,16 +198,16 @@ def test_precond_long_rows_cluster_form(n, ell, prec, transpose):
     assert rel_max(got, want) <= tol_for(S, "heat", prec, n, ell)
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 64, 127, 128, 130, 255])
+@pytest.mark.parametrize("ell", [256, 512, 1024, 2048, 4096])
+@pytest.mark.parametrize("n", [1, 2, 3, 64, 127, 130])
 @pytest.mark.parametrize("prec", ["fp32", "fp32_refined"])
 @pytest.mark.parametrize("transpose", [False, True])
-def test_precond_ell4096_matches_oracle(n, prec, transpose):
-    """ell = 4096, the benchmark length (the four-step FP32 transforms), at
-    column counts that leave ragged 64-column blocks; the refined mode also
-    runs the inverse with its base (z0 - P^{-1} r)."""
+def test_precond_four_step_lengths_match_oracle(ell, n, prec, transpose):
+    """ell = 256 ... 4096 (the four-step FP32 transforms, factors 16/32/64),
+    at column counts that leave ragged 32-column blocks; the refined mode
+    also runs the inverse with its base (z0 - P^{-1} r)."""
     torch = need_gpu()
     from paper_1810_00615_gb300 import AllAtOnce
-    ell = 4096
     S = oracle_system("heat", n, ell)
     X = rand_block(n, ell, 4000 + n)
     want = precond.circulant_inverse_spectral(S, X, transpose=transpose)
