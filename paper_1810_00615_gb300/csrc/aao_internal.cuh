@@ -89,6 +89,11 @@ __device__ __forceinline__ double to_f64(float f) {
 #ifndef AAO_L2_HINTS
 #define AAO_L2_HINTS 1
 #endif
+// Drop the 128-byte L2 line at p (128-byte aligned) without writing it back
+// to memory: for scratch data that no later access reads.
+__device__ __forceinline__ void discard_l2(const void *p) {
+  asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(p) : "memory");
+}
 __device__ __forceinline__ unsigned long long l2_evict_first() {
   unsigned long long p = 0;
 #if AAO_L2_HINTS

@@ -156,12 +156,31 @@ __device__ __forceinline__ void load_rows(const cx<float> *__restrict__ inter, i
   for (int u = 0; u < U; u++) S[u * kFourT + threadIdx.x] = v[u];
 }
 
+// The W-column segments (two 128-byte lines each, W = 32) of the
+// intermediate rows this CTA has read are dead: drop them from L2 without a
+// write-back.  Rows: (k1a, r) and, if k1b >= 0, (k1b, r) for r < NR when
+// STRIDE = 1 (rows k1 * NR + r); rows (k, STRIDE * k + t) for k < NR when
+// k1b < 0 and STRIDE > 1 (the inverse B access, t = k1a).
+template <int NR, int W>
+__device__ __forceinline__ void discard_rows(const cx<float> *inter, int k1a, int k1b, int stride,
+                                             int ncx, int cb) {
+  static_assert(W * sizeof(cx<float>) == 256, "two lines per row segment");
+  const int nrows = (stride == 1 && k1b >= 0) ? 2 * NR : NR;
+  for (int q = threadIdx.x; q < 2 * nrows; q += kFourT) {
+    const int rr = q >> 1, half = q & 1;
+    size_t row;
+    if (stride == 1) row = (size_t)(rr < NR ? k1a : k1b) * NR + (rr % NR);
+    else row = (size_t)rr * stride + k1a;
+    discard_l2(reinterpret_cast<const char *>(inter + row * ncx + cb) + 128 * half);
+  }
+}
+
 // Forward 2.  grid (ncx / W, L1/2 + 1 = k1 groups {g, L1 - g}); 2 L2 W
 // complex of dynamic shared memory.
 template <int L, int W>
 __global__ void __launch_bounds__(kFourT)
 k_fft4_forward2(const cx<float> *__restrict__ inter, cx<float> *__restrict__ spec, int n,
-                int ncx, int64_t n_pad, const cx<float> *__restrict__ tw) {
+                int ncx, int64_t n_pad, const cx<float> *__restrict__ tw, int discard) {
   constexpr int L1 = Four<L>::L1, L2 = Four<L>::L2;
   extern __shared__ __align__(16) unsigned char four_smem[];
   cx<float> *S0 = reinterpret_cast<cx<float> *>(four_smem), *S1 = S0 + L2 * W;
@@ -172,6 +191,7 @@ k_fft4_forward2(const cx<float> *__restrict__ inter, cx<float> *__restrict__ spe
   load_rows<L2, W>(inter, g, ncx, cb, S0, pol_done);
   if (pair) load_rows<L2, W>(inter, gb, ncx, cb, S1, pol_done);
   __syncthreads();
+  if (discard) discard_rows<L2, W>(inter, g, pair ? gb : -1, 1, ncx, cb);
   dft_columns<L2, W, L, -1>(S0, tw);
   if (pair) dft_columns<L2, W, L, -1>(S1, tw);
   // Z_k for k = k1 + L1 k2 sits at row k2 of its member's buffer; the mirror
@@ -204,7 +224,7 @@ k_fft4_forward2(const cx<float> *__restrict__ inter, cx<float> *__restrict__ spe
 template <int L, int W>
 __global__ void __launch_bounds__(kFourT)
 k_fft4_inverseA(const cx<float> *__restrict__ spec, cx<float> *__restrict__ inter, int n,
-                int ncx, int64_t n_pad, const cx<float> *__restrict__ tw) {
+                int ncx, int64_t n_pad, const cx<float> *__restrict__ tw, int discard) {
   constexpr int L1 = Four<L>::L1, L2 = Four<L>::L2;
   extern __shared__ __align__(16) unsigned char four_smem[];
   cx<float> *S0 = reinterpret_cast<cx<float> *>(four_smem), *S1 = S0 + L2 * W;
@@ -253,6 +273,18 @@ k_fft4_inverseA(const cx<float> *__restrict__ spec, cx<float> *__restrict__ inte
     }
   }
   __syncthreads();
+  if (discard) {
+    // the spectrum rows read here are dead after this kernel: their lines
+    // (2W complex = 512 bytes = 4 lines per row, clipped to the row's n_pad)
+    // leave L2 without a write-back
+    for (int q = threadIdx.x; q < 2 * L2 * 4; q += kFourT) {
+      const int m = q / (L2 * 4), r = q - m * L2 * 4, k2 = r >> 2, part = r & 3;
+      if (m == 1 && !pair) break;
+      const int k = (m ? gb : g) + L1 * k2, col = 2 * cb + 16 * part;
+      if (2 * k > L || col + 16 > n_pad) continue;
+      discard_l2(spec + (size_t)k * n_pad + col);
+    }
+  }
   dft_columns<L2, W, L, +1>(S0, tw);
   if (pair) dft_columns<L2, W, L, +1>(S1, tw);
   for (int e = threadIdx.x; e < 2 * L2 * W; e += kFourT) {
@@ -271,7 +303,7 @@ k_fft4_inverseA(const cx<float> *__restrict__ spec, cx<float> *__restrict__ inte
 template <int L, int W, typename OT>
 __global__ void __launch_bounds__(kFourT)
 k_fft4_inverseB(const cx<float> *__restrict__ inter, OT *__restrict__ y, int n, int ncx,
-                const cx<float> *__restrict__ tw, const float *__restrict__ base) {
+                const cx<float> *__restrict__ tw, const float *__restrict__ base, int discard) {
   constexpr int L1 = Four<L>::L1, L2 = Four<L>::L2;
   extern __shared__ __align__(16) unsigned char four_smem[];
   cx<float> *S = reinterpret_cast<cx<float> *>(four_smem);
@@ -291,6 +323,7 @@ k_fft4_inverseB(const cx<float> *__restrict__ inter, OT *__restrict__ y, int n, 
     for (int u = 0; u < U; u++) S[u * kFourT + threadIdx.x] = v[u];
   }
   __syncthreads();
+  if (discard) discard_rows<L1, W>(inter, t2, -1, L2, ncx, cb);
   dft_columns<L1, W, L, +1>(S, tw);
   // row t1 of S holds time step L2 t1 + t2, real columns in order (re, im)
   const float *Sf = reinterpret_cast<const float *>(S);
@@ -323,6 +356,17 @@ k_fft4_inverseB(const cx<float> *__restrict__ inter, OT *__restrict__ y, int n, 
   }
 }
 
+// The line discards assume 128-byte aligned row segments: the intermediate
+// and the spectrum 256-byte aligned and the spectrum row stride a multiple
+// of 16 complex values.  Otherwise the kernels keep every line.
+#ifndef AAO_FOUR_DISCARD
+#define AAO_FOUR_DISCARD 1
+#endif
+inline bool four_discard_ok(const void *inter, const void *spec, int64_t n_pad) {
+  return AAO_FOUR_DISCARD && (reinterpret_cast<uintptr_t>(inter) & 255) == 0 &&
+         (reinterpret_cast<uintptr_t>(spec) & 255) == 0 && (n_pad % 16) == 0;
+}
+
 template <int L>
 cudaError_t four_forward(int64_t n, int64_t n_pad, const double *x, cx<float> *spec,
                          const cx<float> *tw, cudaStream_t s, void *inter) {
@@ -337,7 +381,7 @@ cudaError_t four_forward(int64_t n, int64_t n_pad, const double *x, cx<float> *s
   k_fft4_forward1<L, W><<<dim3((unsigned)(ncx / W), L2), kFourT, sm1, s>>>(x, ip, (int)n, ncx, tw);
   note_launch();
   k_fft4_forward2<L, W><<<dim3((unsigned)(ncx / W), L1 / 2 + 1), kFourT, sm2, s>>>(
-      ip, spec, (int)n, ncx, n_pad, tw);
+      ip, spec, (int)n, ncx, n_pad, tw, four_discard_ok(ip, spec, n_pad) ? 1 : 0);
   note_launch();
   return cudaGetLastError();
 }
@@ -353,11 +397,12 @@ cudaError_t four_inverse(int64_t n, int64_t n_pad, const cx<float> *spec, OT *y,
   cudaError_t e = kernel_setup((const void *)k_fft4_inverseA<L, W>, kFourT, sm2);
   if (e == cudaSuccess) e = kernel_setup((const void *)k_fft4_inverseB<L, W, OT>, kFourT, sm1);
   if (e != cudaSuccess) return e;
+  const int dis = four_discard_ok(ip, spec, n_pad) ? 1 : 0;
   k_fft4_inverseA<L, W><<<dim3((unsigned)(ncx / W), L1 / 2 + 1), kFourT, sm2, s>>>(
-      spec, ip, (int)n, ncx, n_pad, tw);
+      spec, ip, (int)n, ncx, n_pad, tw, dis);
   note_launch();
   k_fft4_inverseB<L, W, OT><<<dim3((unsigned)(ncx / W), L2), kFourT, sm1, s>>>(
-      ip, y, (int)n, ncx, tw, base);
+      ip, y, (int)n, ncx, tw, base, dis);
   note_launch();
   return cudaGetLastError();
 }
