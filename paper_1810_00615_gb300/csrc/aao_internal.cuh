@@ -348,6 +348,7 @@ struct WsLayout {
   size_t red = 0, red_bytes = 0;
   size_t rf32 = 0;        // refined apply: z0 (N floats)
   size_t rf64 = 0;        // refined apply: residual, Neumann right-hand side (2 x N doubles)
+  size_t dots = 0;        // block partials of the matvec with fused dots
   size_t vecs = 0;        // first FP64 vector (V_0 ...)
   size_t vec_bytes = 0;   // bytes per vector (rounded)
   size_t total = 0;
@@ -388,6 +389,17 @@ cudaError_t launch_tridiag(const Ctx &c, void *spec, int prec, int transpose,
 constexpr int64_t kDstMaxL = 4096;   // n + 1 <= kDstMaxL, a power of two
 bool dst_supported(int64_t n);
 cudaError_t launch_dst_solve(const Ctx &c, void *spec, int prec, int transpose, cudaStream_t s);
+// w = A x - sub (or A^T x - sub) with the Arnoldi dots of w in the same pass:
+// out = [v0 . w (when v0 is given),] sub . w, w . w (the layout launch_multidot
+// gives for the vectors (v0,) sub).  dpart: matvec_dot_partials(c) doubles.
+// cudaErrorNotSupported for the literal heat form (FP64 stencil kernel).
+size_t matvec_dot_partials(const Ctx &c);
+cudaError_t launch_matvec_dots(const Ctx &c, const double *x, double *y, int transpose,
+                               cudaStream_t s, const double *sub, const double *v0,
+                               double *dpart, double *out);
+cudaError_t launch_matvec_dots(const Ctx &c, const float *x, double *y, int transpose,
+                               cudaStream_t s, const double *sub, const double *v0,
+                               double *dpart, double *out);
 // y = A x (or A^T x); with `sub`, y = A x - sub (fused, for the shifted Arnoldi).
 cudaError_t launch_matvec(const Ctx &c, const double *x, double *y, int transpose,
                           cudaStream_t s, const double *sub = nullptr);

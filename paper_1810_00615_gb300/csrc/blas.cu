@@ -233,19 +233,67 @@ __device__ __forceinline__ double fx_to_f64(long long S, int unit) {
 #ifndef AAO_MVFX_MINB
 #define AAO_MVFX_MINB 1
 #endif
-template <int NB, bool TR, bool SUB, typename XT, bool CIRC>
+
+// The fused Arnoldi dots of the matvec: each warp sums its ND accumulators,
+// parks them in shared memory, and the last warp of the block to arrive adds
+// the warps' values in warp order and stores the block partial (the result
+// does not depend on the arrival order).  Every warp calls it exactly once,
+// with all 32 lanes.
+template <int ND, int NW>
+__device__ __forceinline__ void dots_commit(double (&acc)[ND], double (*s_dot)[ND], int *s_cnt,
+                                            double *__restrict__ dpart) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < ND; q++) acc[q] = warp_sum(acc[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < ND; q++) s_dot[warp][q] = acc[q];
+    __threadfence_block();
+    if (atomicAdd(s_cnt, 1) == NW - 1) {
+      __threadfence_block();
+      const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll
+      for (int q = 0; q < ND; q++) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < NW; w++) t += reinterpret_cast<volatile double *>(s_dot[w])[q];
+        dpart[b * ND + q] = t;
+      }
+    }
+  }
+}
+
+// DK >= 0 (with SUB): the kernel also forms the Arnoldi dots of its output
+// w = A x - v: (v0 . w if DK = 1), v . w and w . w, as block partials in
+// dpart (ND = DK + 2 values per block, in that order).
+template <int NB, bool TR, bool SUB, typename XT, bool CIRC, int DK = -1>
 __global__ void __launch_bounds__(kMvCols, AAO_MVFX_MINB)
 k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
-            const MvRow *__restrict__ rows, const double *__restrict__ sub) {
+            const MvRow *__restrict__ rows, const double *__restrict__ sub,
+            const double *__restrict__ dv0 = nullptr, double *__restrict__ dpart = nullptr) {
   constexpr int R = kFxRows, IN = R + NB - 1;   // input time steps per tile
   constexpr int kWarps = kMvCols / 32;
   constexpr int G = NB == 4 ? 2 : 0;            // guard bits (sums below 2^63)
+  constexpr int ND = DK >= 0 ? DK + 2 : 1;
+  static_assert(DK < 0 || SUB, "the dots need the subtrahend");
   using F = Fx<XT>;
   __shared__ long long s_halo[kWarps][2][IN];   // converted halo columns, walk order
+  __shared__ double s_dot[kWarps][ND];
+  __shared__ int s_cnt;
+  if constexpr (DK >= 0) {
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();   // before any warp can leave
+  }
+  double dacc[ND];
+#pragma unroll
+  for (int q = 0; q < ND; q++) dacc[q] = 0.0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i = blockIdx.x * kMvCols + threadIdx.x;
   const int iw = i - lane;                      // first column of the warp
-  if (iw >= n) return;                          // whole warp past the end
+  if (iw >= n) {                                // whole warp past the end
+    if constexpr (DK >= 0) dots_commit<ND, kWarps>(dacc, s_dot, &s_cnt, dpart);
+    return;
+  }
   const bool col_ok = i < n;
   // walk step k = 0..IN-1 visits time step t0 + k dir: forward from the
   // oldest lag up, transpose from the newest lead down
@@ -290,6 +338,11 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
     if (col_ok)
       for (int t = c0; t < min(ell, c0 + R); t++)
         y[(int64_t)t * n + i] = __longlong_as_double(0x7ff8000000000000ll);
+    if constexpr (DK >= 0) {
+#pragma unroll
+      for (int q = 0; q < ND; q++) dacc[q] = __longlong_as_double(0x7ff8000000000000ll);
+      dots_commit<ND, kWarps>(dacc, s_dot, &s_cnt, dpart);
+    }
     return;
   }
   const int unit = F::template unit<G>(em);
@@ -307,16 +360,19 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
   // their latency hides behind the integer work of the steps in between
   constexpr int kPre = AAO_MVFX_PRE;
   const double *pv0 = SUB ? sub + (int64_t)t0 * n + ic : nullptr;
+  const double *pd0 = (DK >= 1) ? dv0 + (int64_t)t0 * n + ic : nullptr;
   XT zpre[kPre];
-  double vpre[kPre];
+  double vpre[kPre], dpre[kPre];
 #pragma unroll
   for (int k = 0; k < kPre; k++) {
     const int t = t0 + k * dir;
     zpre[k] = z_ok(t) ? __ldg(zaddr(t, px0 + k * step)) : (XT)0;
     vpre[k] = (SUB && col_ok && t_ok(t) && k >= NB - 1) ? __ldg(pv0 + k * step) : 0.0;
+    dpre[k] = (DK >= 1 && col_ok && t_ok(t) && k >= NB - 1) ? __ldg(pd0 + k * step) : 0.0;
   }
   const XT *pz = px0 + kPre * step;
   const double *pv = SUB ? pv0 + kPre * step : nullptr;
+  const double *pd = (DK >= 1) ? pd0 + kPre * step : nullptr;
   double *py = y + (int64_t)t0 * n + ic;
   long long q1 = 0, q2 = 0, q3 = 0;             // q of the previous steps walked
 #pragma unroll 1
@@ -326,14 +382,16 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
       const int k = kb + u;
       const int t = t0 + k * dir;
       const XT zk = zpre[u];
-      const double vk = vpre[u];
+      const double vk = vpre[u], dk = dpre[u];
       {
         const int tn = t + kPre * dir;
         const bool inb = k + kPre < IN;
         zpre[u] = (inb && z_ok(tn)) ? __ldg(zaddr(tn, pz)) : (XT)0;
         if (SUB) vpre[u] = (inb && col_ok && t_ok(tn)) ? __ldg(pv) : 0.0;
+        if (DK >= 1) dpre[u] = (inb && col_ok && t_ok(tn)) ? __ldg(pd) : 0.0;
         pz += step;
         if (SUB) pv += step;
+        if (DK >= 1) pd += step;
       }
       const long long X = F::template fixed<G>(zk, em);
       long long Xl = __shfl_up_sync(0xffffffffu, X, 1);
@@ -366,13 +424,20 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
         const long long T = s_main + (so_neg ? -prod : prod);
         constexpr bool RANGE = sizeof(XT) == 8;
         const double td = fx_to_f64<RANGE>(T, unit);
-        py[(int64_t)k * step] = SUB ? fma(rw.coef, td, -vk) : rw.coef * td;
+        const double yv = SUB ? fma(rw.coef, td, -vk) : rw.coef * td;
+        py[(int64_t)k * step] = yv;
+        if constexpr (DK >= 0) {
+          if constexpr (DK >= 1) dacc[0] = fma(dk, yv, dacc[0]);
+          dacc[ND - 2] = fma(vk, yv, dacc[ND - 2]);
+          dacc[ND - 1] = fma(yv, yv, dacc[ND - 1]);
+        }
       }
       q3 = q2;
       q2 = q1;
       q1 = q;
     }
   }
+  if constexpr (DK >= 0) dots_commit<ND, kWarps>(dacc, s_dot, &s_cnt, dpart);
 }
 
 template <int NB, bool TR, typename XT, bool CIRC>
@@ -434,6 +499,77 @@ static cudaError_t matvec_dispatch(const Ctx &c, const XT *x, double *y, int tra
   else mv_fx<2, false, XT, CIRC>(c, grid, x, y, sub, s);
   note_launch();
   return cudaGetLastError();
+}
+
+// out[j] = sum_b p[b * nd + j] in a fixed order, one 256-thread CTA per value
+// (the fused matvec leaves one partial per block: thousands of them).
+__global__ void __launch_bounds__(kThreads)
+k_finish_wide(const double *__restrict__ p, int nb, int nd, double *__restrict__ out) {
+  __shared__ double sm[kThreads / 32];
+  const int j = blockIdx.x;
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kThreads) v += p[(size_t)b * nd + j];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; w++) t += sm[w];
+    out[j] = t;
+  }
+}
+
+static dim3 mv_fx_grid(const Ctx &c) {
+  return dim3((unsigned)((c.n + kMvCols - 1) / kMvCols),
+              (unsigned)((c.ell + kFxRows - 1) / kFxRows));
+}
+
+size_t matvec_dot_partials(const Ctx &c) {
+  const dim3 g = mv_fx_grid(c);
+  return (size_t)g.x * g.y * 3;
+}
+
+// w = A x - sub with the Arnoldi dots of w fused in (DK = 1: with v0 too):
+// out = [v0 . w,] sub . w, w . w.
+template <typename XT>
+static cudaError_t matvec_dots_dispatch(const Ctx &c, const XT *x, double *y, int transpose,
+                                        cudaStream_t s, const double *sub, const double *v0,
+                                        double *dpart, double *out) {
+  if (c.equation == AAO_HEAT_LITERAL || !sub) return cudaErrorNotSupported;
+  const dim3 grid = mv_fx_grid(c);
+  const int n = (int)c.n, ell = (int)c.ell;
+  const int nb = c.equation == AAO_WAVE_BD4 ? 4 : (c.equation == AAO_WAVE_BD2 ? 3 : 2);
+  const int key = nb * 4 + (transpose ? 2 : 0) + (v0 ? 1 : 0);
+#define AAO_MVD(NBV, TRV, DKV)                                                           \
+  case NBV * 4 + (TRV ? 2 : 0) + DKV:                                                    \
+    k_matvec_fx<NBV, TRV, true, XT, false, DKV><<<grid, kMvCols, 0, s>>>(               \
+        x, y, n, ell, c.mv_rows, sub, v0, dpart);                                        \
+    break;
+  switch (key) {
+    AAO_MVD(2, false, 0) AAO_MVD(2, false, 1) AAO_MVD(2, true, 0) AAO_MVD(2, true, 1)
+    AAO_MVD(3, false, 0) AAO_MVD(3, false, 1) AAO_MVD(3, true, 0) AAO_MVD(3, true, 1)
+    AAO_MVD(4, false, 0) AAO_MVD(4, false, 1) AAO_MVD(4, true, 0) AAO_MVD(4, true, 1)
+    default: return cudaErrorNotSupported;
+  }
+#undef AAO_MVD
+  note_launch();
+  const int nd = v0 ? 3 : 2;
+  k_finish_wide<<<nd, kThreads, 0, s>>>(dpart, (int)(grid.x * grid.y), nd, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matvec_dots(const Ctx &c, const double *x, double *y, int transpose,
+                               cudaStream_t s, const double *sub, const double *v0,
+                               double *dpart, double *out) {
+  return matvec_dots_dispatch(c, x, y, transpose, s, sub, v0, dpart, out);
+}
+
+cudaError_t launch_matvec_dots(const Ctx &c, const float *x, double *y, int transpose,
+                               cudaStream_t s, const double *sub, const double *v0,
+                               double *dpart, double *out) {
+  return matvec_dots_dispatch(c, x, y, transpose, s, sub, v0, dpart, out);
 }
 
 cudaError_t launch_circ_residual(const Ctx &c, const float *z, double *y, int transpose,

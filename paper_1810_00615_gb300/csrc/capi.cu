@@ -525,7 +525,8 @@ WsLayout ws_layout(const Ctx &c, int restart) {
   L.red_bytes = round_up((size_t)(kPartials + kSmall) * sizeof(double), kAlign);
   L.rf32 = L.red + L.red_bytes;
   L.rf64 = L.rf32 + round_up((size_t)c.N * sizeof(float), kAlign);
-  L.vecs = L.rf64 + 2 * round_up((size_t)c.N * sizeof(double), kAlign);
+  L.dots = L.rf64 + 2 * round_up((size_t)c.N * sizeof(double), kAlign);
+  L.vecs = L.dots + round_up(aao::matvec_dot_partials(c) * sizeof(double), kAlign);
   L.vec_bytes = round_up((size_t)c.N * sizeof(double), kAlign);
   const int nvec = restart > 0 ? (restart + 1) + restart + 2 : 0;
   L.total = L.vecs + (size_t)nvec * L.vec_bytes;
@@ -640,6 +641,7 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
   const size_t vb = (size_t)N * sizeof(double);
   if (overlap(b, x, vb)) return AAO_EINVAL;
   double *red = reinterpret_cast<double *>(c.ws + L.red);
+  double *dpart = reinterpret_cast<double *>(c.ws + L.dots);
   double *small = red + kPartials;
   double *d_h1 = small, *d_h2 = small + 160, *d_nr = small + 320, *d_y = small + 480;
   double *hs = c.host_small;   // pinned mirror of the same offsets
@@ -745,17 +747,28 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
         AAO_CK(c, neumann<double>(c, precond, V[(size_t)j], Z[(size_t)j], tr, s));
       }
       double *w = V[(size_t)j + 1];
-      // w~ = A z_j - V_j (unscaled; the true vector is sc[j] times it)
-      AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] {
-        return zf ? aao::launch_matvec(c, Zf[(size_t)j], w, tr, s, V[(size_t)j])
-                  : aao::launch_matvec(c, Z[(size_t)j], w, tr, s, V[(size_t)j]);
-      }));
       const int nv = j + 1;
+      // w~ = A z_j - V_j (unscaled; the true vector is sc[j] times it), then
+      // pass 1: d = V^T w~ and ||w~||^2 -- fused into the matvec for the
+      // first two steps (their dot vectors are the subtrahend V_j and V_0);
+      // pass 2: w~ -= sum sc_i^2 d_i V_i and its norm
+      const bool fused = nv <= 2 && c.equation != AAO_HEAT_LITERAL;
+      if (fused) {
+        const double *v0 = nv == 2 ? V[0] : nullptr;
+        AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] {
+          return zf ? aao::launch_matvec_dots(c, Zf[(size_t)j], w, tr, s, V[(size_t)j], v0, dpart, d_h1)
+                    : aao::launch_matvec_dots(c, Z[(size_t)j], w, tr, s, V[(size_t)j], v0, dpart, d_h1);
+        }));
+      } else {
+        AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] {
+          return zf ? aao::launch_matvec(c, Zf[(size_t)j], w, tr, s, V[(size_t)j])
+                    : aao::launch_matvec(c, Z[(size_t)j], w, tr, s, V[(size_t)j]);
+        }));
+        AAO_CK(c, run(c, AAO_K_DOTS, s, [&] {
+          return aao::launch_multidot(V.data(), nv, w, N, true, red, d_h1, s);
+        }));
+      }
       for (int i = 0; i < nv; i++) sc2[(size_t)i] = sc[(size_t)i] * sc[(size_t)i];
-      // pass 1: d = V^T w~ and ||w~||^2;  pass 2: w~ -= sum sc_i^2 d_i V_i and its norm
-      AAO_CK(c, run(c, AAO_K_DOTS, s, [&] {
-        return aao::launch_multidot(V.data(), nv, w, N, true, red, d_h1, s);
-      }));
       AAO_CK(c, run(c, AAO_K_UPDATE, s, [&] {
         return aao::launch_update_dots(V.data(), nv, d_h1, w, N, false, red, d_nr, s, sc2.data());
       }));
