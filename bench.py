@@ -612,9 +612,9 @@ def run_gpu(args):
                      for k, v in prof.items() if v[1]}
     # The dominant kernel is the one with the largest total time in the ncu
     # launch list of the timed region (profiles/launches_bench_timed_region_*):
-    # the fused fixed-point matvec.  (The profiling classes group the two
-    # kernels of each FFT direction, so a class total is not one kernel.)
-    dom = "matvec"
+    # the fixed-point circulant residual of the refined apply.  (The profiling
+    # classes group several kernels, so a class total is not one kernel.)
+    dom = "refine"
     sm_mhz = clk.get("sm_mhz") or 2070.0
 
     if dom in per_kernel:
@@ -622,35 +622,31 @@ def run_gpu(args):
         roofline = {"bound": "hbm", "kernel": dom, "achieved": pk["GB_s"], "peak": hbm_peak,
                     "unit": "GB/s", "frac": pk["frac"], "traffic": _traffic(dom),
                     "peak_kind": peak_kind}
-    elif dom == "matvec":
-        # The solve's matvecs are the fixed-point product w = A z - v (Arnoldi,
-        # z FP64 with the refined preconditioner, FP32 with the plain one) and
-        # the residual A x - b (x FP64): one kernel.  Integer-ALU bound: the
+    elif dom == "refine":
+        # The largest single kernel of the timed region (launch list in
+        # profiles/): the fixed-point circulant residual r = P z0 - x of the
+        # refined preconditioner, twice per solve.  Integer-ALU bound: the
         # GB300 ALU pipe issues 64 lanes per clock per SM; achieved = ALU-pipe
         # instructions per launch (ncu, committed summary) / event time here.
-        f32_basis = HEADLINE_PREC == "fp32"
-        z = xs[0].float() if f32_basis else xs[0]
+        z = xs[0].float()
         ts = []
         for k in range(23):
             flush.fill_(float(k))
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a0.record(stream)
-            if f32_basis:
-                solver.matvec_f32(z, sub=xs[1], out=ys[0])
-            else:
-                solver.matvec(z, sub=xs[1], out=ys[0])
+            solver.circulant_residual_f32(z, xs[1], out=ys[0])
             a1.record(stream)
             torch.cuda.synchronize()
             if k >= 3:
                 ts.append(a0.elapsed_time(a1) * 1e-3)
         mv_s = float(np.median(ts))
-        key = "matvec_f32" if f32_basis else "matvec_f64"
+        key = "circ_residual"
         alu = _profile_value("alu_inst_per_launch", key)
         alu_peak = 152 * 64 * sm_mhz * 1e6 / 1e9                 # Gop/s
-        mv_bytes = Nel * ((4 if f32_basis else 8) + 8 + 8)        # z, v, w
+        mv_bytes = Nel * (4 + 8 + 8)                              # z (FP32), x, r
         achieved = alu / mv_s / 1e9 if alu else None
         roofline = {"bound": "alu",
-                    "kernel": f"{key}: w = A z - v, fixed point",
+                    "kernel": "circ_residual: r = P z0 - x, fixed point (refined apply)",
                     "achieved": round(achieved, 1) if achieved else None,
                     "peak": round(alu_peak, 1), "unit": "Gop/s",
                     "frac": round(achieved / alu_peak, 4) if achieved else None,

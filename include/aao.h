@@ -210,6 +210,17 @@ int aao_matvec_sub(aao_ctx *ctx, const double *x, const double *sub, double *y, 
 int aao_matvec_f32(aao_ctx *ctx, const float *x, const double *sub, double *y, int transpose,
                    void *stream);
 
+/* r = P z - x (or P^T z - x) for an FP32 z, in FP64 (Section 2, P the block
+ * circulant of Section 3 with the constant step): the residual of the refined
+ * FP32 preconditioner apply (AAO_PREC_FP32_REFINED), which corrects
+ * z = P32^{-1} x by P32^{-1} r.  Evaluated like aao_matvec_f32 (exact
+ * fixed-point stencil sums per 32-column, 32-step tile, time wrapped around,
+ * one rounding) so that r keeps its relative accuracy however much P z and x
+ * cancel; the literal heat form widens z and runs the FP64 stencil.
+ * z: device, N floats; x, r: device, N doubles; r overlaps neither. */
+int aao_circulant_residual_f32(aao_ctx *ctx, const float *z, const double *x, double *r,
+                               int transpose, void *stream);
+
 /* Right-hand side from initial data (Section 2): heat b = [M u0; 0; ...];
  * BD2 b = [A0 (u0 + tau v0); -M u0; 0; ...] (v0 may be NULL = at rest, which
  * is the paper's b_BD2); BD4 b = [B (u0 + tau v0); -M u0; M u0; 0; ...]

@@ -182,6 +182,18 @@ class AllAtOnce:
               "aao_matvec_f32", self._ctx)
         return y
 
+    def circulant_residual_f32(self, z, x, transpose=False, out=None, stream=None):
+        """r = P z - x (or P^T z - x) for an FP32 z, in FP64: the residual of
+        the refined FP32 preconditioner apply."""
+        z = _dev_f64(z, self.N, "z", torch.float32)
+        x = _dev_f64(x, self.N, "x")
+        r = self._out(out)
+        check(self.lib.aao_circulant_residual_f32(self._ctx, z.data_ptr(), x.data_ptr(),
+                                                  r.data_ptr(), int(bool(transpose)),
+                                                  _stream(stream)),
+              "aao_circulant_residual_f32", self._ctx)
+        return r
+
     def build_rhs(self, u0, v0=None, out=None, stream=None):
         u0 = _dev_f64(u0, self.n, "u0")
         vp = None

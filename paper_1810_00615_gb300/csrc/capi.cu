@@ -1099,6 +1099,19 @@ int aao_matvec_f32(aao_ctx *ctx, const float *x, const double *sub, double *y, i
   return AAO_OK;
 }
 
+int aao_circulant_residual_f32(aao_ctx *ctx, const float *z, const double *x, double *r,
+                               int transpose, void *stream) {
+  if (!ctx || !z || !x || !r) return AAO_EINVAL;
+  Ctx &c = ctx->c;
+  const size_t vb = (size_t)c.N * sizeof(double);
+  if (overlap2(z, (size_t)c.N * sizeof(float), r, vb) || overlap(x, r, vb)) return AAO_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  AAO_CK(c, run(c, AAO_K_REFINE, s, [&] {
+    return aao::launch_circ_residual(c, z, r, transpose ? 1 : 0, s, x);
+  }));
+  return AAO_OK;
+}
+
 int aao_build_rhs(aao_ctx *ctx, const double *u0, const double *v0, double *b, void *stream) {
   if (!ctx || !u0 || !b) return AAO_EINVAL;
   Ctx &c = ctx->c;

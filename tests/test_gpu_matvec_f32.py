@@ -196,3 +196,55 @@ def test_matvec_f32_full_size():
         got = to_host(a.matvec_f32(Xd, transpose=tr))
         want = system.matvec_T(S, X) if tr else system.matvec(S, X)
         assert rel_max(got, want) <= 1e-13
+
+
+def _exact_circulant(S, Z, X, transpose, absolute=False):
+    """P z - x with the oracle's FP64 blocks, summed in long double (P the
+    block circulant: constant-step A0, lags wrapped around in time); with
+    absolute, |P| |z| (the size of the terms) instead."""
+    from oracle import system as osys
+    Zl = np.abs(Z).astype(np.longdouble) if absolute else Z.astype(np.longdouble)
+    A0 = osys.constant_A0(S).tocsr()
+
+    def apply(Mat, v):
+        out = np.zeros(Mat.shape[0], dtype=np.longdouble)
+        for r in range(Mat.shape[0]):
+            lo, hi = Mat.indptr[r], Mat.indptr[r + 1]
+            d = Mat.data[lo:hi].astype(np.longdouble)
+            out[r] = np.sum((np.abs(d) if absolute else d) * v[Mat.indices[lo:hi]])
+        return out
+
+    Y = np.zeros_like(Zl)
+    for t in range(S.ell):
+        y = apply(A0, Zl[t])
+        for j, Aj in enumerate(S.lower, start=1):
+            src = (t + j) % S.ell if transpose else (t - j) % S.ell
+            y = y + apply(Aj.tocsr(), Zl[src])
+        Y[t] = y if absolute else y - X[t].astype(np.longdouble)
+    return Y
+
+
+@pytest.mark.parametrize("kind", ["heat", "wave_bd2", "wave_bd4", "heat_literal"])
+@pytest.mark.parametrize("transpose", [False, True])
+@pytest.mark.parametrize("n,ell", [(1, 1), (5, 3), (70, 64), (33, 2)])
+def test_circulant_residual_f32(kind, transpose, n, ell):
+    """aao_circulant_residual_f32: r = P z - x for an FP32 z.  With z the FP32
+    rounding of P^{-1} x, P z and x cancel to ~1e-7 of their size; the
+    fixed-point evaluation keeps r to a few FP64 roundings of the terms
+    (the literal form's FP64 stencil to a few hundred)."""
+    torch = need_gpu()
+    from oracle import precond
+    from paper_1810_00615_gb300 import AllAtOnce
+    S = oracle_system(kind, n, ell)
+    a = AllAtOnce(n, ell, 1.0 / ell, equation=kind, restart=1, precision="fp32")
+    X = rand_block(n, ell, 90 + n)
+    Z = precond.circulant_inverse(S, X, transpose=transpose).astype(np.float32)
+    got = to_host(a.circulant_residual_f32(_f32_dev(torch, Z), torch.from_numpy(X).cuda(),
+                                           transpose=transpose)).astype(np.longdouble)
+    exact = _exact_circulant(S, Z.astype(np.float64), X, transpose)
+    terms = _exact_circulant(S, Z.astype(np.float64), X, transpose, absolute=True)
+    scale = float(np.max(terms)) + float(np.max(np.abs(X)))
+    tol = (16 if kind == "heat_literal" else 4) * EPS * scale
+    assert float(np.max(np.abs(got - exact))) <= tol
+    # the residual is the FP32 rounding error of z, far below the terms
+    assert float(np.max(np.abs(exact))) <= 1e-3 * scale
