@@ -711,10 +711,21 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
       v0_sign = 1.0;
       x0_zero = false;
     } else {
-      // V_0 = A x - b = -r (one fused pass); v_0 = -V_0 / beta
+      // V_0 = A x - b = -r (one fused pass, its squared norm formed in the
+      // same kernel where the fixed-point matvec serves); v_0 = -V_0 / beta
       V[0] = v0_slot;
-      AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] { return aao::launch_matvec(c, x, V[0], tr, s, b); }));
-      AAO_CK(c, norm2(V[0]));
+      if (c.equation != AAO_HEAT_LITERAL) {
+        // out = [b . V_0, V_0 . V_0] at d_nr
+        AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] {
+          return aao::launch_matvec_dots(c, x, V[0], tr, s, b, nullptr, dpart, d_nr);
+        }));
+        AAO_CK(c, fetch(d_nr, 2));
+        AAO_CK(c, cudaStreamSynchronize(s));
+        hs[320] = hs[321];
+      } else {
+        AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] { return aao::launch_matvec(c, x, V[0], tr, s, b); }));
+        AAO_CK(c, norm2(V[0]));
+      }
       beta = std::sqrt(hs[320]);
       v0_sign = -1.0;
     }
