@@ -303,6 +303,8 @@ struct Ctx {
   double *sigk = nullptr;         // per-step Neumann coefficient (tau_t - tau) kappa / h
   float *sigk32 = nullptr;
   double *host_small = nullptr;   // pinned host scratch for small results (1024 doubles)
+  cudaStream_t copy_stream = nullptr;   // host solve: copy of x overlapping the residual
+  cudaEvent_t ev_x = nullptr, ev_copy = nullptr;
 
   // caller workspace
   char *ws = nullptr;

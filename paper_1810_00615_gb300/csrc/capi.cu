@@ -632,8 +632,11 @@ cudaError_t neumann(Ctx &c, int terms, const double *x, YT *y, int tr, cudaStrea
 // Lazy normalisation: basis vectors are stored unscaled, v_j = sc[j] * V_j,
 // and the scales are folded into the coefficients the kernels receive (the
 // preconditioner and A are linear), which saves a full pass per step.
+// x_host (host solve only): x is copied there after every update on a second
+// stream, so the copy of the final iterate overlaps the true-residual check
+// that confirms it.
 int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, int maxit,
-               int precond, aao_solve_info *info, cudaStream_t s) {
+               int precond, aao_solve_info *info, cudaStream_t s, double *x_host = nullptr) {
   if (m < 1 || m > kMaxRestart || !(rtol > 0.0) || maxit < 0 || precond < 0) return AAO_EINVAL;
   if (check_ws(c, m) != AAO_OK) return AAO_EINVAL;
   const aao::WsLayout L = aao::ws_layout(c, m);
@@ -691,9 +694,17 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
   if (!std::isfinite(bnorm)) return AAO_ENUMERIC;
   if (bnorm == 0.0) {
     AAO_CK(c, cudaMemsetAsync(x, 0, vb, s));
+    if (x_host) AAO_CK(c, cudaMemcpyAsync(x_host, x, vb, cudaMemcpyDeviceToHost, s));
     AAO_CK(c, cudaStreamSynchronize(s));
     if (info) { info->relres_true = 0.0; info->relres_est = 0.0; }
     return AAO_OK;
+  }
+  bool copy_pending = false;   // a copy of x to x_host is in flight
+  bool host_current = false;   // x_host holds (or will hold) the current x
+  if (x_host && !c.copy_stream) {
+    AAO_CK(c, cudaStreamCreateWithFlags(&c.copy_stream, cudaStreamNonBlocking));
+    AAO_CK(c, cudaEventCreateWithFlags(&c.ev_x, cudaEventDisableTiming));
+    AAO_CK(c, cudaEventCreateWithFlags(&c.ev_copy, cudaEventDisableTiming));
   }
   std::vector<double> H((size_t)(m + 1) * m), cs((size_t)m), sn((size_t)m), g((size_t)m + 1);
   std::vector<double> sc((size_t)m + 1), sc2((size_t)m + 1);
@@ -876,14 +887,29 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
     }
     for (int i = 0; i < jd; i++) hs[480 + i] = y[(size_t)i] * sc[(size_t)i];   // z_i = sc_i Z_i
     AAO_CK(c, cudaMemcpyAsync(d_y, hs + 480, jd * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (copy_pending) AAO_CK(c, cudaStreamWaitEvent(s, c.ev_copy, 0));   // x is read by it
     AAO_CK(c, run(c, AAO_K_COMBINE, s, [&] {
       return zf ? aao::launch_combine(Zf.data(), jd, d_y, x, N, s, x_unset)
                 : aao::launch_combine(Z.data(), jd, d_y, x, N, s, x_unset);
     }));
     if (jd > 0) x_unset = false;
+    if (x_host && jd > 0) {
+      AAO_CK(c, cudaEventRecord(c.ev_x, s));
+      AAO_CK(c, cudaStreamWaitEvent(c.copy_stream, c.ev_x, 0));
+      AAO_CK(c, cudaMemcpyAsync(x_host, x, vb, cudaMemcpyDeviceToHost, c.copy_stream));
+      AAO_CK(c, cudaEventRecord(c.ev_copy, c.copy_stream));
+      copy_pending = host_current = true;
+    }
     restarts++;
   }
-  if (x_unset) AAO_CK(c, cudaMemsetAsync(x, 0, vb, s));   // stopped before the first update
+  if (x_unset) {                                          // stopped before the first update
+    if (copy_pending) AAO_CK(c, cudaStreamWaitEvent(s, c.ev_copy, 0));
+    AAO_CK(c, cudaMemsetAsync(x, 0, vb, s));
+    host_current = false;
+  }
+  if (x_host && !host_current)
+    AAO_CK(c, cudaMemcpyAsync(x_host, x, vb, cudaMemcpyDeviceToHost, s));
+  if (copy_pending) AAO_CK(c, cudaStreamSynchronize(c.copy_stream));
   AAO_CK(c, cudaStreamSynchronize(s));
   AAO_CK(c, collect(c));
   if (info) {
@@ -989,6 +1015,9 @@ void aao_destroy(aao_ctx *ctx) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c.host_small) cudaFreeHost(c.host_small);
+  if (c.ev_x) cudaEventDestroy(c.ev_x);
+  if (c.ev_copy) cudaEventDestroy(c.ev_copy);
+  if (c.copy_stream) cudaStreamDestroy(c.copy_stream);
   for (auto &p : c.pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -1210,11 +1239,10 @@ int aao_solve_host(aao_ctx *ctx, const double *u0_host, const double *v0_host, d
   AAO_CK(c, run(c, AAO_K_OTHER, s, [&] { return aao::launch_rhs(c, dx, v0_host ? dx + c.n : nullptr, db, s); }));
   const int guess = c.guess;
   c.guess = AAO_GUESS_ZERO;
-  const int st = solve_core(c, 0, db, dx, restart, rtol, maxit, precond, info, s);
+  // the solution reaches U_host from inside the solve, its copy overlapping
+  // the final true-residual check
+  const int st = solve_core(c, 0, db, dx, restart, rtol, maxit, precond, info, s, U_host);
   c.guess = guess;
-  if (st < 0) return st;
-  AAO_CK(c, cudaMemcpyAsync(U_host, dx, (size_t)c.N * sizeof(double), cudaMemcpyDeviceToHost, s));
-  AAO_CK(c, cudaStreamSynchronize(s));
   return st;
 }
 

@@ -159,6 +159,28 @@ def test_solve_host_matches_device_solve():
     assert torch.equal(U, x.cpu())
 
 
+@pytest.mark.parametrize("case", ["zero_u0", "maxit0", "many_cycles"])
+def test_solve_host_copy_paths(case):
+    """The host solve copies x to the host after every update, overlapping
+    the next true-residual check: a zero right-hand side, a solve stopped
+    before its first update and a many-cycle solve (restart 2, each copy
+    waited for before the next update) all return the device solve's x."""
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    n, ell = 63, 64
+    kind = "wave_bd2" if case == "many_cycles" else "heat"
+    a = AllAtOnce(n, ell, 1.0 / ell, equation=kind, restart=2)
+    u0 = np.zeros(n) if case == "zero_u0" else syn.heat_initial(n)
+    maxit = 0 if case == "maxit0" else 300
+    x, info_d = a.solve(a.build_rhs(to_dev(torch, u0)), restart=2, rtol=1e-10, maxit=maxit)
+    U = torch.full((ell, n), float("nan"), dtype=torch.float64).pin_memory()
+    U, info = a.solve_host(torch.from_numpy(u0), out=U, restart=2, rtol=1e-10, maxit=maxit)
+    assert torch.equal(U, x.cpu())
+    assert info["iters"] == info_d["iters"]
+    if case == "many_cycles":
+        assert info["iters"] > 4
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_adjoint_n16383_ell1024(prec):
     """Adjoint workload: loss 1/2 ||U - U_obs||^2, U_obs from a seeded
