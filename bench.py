@@ -612,9 +612,10 @@ def run_gpu(args):
                      for k, v in prof.items() if v[1]}
     # The dominant kernel is the one with the largest total time in the ncu
     # launch list of the timed region (profiles/launches_bench_timed_region_*):
-    # the fixed-point circulant residual of the refined apply.  (The profiling
-    # classes group several kernels, so a class total is not one kernel.)
-    dom = "refine"
+    # the fixed-point matvec with fused dots (DK = 0), ahead of the circulant
+    # residual of the refined apply.  (The profiling classes group several
+    # kernels, so a class total is not one kernel.)
+    dom = "matvec_dots"
     sm_mhz = clk.get("sm_mhz") or 2070.0
 
     if dom in per_kernel:
@@ -622,6 +623,44 @@ def run_gpu(args):
         roofline = {"bound": "hbm", "kernel": dom, "achieved": pk["GB_s"], "peak": hbm_peak,
                     "unit": "GB/s", "frac": pk["frac"], "traffic": _traffic(dom),
                     "peak_kind": peak_kind}
+    elif dom == "matvec_dots":
+        # The largest single kernel of the timed region (launch list in
+        # profiles/): the fixed-point matvec with its dots fused,
+        # k_matvec_fx<..., DK = 0> (Arnoldi step 0, w = A z - b, and the
+        # true residual r = A x - b with ||r||^2).  Timed here through
+        # aao_residual with the library's per-class CUDA events (kernel plus
+        # the 5 us fixed-order finish of its block partials).  Integer-ALU
+        # bound: 64 ALU lanes per clock per SM; achieved = ALU-pipe
+        # instructions per launch (ncu, committed summary) / event time.
+        solver.profile_read(reset=True)
+        solver.profile(True)
+        nres = 20
+        for k in range(nres + 3):
+            flush.fill_(float(k))
+            if k == 3:
+                solver.profile_read(reset=True)
+            solver.residual(xs[0], xs[1], out=ys[0])
+        torch.cuda.synchronize()
+        rp = solver.profile_read(reset=True)
+        solver.profile(False)
+        mv_s = rp["matvec"][0] * 1e-3 / nres
+        key = "matvec_dots0_double"
+        alu = _profile_value("alu_inst_per_launch", key)
+        alu_peak = 152 * 64 * sm_mhz * 1e6 / 1e9                 # Gop/s
+        mv_bytes = Nel * (8 + 8 + 8)                              # x, b, r
+        achieved = alu / mv_s / 1e9 if alu else None
+        roofline = {"bound": "alu",
+                    "kernel": "matvec_dots0: r = A x - b with r.r fused, fixed point",
+                    "achieved": round(achieved, 1) if achieved else None,
+                    "peak": round(alu_peak, 1), "unit": "Gop/s",
+                    "frac": round(achieved / alu_peak, 4) if achieved else None,
+                    "traffic": _traffic(key), "us": round(mv_s * 1e6, 1),
+                    "algorithmic_bytes": mv_bytes,
+                    "hbm_GB_s": round(mv_bytes / mv_s / 1e9, 1),
+                    "hbm_frac": round(mv_bytes / mv_s / 1e9 / hbm_peak, 3),
+                    "note": "integer ALU pipe bound; peak = 152 SMs x 64 ALU lanes/clk x "
+                            "sampled SM clock; achieved = ncu ALU-pipe instructions per "
+                            "launch / event time (kernel + partials finish)"}
     elif dom == "refine":
         # The largest single kernel of the timed region (launch list in
         # profiles/): the fixed-point circulant residual r = P z0 - x of the

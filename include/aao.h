@@ -210,6 +210,17 @@ int aao_matvec_sub(aao_ctx *ctx, const double *x, const double *sub, double *y, 
 int aao_matvec_f32(aao_ctx *ctx, const float *x, const double *sub, double *y, int transpose,
                    void *stream);
 
+/* r = A x - b (or A^T x - b) and its squared norm, in one pass: the true
+ * residual the solves check at every restart (Section 2).  The matvec is
+ * the fixed-point stencil of aao_matvec; each thread accumulates r . r (and
+ * b . r) and the block and grid sums are added in a fixed order, so the
+ * norm is deterministic.  The literal heat form runs the FP64 stencil and a
+ * separate norm pass.  x, b, r: device, N doubles, r overlaps neither;
+ * norm2: host, 1 double, written before return (synchronises `stream`).
+ * Needs the workspace. */
+int aao_residual(aao_ctx *ctx, const double *x, const double *b, double *r, int transpose,
+                 double *norm2, void *stream);
+
 /* r = P z - x (or P^T z - x) for an FP32 z, in FP64 (Section 2, P the block
  * circulant of Section 3 with the constant step): the residual of the refined
  * FP32 preconditioner apply (AAO_PREC_FP32_REFINED), which corrects

@@ -182,6 +182,18 @@ class AllAtOnce:
               "aao_matvec_f32", self._ctx)
         return y
 
+    def residual(self, x, b, transpose=False, out=None, stream=None):
+        """r = A x - b (or A^T x - b) and ||r||^2 in one pass (synchronises)."""
+        self.ensure_workspace(self._restart)
+        x = _dev_f64(x, self.N, "x")
+        b = _dev_f64(b, self.N, "b")
+        r = self._out(out)
+        nrm = C.c_double()
+        check(self.lib.aao_residual(self._ctx, x.data_ptr(), b.data_ptr(), r.data_ptr(),
+                                    int(bool(transpose)), C.byref(nrm), _stream(stream)),
+              "aao_residual", self._ctx)
+        return r, float(nrm.value)
+
     def circulant_residual_f32(self, z, x, transpose=False, out=None, stream=None):
         """r = P z - x (or P^T z - x) for an FP32 z, in FP64: the residual of
         the refined FP32 preconditioner apply."""

@@ -1139,6 +1139,38 @@ int aao_matvec_f32(aao_ctx *ctx, const float *x, const double *sub, double *y, i
   return AAO_OK;
 }
 
+int aao_residual(aao_ctx *ctx, const double *x, const double *b, double *r, int transpose,
+                 double *norm2, void *stream) {
+  if (!ctx || !x || !b || !r || !norm2) return AAO_EINVAL;
+  Ctx &c = ctx->c;
+  const size_t vb = (size_t)c.N * sizeof(double);
+  if (overlap(x, r, vb) || overlap(b, r, vb)) return AAO_EINVAL;
+  if (check_ws(c, 0) != AAO_OK) return AAO_EINVAL;
+  const aao::WsLayout L = aao::ws_layout(c, 0);
+  double *red = reinterpret_cast<double *>(c.ws + L.red);
+  double *dpart = reinterpret_cast<double *>(c.ws + L.dots);
+  double *out = red + kPartials + 970;   // 2 doubles of the small-result area
+  cudaStream_t s = as_stream(stream);
+  const int tr = transpose ? 1 : 0;
+  if (c.equation != AAO_HEAT_LITERAL) {
+    AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] {
+      return aao::launch_matvec_dots(c, x, r, tr, s, b, nullptr, dpart, out);
+    }));
+    AAO_CK(c, cudaMemcpyAsync(c.host_small + 970, out + 1, sizeof(double),
+                              cudaMemcpyDeviceToHost, s));
+  } else {
+    AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] { return aao::launch_matvec(c, x, r, tr, s, b); }));
+    AAO_CK(c, run(c, AAO_K_DOTS, s, [&] {
+      return aao::launch_multidot(nullptr, 0, r, c.N, true, red, out, s);
+    }));
+    AAO_CK(c, cudaMemcpyAsync(c.host_small + 970, out, sizeof(double), cudaMemcpyDeviceToHost,
+                              s));
+  }
+  AAO_CK(c, cudaStreamSynchronize(s));
+  *norm2 = c.host_small[970];
+  return AAO_OK;
+}
+
 int aao_circulant_residual_f32(aao_ctx *ctx, const float *z, const double *x, double *r,
                                int transpose, void *stream) {
   if (!ctx || !z || !x || !r) return AAO_EINVAL;

@@ -76,3 +76,25 @@ def test_rhs_matches_oracle(kind, with_v0, ell):
         want = system.rhs_heat(S, u0)
     got = to_host(a.build_rhs(to_dev(torch, u0), to_dev(torch, v0) if with_v0 else None))
     assert rel_max(got, want) <= 1e-13
+
+
+@pytest.mark.parametrize("kind", ["heat", "wave_bd2", "wave_bd4", "heat_literal", "steps"])
+@pytest.mark.parametrize("transpose", [False, True])
+@pytest.mark.parametrize("n,ell", [(1, 1), (33, 16), (255, 64), (70, 3)])
+def test_residual_and_fused_norm(kind, transpose, n, ell):
+    """aao_residual: r = A x - b and ||r||^2 from the same pass, against the
+    oracle's A x - b and numpy's norm of it."""
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    taus = syn.time_steps(ell, 0.6, syn.rng(ell)) if kind == "steps" else None
+    S = oracle_system("heat" if kind == "steps" else kind, n, ell, kappa=1.0, taus=taus)
+    a = AllAtOnce(n, ell, 1.0 / ell, equation="heat" if kind == "steps" else kind, restart=1)
+    if taus is not None:
+        a.set_steps(taus)
+    X = rand_block(n, ell, 5 + n)
+    B = rand_block(n, ell, 6 + n)
+    want = (system.matvec_T(S, X) if transpose else system.matvec(S, X)) - B
+    r, nrm2 = a.residual(to_dev(torch, X), to_dev(torch, B), transpose=transpose)
+    assert rel_max(to_host(r), want) <= 1e-13
+    ref = float(np.sum(want * want))
+    assert abs(nrm2 - ref) <= 1e-12 * ref
