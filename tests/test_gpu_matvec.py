@@ -19,8 +19,12 @@ pytestmark = pytest.mark.gpu
 def test_matvec_matches_oracle(n, ell, kind, transpose):
     torch = need_gpu()
     from paper_1810_00615_gb300 import AllAtOnce
-    if (ell & (ell - 1)) != 0:
-        pytest.skip("contexts need a power-of-two ell")
+    m = ell
+    for p in (2, 3, 5):
+        while m % p == 0:
+            m //= p
+    if m != 1:
+        pytest.skip("contexts need ell = 2^a 3^b 5^c")
     taus = syn.time_steps(ell, 0.6, syn.rng(ell)) if kind == "steps" else None
     S = oracle_system("heat" if kind == "steps" else kind, n, ell, kappa=1.0, taus=taus)
     X = rand_block(n, ell, 3 + n)
