@@ -119,25 +119,35 @@ k_fft4_forward1(const double *__restrict__ x, cx<float> *__restrict__ inter, int
   // aligned), up to 16 in flight per thread, converted to FP32 on the way in
   constexpr int NE = L1 * 2 * W / kFourT;                   // loads per thread
   constexpr int B = NE < 16 ? NE : 16;
+  constexpr int RPU = kFourT / (2 * W);                     // tile rows per load step
+  static_assert(kFourT % (2 * W) == 0, "whole rows per load step");
+  // element (u, thread) of the L1 x 2W tile: row t1 = RPU u + thread / 2W,
+  // column q = thread % 2W, the same for every u
+  const int q = threadIdx.x % (2 * W), i = i0 + q;
+  const bool in = i < n;
+  const double *px = x + (size_t)(L2 * (threadIdx.x / (2 * W)) + t2) * n + i;
+  const size_t ustride = (size_t)RPU * L2 * n;
 #pragma unroll
   for (int b0 = 0; b0 < NE; b0 += B) {
     double d[B];
 #pragma unroll
-    for (int u = 0; u < B; u++) {
-      const int e = (b0 + u) * kFourT + threadIdx.x;        // element of the L1 x 2W tile
-      const int t1 = e / (2 * W), q = e - t1 * 2 * W, i = i0 + q;
-      d[u] = (i < n) ? ld_hint(&x[(size_t)(L2 * t1 + t2) * n + i], pol_stream) : 0.0;
-    }
+    for (int u = 0; u < B; u++) d[u] = in ? ld_hint(px + (b0 + u) * ustride, pol_stream) : 0.0;
 #pragma unroll
     for (int u = 0; u < B; u++) Sf[(b0 + u) * kFourT + threadIdx.x] = to_f32(d[u]);
   }
   __syncthreads();
   dft_columns<L1, W, L, -1>(S, tw);
-  // row k1 = DFT output; times w^{t2 k1}
-  for (int e = threadIdx.x; e < L1 * W; e += kFourT) {
-    const int k1 = e / W, c = e - k1 * W;
-    const cx<float> v = twiddle<float, -1>(S[e], tw[t2 * k1]);
-    st_hint(inter + ((size_t)k1 * L2 + t2) * ncx + W * blockIdx.x + c, v, pol_keep);
+  // row k1 = DFT output; times w^{t2 k1}.  Element (h, thread): k1 =
+  // KPH h + thread / W, c = thread % W.
+  constexpr int KPH = kFourT / W;
+  cx<float> *pi = inter + ((size_t)(threadIdx.x / W) * L2 + t2) * ncx + W * blockIdx.x +
+                  threadIdx.x % W;
+  const size_t hstride = (size_t)KPH * L2 * ncx;
+#pragma unroll
+  for (int h = 0; h < L1 * W / kFourT; h++) {
+    const int k1 = KPH * h + threadIdx.x / W;
+    const cx<float> v = twiddle<float, -1>(S[h * kFourT + threadIdx.x], tw[t2 * k1]);
+    st_hint(pi + h * hstride, v, pol_keep);
   }
 }
 
@@ -145,13 +155,13 @@ k_fft4_forward1(const double *__restrict__ x, cx<float> *__restrict__ inter, int
 template <int L2, int W>
 __device__ __forceinline__ void load_rows(const cx<float> *__restrict__ inter, int k1, int ncx,
                                           int cb, cx<float> *S, unsigned long long pol) {
-  constexpr int U = L2 * W / kFourT;
+  constexpr int U = L2 * W / kFourT, RPU = kFourT / W;
+  // element (u, thread): row r = RPU u + thread / W, column thread % W
+  const cx<float> *pr = inter + ((size_t)k1 * L2 + threadIdx.x / W) * ncx + cb + threadIdx.x % W;
+  const size_t ustride = (size_t)RPU * ncx;
   cx<float> v[U];
 #pragma unroll
-  for (int u = 0; u < U; u++) {
-    const int e = u * kFourT + threadIdx.x, r = e / W, c = e - r * W;
-    v[u] = ld_hintc(inter + ((size_t)k1 * L2 + r) * ncx + cb + c, pol);
-  }
+  for (int u = 0; u < U; u++) v[u] = ld_hintc(pr + u * ustride, pol);
 #pragma unroll
   for (int u = 0; u < U; u++) S[u * kFourT + threadIdx.x] = v[u];
 }
@@ -312,13 +322,14 @@ k_fft4_inverseB(const cx<float> *__restrict__ inter, OT *__restrict__ y, int n, 
   const unsigned long long pol_done = l2_evict_first();
   // rows k1 = 0..L1-1 of this t2 (stride L2 rows in the intermediate)
   {
-    constexpr int U = L1 * W / kFourT;
+    constexpr int U = L1 * W / kFourT, RPU = kFourT / W;
+    // element (u, thread): k1 = RPU u + thread / W, column thread % W
+    const cx<float> *pr = inter + ((size_t)(threadIdx.x / W) * L2 + t2) * ncx + cb +
+                          threadIdx.x % W;
+    const size_t ustride = (size_t)RPU * L2 * ncx;
     cx<float> v[U];
 #pragma unroll
-    for (int u = 0; u < U; u++) {
-      const int e = u * kFourT + threadIdx.x, k1 = e / W, c = e - k1 * W;
-      v[u] = ld_hintc(inter + ((size_t)k1 * L2 + t2) * ncx + cb + c, pol_done);
-    }
+    for (int u = 0; u < U; u++) v[u] = ld_hintc(pr + u * ustride, pol_done);
 #pragma unroll
     for (int u = 0; u < U; u++) S[u * kFourT + threadIdx.x] = v[u];
   }
@@ -330,28 +341,29 @@ k_fft4_inverseB(const cx<float> *__restrict__ inter, OT *__restrict__ y, int n, 
   const float scale = 1.0f / (float)L;
   constexpr int NE = L1 * 2 * W / kFourT;
   constexpr int B = NE < 16 ? NE : 16;
+  constexpr int RPU = kFourT / (2 * W);
+  // element (u, thread): row t1 = RPU u + thread / 2W, column thread % 2W
+  const int i = i0 + threadIdx.x % (2 * W);
+  const bool in = i < n;
+  const size_t row0 = (size_t)(L2 * (threadIdx.x / (2 * W)) + t2) * n + i;
+  const size_t ustride = (size_t)RPU * L2 * n;
 #pragma unroll
   for (int b0 = 0; b0 < NE; b0 += B) {
     float bv[B];
     if constexpr (sizeof(OT) == 8) {
       if (base) {
 #pragma unroll
-        for (int u = 0; u < B; u++) {
-          const int e = (b0 + u) * kFourT + threadIdx.x;
-          const int t1 = e / (2 * W), q = e - t1 * 2 * W, i = i0 + q;
-          bv[u] = (i < n) ? __ldg(&base[(size_t)(L2 * t1 + t2) * n + i]) : 0.f;
-        }
+        for (int u = 0; u < B; u++) bv[u] = in ? __ldg(&base[row0 + (b0 + u) * ustride]) : 0.f;
       }
     }
+    if (in) {
 #pragma unroll
-    for (int u = 0; u < B; u++) {
-      const int e = (b0 + u) * kFourT + threadIdx.x;
-      const int t1 = e / (2 * W), q = e - t1 * 2 * W, i = i0 + q;
-      if (i >= n) continue;
-      const OT val = to_out<float, OT>(scale * Sf[e]);
-      OT *dst = y + (size_t)(L2 * t1 + t2) * n + i;
-      if constexpr (sizeof(OT) == 8) *dst = base ? to_f64(bv[u]) - val : val;
-      else *dst = val;
+      for (int u = 0; u < B; u++) {
+        const OT val = to_out<float, OT>(scale * Sf[(b0 + u) * kFourT + threadIdx.x]);
+        OT *dst = y + row0 + (b0 + u) * ustride;
+        if constexpr (sizeof(OT) == 8) *dst = base ? to_f64(bv[u]) - val : val;
+        else *dst = val;
+      }
     }
   }
 }
