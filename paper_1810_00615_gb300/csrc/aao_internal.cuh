@@ -393,15 +393,16 @@ bool dst_supported(int64_t n);
 cudaError_t launch_dst_solve(const Ctx &c, void *spec, int prec, int transpose, cudaStream_t s);
 // w = A x - sub (or A^T x - sub) with the Arnoldi dots of w in the same pass:
 // out = [v0 . w (when v0 is given),] sub . w, w . w (the layout launch_multidot
-// gives for the vectors (v0,) sub).  dpart: matvec_dot_partials(c) doubles.
-// cudaErrorNotSupported for the literal heat form (FP64 stencil kernel).
+// gives for the vectors (v0,) sub), then sub . sub with self_dot (no v0).
+// dpart: matvec_dot_partials(c) doubles.  cudaErrorNotSupported for the
+// literal heat form (FP64 stencil kernel).
 size_t matvec_dot_partials(const Ctx &c);
 cudaError_t launch_matvec_dots(const Ctx &c, const double *x, double *y, int transpose,
                                cudaStream_t s, const double *sub, const double *v0,
-                               double *dpart, double *out);
+                               double *dpart, double *out, bool self_dot = false);
 cudaError_t launch_matvec_dots(const Ctx &c, const float *x, double *y, int transpose,
                                cudaStream_t s, const double *sub, const double *v0,
-                               double *dpart, double *out);
+                               double *dpart, double *out, bool self_dot = false);
 // y = A x (or A^T x); with `sub`, y = A x - sub (fused, for the shifted Arnoldi).
 cudaError_t launch_matvec(const Ctx &c, const double *x, double *y, int transpose,
                           cudaStream_t s, const double *sub = nullptr);
@@ -426,12 +427,14 @@ cudaError_t launch_norms2(const double *a, const double *b, int64_t N, double *p
                           double *out, cudaStream_t s);
 cudaError_t launch_multidot(const double *const *V, int nv, const double *w, int64_t N,
                             bool with_norm, double *partials, double *out, cudaStream_t s);
-// w -= sum_j hf[j] h[j] V_j (h on device, hf host factors, NULL = 1);
+// w -= sum_j hf[j] h[j] V_j (h on device, hf host factors, NULL = 1; with
+// div0 the j = 0 term is also divided by the device value *div0);
 // optionally fused: dots of the updated w with V_j (out2[j]); always its
 // squared norm (out2[nv]).
 cudaError_t launch_update_dots(const double *const *V, int nv, const double *h,
                                double *w, int64_t N, bool want_dots, double *partials,
-                               double *out2, cudaStream_t s, const double *hf = nullptr);
+                               double *out2, cudaStream_t s, const double *hf = nullptr,
+                               const double *div0 = nullptr);
 // x += sum_j y[j] Z_j (y on device)
 // x += Z y, or x = Z y (x not read) with assign
 cudaError_t launch_combine(const double *const *Z, int nv, const double *y, double *x,

@@ -264,8 +264,10 @@ __device__ __forceinline__ void dots_commit(double (&acc)[ND], double (*s_dot)[N
 }
 
 // DK >= 0 (with SUB): the kernel also forms the Arnoldi dots of its output
-// w = A x - v: (v0 . w if DK = 1), v . w and w . w, as block partials in
-// dpart (ND = DK + 2 values per block, in that order).
+// w = A x - v, as block partials in dpart, ND values per block in order:
+//   DK = 0: v . w, w . w
+//   DK = 1: v0 . w, v . w, w . w
+//   DK = 2: v . w, w . w, v . v   (the first step from x0 = 0, v = b: ||b||^2)
 template <int NB, bool TR, bool SUB, typename XT, bool CIRC, int DK = -1>
 __global__ void __launch_bounds__(kMvCols, AAO_MVFX_MINB)
 k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
@@ -274,7 +276,7 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
   constexpr int R = kFxRows, IN = R + NB - 1;   // input time steps per tile
   constexpr int kWarps = kMvCols / 32;
   constexpr int G = NB == 4 ? 2 : 0;            // guard bits (sums below 2^63)
-  constexpr int ND = DK >= 0 ? DK + 2 : 1;
+  constexpr int ND = DK < 0 ? 1 : (DK == 0 ? 2 : 3);
   static_assert(DK < 0 || SUB, "the dots need the subtrahend");
   using F = Fx<XT>;
   __shared__ long long s_halo[kWarps][2][IN];   // converted halo columns, walk order
@@ -360,7 +362,7 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
   // their latency hides behind the integer work of the steps in between
   constexpr int kPre = AAO_MVFX_PRE;
   const double *pv0 = SUB ? sub + (int64_t)t0 * n + ic : nullptr;
-  const double *pd0 = (DK >= 1) ? dv0 + (int64_t)t0 * n + ic : nullptr;
+  const double *pd0 = (DK == 1) ? dv0 + (int64_t)t0 * n + ic : nullptr;
   XT zpre[kPre];
   double vpre[kPre], dpre[kPre];
 #pragma unroll
@@ -368,11 +370,11 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
     const int t = t0 + k * dir;
     zpre[k] = z_ok(t) ? __ldg(zaddr(t, px0 + k * step)) : (XT)0;
     vpre[k] = (SUB && col_ok && t_ok(t) && k >= NB - 1) ? __ldg(pv0 + k * step) : 0.0;
-    dpre[k] = (DK >= 1 && col_ok && t_ok(t) && k >= NB - 1) ? __ldg(pd0 + k * step) : 0.0;
+    dpre[k] = (DK == 1 && col_ok && t_ok(t) && k >= NB - 1) ? __ldg(pd0 + k * step) : 0.0;
   }
   const XT *pz = px0 + kPre * step;
   const double *pv = SUB ? pv0 + kPre * step : nullptr;
-  const double *pd = (DK >= 1) ? pd0 + kPre * step : nullptr;
+  const double *pd = (DK == 1) ? pd0 + kPre * step : nullptr;
   double *py = y + (int64_t)t0 * n + ic;
   long long q1 = 0, q2 = 0, q3 = 0;             // q of the previous steps walked
 #pragma unroll 1
@@ -388,10 +390,10 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
         const bool inb = k + kPre < IN;
         zpre[u] = (inb && z_ok(tn)) ? __ldg(zaddr(tn, pz)) : (XT)0;
         if (SUB) vpre[u] = (inb && col_ok && t_ok(tn)) ? __ldg(pv) : 0.0;
-        if (DK >= 1) dpre[u] = (inb && col_ok && t_ok(tn)) ? __ldg(pd) : 0.0;
+        if (DK == 1) dpre[u] = (inb && col_ok && t_ok(tn)) ? __ldg(pd) : 0.0;
         pz += step;
         if (SUB) pv += step;
-        if (DK >= 1) pd += step;
+        if (DK == 1) pd += step;
       }
       const long long X = F::template fixed<G>(zk, em);
       long long Xl = __shfl_up_sync(0xffffffffu, X, 1);
@@ -426,10 +428,14 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
         const double td = fx_to_f64<RANGE>(T, unit);
         const double yv = SUB ? fma(rw.coef, td, -vk) : rw.coef * td;
         py[(int64_t)k * step] = yv;
-        if constexpr (DK >= 0) {
-          if constexpr (DK >= 1) dacc[0] = fma(dk, yv, dacc[0]);
-          dacc[ND - 2] = fma(vk, yv, dacc[ND - 2]);
-          dacc[ND - 1] = fma(yv, yv, dacc[ND - 1]);
+        if constexpr (DK == 1) {
+          dacc[0] = fma(dk, yv, dacc[0]);
+          dacc[1] = fma(vk, yv, dacc[1]);
+          dacc[2] = fma(yv, yv, dacc[2]);
+        } else if constexpr (DK >= 0) {
+          dacc[0] = fma(vk, yv, dacc[0]);
+          dacc[1] = fma(yv, yv, dacc[1]);
+          if constexpr (DK == 2) dacc[2] = fma(vk, vk, dacc[2]);
         }
       }
       q3 = q2;
@@ -530,31 +536,33 @@ size_t matvec_dot_partials(const Ctx &c) {
   return (size_t)g.x * g.y * 3;
 }
 
-// w = A x - sub with the Arnoldi dots of w fused in (DK = 1: with v0 too):
-// out = [v0 . w,] sub . w, w . w.
+// w = A x - sub with the Arnoldi dots of w fused in: out = [v0 . w,] sub . w,
+// w . w (DK = 0, 1), or sub . w, w . w, sub . sub with self_dot (DK = 2).
 template <typename XT>
 static cudaError_t matvec_dots_dispatch(const Ctx &c, const XT *x, double *y, int transpose,
                                         cudaStream_t s, const double *sub, const double *v0,
-                                        double *dpart, double *out) {
-  if (c.equation == AAO_HEAT_LITERAL || !sub) return cudaErrorNotSupported;
+                                        double *dpart, double *out, bool self_dot) {
+  if (c.equation == AAO_HEAT_LITERAL || !sub || (v0 && self_dot)) return cudaErrorNotSupported;
   const dim3 grid = mv_fx_grid(c);
   const int n = (int)c.n, ell = (int)c.ell;
   const int nb = c.equation == AAO_WAVE_BD4 ? 4 : (c.equation == AAO_WAVE_BD2 ? 3 : 2);
-  const int key = nb * 4 + (transpose ? 2 : 0) + (v0 ? 1 : 0);
+  const int dk = v0 ? 1 : (self_dot ? 2 : 0);
+  const int key = nb * 8 + (transpose ? 4 : 0) + dk;
 #define AAO_MVD(NBV, TRV, DKV)                                                           \
-  case NBV * 4 + (TRV ? 2 : 0) + DKV:                                                    \
+  case NBV * 8 + (TRV ? 4 : 0) + DKV:                                                    \
     k_matvec_fx<NBV, TRV, true, XT, false, DKV><<<grid, kMvCols, 0, s>>>(               \
         x, y, n, ell, c.mv_rows, sub, v0, dpart);                                        \
     break;
+#define AAO_MVD3(NBV, TRV) AAO_MVD(NBV, TRV, 0) AAO_MVD(NBV, TRV, 1) AAO_MVD(NBV, TRV, 2)
   switch (key) {
-    AAO_MVD(2, false, 0) AAO_MVD(2, false, 1) AAO_MVD(2, true, 0) AAO_MVD(2, true, 1)
-    AAO_MVD(3, false, 0) AAO_MVD(3, false, 1) AAO_MVD(3, true, 0) AAO_MVD(3, true, 1)
-    AAO_MVD(4, false, 0) AAO_MVD(4, false, 1) AAO_MVD(4, true, 0) AAO_MVD(4, true, 1)
+    AAO_MVD3(2, false) AAO_MVD3(2, true) AAO_MVD3(3, false) AAO_MVD3(3, true)
+    AAO_MVD3(4, false) AAO_MVD3(4, true)
     default: return cudaErrorNotSupported;
   }
+#undef AAO_MVD3
 #undef AAO_MVD
   note_launch();
-  const int nd = v0 ? 3 : 2;
+  const int nd = dk == 0 ? 2 : 3;
   k_finish_wide<<<nd, kThreads, 0, s>>>(dpart, (int)(grid.x * grid.y), nd, out);
   note_launch();
   return cudaGetLastError();
@@ -562,14 +570,14 @@ static cudaError_t matvec_dots_dispatch(const Ctx &c, const XT *x, double *y, in
 
 cudaError_t launch_matvec_dots(const Ctx &c, const double *x, double *y, int transpose,
                                cudaStream_t s, const double *sub, const double *v0,
-                               double *dpart, double *out) {
-  return matvec_dots_dispatch(c, x, y, transpose, s, sub, v0, dpart, out);
+                               double *dpart, double *out, bool self_dot) {
+  return matvec_dots_dispatch(c, x, y, transpose, s, sub, v0, dpart, out, self_dot);
 }
 
 cudaError_t launch_matvec_dots(const Ctx &c, const float *x, double *y, int transpose,
                                cudaStream_t s, const double *sub, const double *v0,
-                               double *dpart, double *out) {
-  return matvec_dots_dispatch(c, x, y, transpose, s, sub, v0, dpart, out);
+                               double *dpart, double *out, bool self_dot) {
+  return matvec_dots_dispatch(c, x, y, transpose, s, sub, v0, dpart, out, self_dot);
 }
 
 cudaError_t launch_circ_residual(const Ctx &c, const float *z, double *y, int transpose,
@@ -743,11 +751,12 @@ cudaError_t launch_multidot(const double *const *V, int nv, const double *w, int
 template <int NV, bool DOTS>
 __global__ void __launch_bounds__(kThreads)
 k_update(Ptrs8 V, const double *__restrict__ h, Coef8 f, double *__restrict__ w, int64_t N,
-         double *__restrict__ partials) {
+         double *__restrict__ partials, const double *__restrict__ div0) {
   constexpr int NO = (DOTS ? NV : 0) + 1;
   double hv[NV];
 #pragma unroll
   for (int j = 0; j < NV; j++) hv[j] = h[j] * f.c[j];
+  if (div0) hv[0] /= *div0;   // the first vector's squared norm, known only on the device
   double acc[NO];
 #pragma unroll
   for (int j = 0; j < NO; j++) acc[j] = 0.0;
@@ -772,7 +781,7 @@ k_update(Ptrs8 V, const double *__restrict__ h, Coef8 f, double *__restrict__ w,
 
 cudaError_t launch_update_dots(const double *const *V, int nv, const double *h, double *w,
                                int64_t N, bool want_dots, double *partials, double *out2,
-                               cudaStream_t s, const double *hf) {
+                               cudaStream_t s, const double *hf, const double *div0) {
   // Groups of 8 vectors: every group but the last only updates; the dots of
   // the final w with all vectors are then taken by a multi-dot pass when
   // nv > 8 (the fused path covers nv <= 8, the common case).
@@ -788,8 +797,8 @@ cudaError_t launch_update_dots(const double *const *V, int nv, const double *h, 
     const Coef8 F = coef(0, nv);
 #define AAO_UP(G)                                                                          \
   case G:                                                                                  \
-    if (want_dots) k_update<G, true><<<nb, kThreads, 0, s>>>(P, h, F, w, N, partials);     \
-    else k_update<G, false><<<nb, kThreads, 0, s>>>(P, h, F, w, N, partials);              \
+    if (want_dots) k_update<G, true><<<nb, kThreads, 0, s>>>(P, h, F, w, N, partials, div0); \
+    else k_update<G, false><<<nb, kThreads, 0, s>>>(P, h, F, w, N, partials, div0);        \
     note_launch();                                                                         \
     break;
     switch (nv) {
@@ -811,7 +820,7 @@ cudaError_t launch_update_dots(const double *const *V, int nv, const double *h, 
     for (int j = 0; j < g; j++) P.p[j] = V[done + j];
     const Coef8 F = coef(done, g);
     switch (g) {
-#define AAO_UP2(G) case G: k_update<G, false><<<nb, kThreads, 0, s>>>(P, h + done, F, w, N, partials); note_launch(); break;
+#define AAO_UP2(G) case G: k_update<G, false><<<nb, kThreads, 0, s>>>(P, h + done, F, w, N, partials, done == 0 ? div0 : nullptr); note_launch(); break;
       AAO_UP2(1) AAO_UP2(2) AAO_UP2(3) AAO_UP2(4) AAO_UP2(5) AAO_UP2(6) AAO_UP2(7) AAO_UP2(8)
 #undef AAO_UP2
     }

@@ -677,28 +677,37 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
   // residual -b, so the first cycle needs no matvec (V_0 aliases b, the sign
   // goes into its lazy scale).  Under AAO_GUESS_ZERO x is not read at all:
   // only ||b||^2 is formed and the first update assigns x = Z y.
+  // With the fused matvec even ||b||^2 waits for the first Arnoldi step:
+  // its matvec has b as the subtrahend and adds b . b to its dots (the apply
+  // before it is linear, so the scale 1/||b|| can be applied afterwards).
   const bool guess_zero = c.guess == AAO_GUESS_ZERO;
-  if (guess_zero) {
-    AAO_CK(c, run(c, AAO_K_DOTS, s, [&] {
-      return aao::launch_multidot(nullptr, 0, b, N, true, red, d_nr, s);
-    }));
-    AAO_CK(c, fetch(d_nr, 1));
-  } else {
-    AAO_CK(c, run(c, AAO_K_DOTS, s, [&] { return aao::launch_norms2(b, x, N, red, d_nr, s); }));
-    AAO_CK(c, fetch(d_nr, 2));
+  bool defer_b = guess_zero && c.equation != AAO_HEAT_LITERAL && maxit > 0 && m >= 1;
+  double bnorm = 1.0;
+  if (!defer_b) {
+    if (guess_zero) {
+      AAO_CK(c, run(c, AAO_K_DOTS, s, [&] {
+        return aao::launch_multidot(nullptr, 0, b, N, true, red, d_nr, s);
+      }));
+      AAO_CK(c, fetch(d_nr, 1));
+    } else {
+      AAO_CK(c, run(c, AAO_K_DOTS, s, [&] { return aao::launch_norms2(b, x, N, red, d_nr, s); }));
+      AAO_CK(c, fetch(d_nr, 2));
+    }
+    AAO_CK(c, cudaStreamSynchronize(s));
+    bnorm = std::sqrt(hs[320]);
   }
-  AAO_CK(c, cudaStreamSynchronize(s));
-  const double bnorm = std::sqrt(hs[320]);
-  bool x0_zero = guess_zero || hs[321] == 0.0;
+  bool x0_zero = guess_zero || (!defer_b && hs[321] == 0.0);
   bool x_unset = guess_zero;   // x holds no value yet (written by the first update)
-  if (!std::isfinite(bnorm)) return AAO_ENUMERIC;
-  if (bnorm == 0.0) {
+  // x = 0 is the answer to b = 0 (found here or after the first matvec)
+  auto zero_answer = [&]() -> int {
     AAO_CK(c, cudaMemsetAsync(x, 0, vb, s));
     if (x_host) AAO_CK(c, cudaMemcpyAsync(x_host, x, vb, cudaMemcpyDeviceToHost, s));
     AAO_CK(c, cudaStreamSynchronize(s));
     if (info) { info->relres_true = 0.0; info->relres_est = 0.0; }
     return AAO_OK;
-  }
+  };
+  if (!defer_b && !std::isfinite(bnorm)) return AAO_ENUMERIC;
+  if (!defer_b && bnorm == 0.0) return zero_answer();
   bool copy_pending = false;   // a copy of x to x_host is in flight
   bool host_current = false;   // x_host holds (or will hold) the current x
   if (x_host && !c.copy_stream) {
@@ -716,7 +725,8 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
     double beta;
     double v0_sign;
     if (x0_zero) {
-      // x = 0: r = b; V_0 = b read in place, v_0 = V_0 / beta
+      // x = 0: r = b; V_0 = b read in place, v_0 = V_0 / beta (beta = ||b||,
+      // known after the first matvec when deferred)
       V[0] = const_cast<double *>(b);
       beta = bnorm;
       v0_sign = 1.0;
@@ -740,7 +750,7 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
       beta = std::sqrt(hs[320]);
       v0_sign = -1.0;
     }
-    relres_true = beta / bnorm;
+    relres_true = defer_b ? 1.0 : beta / bnorm;
     if (!std::isfinite(beta)) { status = AAO_ENUMERIC; break; }
     if (relres_true <= rtol) { status = AAO_OK; break; }
     if (iters >= maxit) { status = AAO_ENOCONV; break; }
@@ -753,7 +763,7 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
       stalled = 0;
     }
     if (relres_true < best) best = relres_true;
-    sc[0] = v0_sign / beta;
+    sc[0] = defer_b ? 1.0 : v0_sign / beta;
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int jd = 0;
@@ -777,9 +787,10 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
       const bool fused = nv <= 2 && c.equation != AAO_HEAT_LITERAL;
       if (fused) {
         const double *v0 = nv == 2 ? V[0] : nullptr;
+        const bool self = defer_b;   // also b . b (step 0 of the first cycle)
         AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] {
-          return zf ? aao::launch_matvec_dots(c, Zf[(size_t)j], w, tr, s, V[(size_t)j], v0, dpart, d_h1)
-                    : aao::launch_matvec_dots(c, Z[(size_t)j], w, tr, s, V[(size_t)j], v0, dpart, d_h1);
+          return zf ? aao::launch_matvec_dots(c, Zf[(size_t)j], w, tr, s, V[(size_t)j], v0, dpart, d_h1, self)
+                    : aao::launch_matvec_dots(c, Z[(size_t)j], w, tr, s, V[(size_t)j], v0, dpart, d_h1, self);
         }));
       } else {
         AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] {
@@ -791,12 +802,27 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
         }));
       }
       for (int i = 0; i < nv; i++) sc2[(size_t)i] = sc[(size_t)i] * sc[(size_t)i];
+      // deferred ||b||: the projection on V_0 = b divides by b . b on the
+      // device (d_h1[2]), so the update needs no round trip to the host
       AAO_CK(c, run(c, AAO_K_UPDATE, s, [&] {
-        return aao::launch_update_dots(V.data(), nv, d_h1, w, N, false, red, d_nr, s, sc2.data());
+        return aao::launch_update_dots(V.data(), nv, d_h1, w, N, false, red, d_nr, s, sc2.data(),
+                                       defer_b ? d_h1 + 2 : nullptr);
       }));
-      AAO_CK(c, fetch(d_h1, nv + 1));
+      AAO_CK(c, fetch(d_h1, defer_b ? 3 : nv + 1));
       AAO_CK(c, fetch(d_nr + nv, 1));
       AAO_CK(c, cudaStreamSynchronize(s));
+      if (defer_b) {
+        bnorm = std::sqrt(hs[2]);
+        if (!std::isfinite(bnorm)) return AAO_ENUMERIC;
+        if (bnorm == 0.0) return zero_answer();
+        defer_b = false;
+        beta = bnorm;
+        sc[0] = 1.0 / beta;
+        sc2[0] = sc[0] * sc[0];   // for a second Gram-Schmidt pass
+        g[0] = beta;
+        relres_true = 1.0;
+        best = 1.0;
+      }
       const double before = hs[nv];          // ||w~||^2 before the projection (unscaled)
       double after = hs[320 + nv];           // after
       for (int i = 0; i < nv; i++) Hij(i, j) = sc[(size_t)i] * sc[(size_t)j] * hs[i];
