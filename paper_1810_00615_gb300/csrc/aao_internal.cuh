@@ -257,6 +257,15 @@ struct RecTab {
   cx<R> e[kRecLevels];
 };
 
+// Stencil of the block circulant P (Section 3) for the compensated
+// residual: block A_j (time lag j, j < taps) is c0_j on the diagonal and c1_j
+// beside it, each stored as an FP32 pair hi + lo (c = hi + lo to 2^-48).
+struct CircDF {
+  float hi[4][2];
+  float lo[4][2];
+  int taps;
+};
+
 // ------------------------------------------------------------ context
 struct Ctx {
   int64_t n = 0, ell = 0, N = 0;
@@ -296,6 +305,7 @@ struct Ctx {
   struct MvRow *mv_rows = nullptr;     // fixed-point matvec: per-step combination of A
   struct MvRow *mv_rows_p = nullptr;   // the same for the circulant P
   bool refine = false;            // FP32 preconditioner with one refinement sweep
+  CircDF circ_df{};               // P's stencil for the compensated residual
   int guess = AAO_GUESS_GIVEN;    // solves read x as the initial guess, or start from 0
   double *mv_d0 = nullptr;        // per-step diagonal of A0^t (ell)
   double *mv_o0 = nullptr;        // per-step off-diagonal of A0^t (ell)
@@ -343,6 +353,7 @@ struct MvRow {
   int main_k;
   int pad;
 };
+
 
 struct WsLayout {
   size_t spec = 0, spec_bytes = 0;
@@ -410,6 +421,11 @@ cudaError_t launch_matvec(const Ctx &c, const float *x, double *y, int transpose
                           cudaStream_t s, const double *sub = nullptr);
 // y = P z - sub (or P^T z - sub) for an FP32 z: the residual of the refined
 // FP32 preconditioner, P the block circulant of Section 3 (constant step).
+// r = P z - x for an FP32 z in FP32 compensated arithmetic: exact products
+// (FMA), Sum2 summation, x split into two FP32 halves; r to FP32 relative
+// accuracy plus 2^-40 of the terms, written in FP64.  On the FP32 pipe.
+cudaError_t launch_circ_residual_df(const Ctx &c, const float *z, const double *x, double *r,
+                                    int transpose, cudaStream_t s);
 cudaError_t launch_circ_residual(const Ctx &c, const float *z, double *y, int transpose,
                                  cudaStream_t s, const double *sub);
 // u = x - E y, the right-hand side of a Neumann term (Section 2), in FP64.

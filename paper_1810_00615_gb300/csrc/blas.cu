@@ -580,6 +580,128 @@ cudaError_t launch_matvec_dots(const Ctx &c, const float *x, double *y, int tran
   return matvec_dots_dispatch(c, x, y, transpose, s, sub, v0, dpart, out, self_dot);
 }
 
+// ------------------------------------------ compensated circulant residual
+// r = P z - x for an FP32 z (the refined preconditioner's residual) on the
+// FP32 pipe.  r is needed to FP32 relative accuracy only (it feeds the FP32
+// apply of the correction), but P z and x cancel to ~1e-7 of their size, so
+// the sum is compensated: every product c z is formed exactly as an FP32
+// pair (FMA; c = hi + lo to 2^-48), x is split into two FP32 halves, and the
+// terms are added by Sum2 (Ogita, Rump and Oishi 2005, a TwoSum per term with
+// the errors accumulated): the result is within 2^-24 |r| plus about
+// n^2 2^-48 of the terms' magnitudes, n <= 14 terms.  It is rounded to FP32
+// (the FP32 apply of the correction reads no more) and stored widened.  No
+// FP64 instruction: the kernel runs on the FP32 and integer pipes.
+
+// x = hi + lo: hi the FP32 rounding of x (to nearest even), lo = x - hi to
+// FP32, from the bits of x with integer operations only (the FP64 pipe is
+// 1/64 of the FP32 one).  |x| < 2^-74 is flushed to zero (an absolute error
+// below 2^-74; the block vectors the solver applies this to are scaled to
+// unit norm), |x| >= 2^127 and non-finite x give an infinite or NaN hi.
+__device__ __forceinline__ void split_f64(double x, float &hi, float &lo) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned w = (unsigned)(u >> 32), l = (unsigned)u;
+  const unsigned e = (w >> 20) & 0x7ffu, sign = w & 0x80000000u;
+  if (e - 949u > 201u) {               // outside [949, 1150]
+    const bool nan = e == 2047u && ((w & 0xfffffu) | l);
+    hi = __uint_as_float(sign | (e > 1150u ? (0x7f800000u | (nan ? 0x400000u : 0u)) : 0u));
+    lo = 0.f;
+    return;
+  }
+  unsigned bits = ((e - 896u) << 23) | ((w & 0xfffffu) << 3) | (l >> 29);
+  int rem = (int)(l & 0x1fffffffu);    // the 29 bits below hi's last place
+  const bool up = rem > (1 << 28) || (rem == (1 << 28) && (bits & 1u));
+  bits += up ? 1u : 0u;
+  if (up) rem -= (1 << 29);
+  hi = __uint_as_float(sign | bits);
+  const float fl = __int2float_rn(rem) * __uint_as_float((e - 1075u + 127u) << 23);
+  lo = __uint_as_float(__float_as_uint(fl) ^ sign);
+}
+
+// An FP32 value widened to FP64 with integer operations (subnormals flushed
+// to zero; infinities and NaN kept).
+__device__ __forceinline__ double widen_f32(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned e = (u >> 23) & 0xffu, sign = u & 0x80000000u;
+  if (e == 0u) return __hiloint2double((int)sign, 0);
+  const unsigned hi = sign | ((e == 255u ? 2047u : e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+template <int NB, bool TR>
+__global__ void __launch_bounds__(kMvCols)
+k_circ_residual_df(const float *__restrict__ z, const double *__restrict__ x,
+                   double *__restrict__ r, int n, int ell, CircDF cf) {
+  const int i = blockIdx.x * kMvCols + threadIdx.x;
+  if (i >= n) return;                  // no barriers in this kernel
+  const int c0 = blockIdx.y * kMvRows;
+  const int c1 = min(ell, c0 + kMvRows);
+  auto load = [&](int t, float (&v)[3]) {
+    const float *zr = z + (int64_t)t * n;
+    v[0] = __ldg(&zr[i]);
+    v[1] = (i > 0) ? __ldg(&zr[i - 1]) : 0.f;
+    v[2] = (i + 1 < n) ? __ldg(&zr[i + 1]) : 0.f;
+  };
+  // lag[j]: the step j behind in walk order (time wrapped around: P)
+  float lag[NB][3];
+  const int first = TR ? c1 - 1 : c0, stp = TR ? -1 : 1;
+#pragma unroll
+  for (int j = 1; j < NB; j++) {
+    int tj = first - j * stp;
+    tj = ((tj % ell) + ell) % ell;
+    load(tj, lag[j]);
+  }
+  float s, e;
+  auto add = [&](float chi, float clo, float v) {
+    const float p = __fmul_rn(chi, v);
+    const float pe = __fmaf_rn(chi, v, -p);              // chi v = p + pe exactly
+    const float s1 = __fadd_rn(s, p);                    // TwoSum(s, p)
+    const float bb = __fsub_rn(s1, s);
+    const float er = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bb)), __fsub_rn(p, bb));
+    s = s1;
+    e = __fadd_rn(e, __fadd_rn(er, __fmaf_rn(clo, v, pe)));
+  };
+  for (int k = 0; k < c1 - c0; k++) {
+    const int t = first + k * stp;
+    load(t, lag[0]);
+    const int64_t g = (int64_t)t * n + i;
+    float xh, xl;
+    split_f64(__ldg(&x[g]), xh, xl);
+    s = -xh;
+    e = -xl;
+#pragma unroll
+    for (int j = 0; j < NB; j++) {
+      add(cf.hi[j][0], cf.lo[j][0], lag[j][0]);
+      add(cf.hi[j][1], cf.lo[j][1], lag[j][1]);
+      add(cf.hi[j][1], cf.lo[j][1], lag[j][2]);
+    }
+    r[g] = widen_f32(__fadd_rn(s, e));   // r to FP32: all the apply that follows reads
+#pragma unroll
+    for (int j = NB - 1; j >= 1; j--) {
+      lag[j][0] = lag[j - 1][0];
+      lag[j][1] = lag[j - 1][1];
+      lag[j][2] = lag[j - 1][2];
+    }
+  }
+}
+
+cudaError_t launch_circ_residual_df(const Ctx &c, const float *z, const double *x, double *r,
+                                    int transpose, cudaStream_t s) {
+  const dim3 grid((unsigned)((c.n + kMvCols - 1) / kMvCols),
+                  (unsigned)((c.ell + kMvRows - 1) / kMvRows));
+  const int n = (int)c.n, ell = (int)c.ell;
+  switch (c.circ_df.taps * 2 + (transpose ? 1 : 0)) {
+    case 4: k_circ_residual_df<2, false><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
+    case 5: k_circ_residual_df<2, true><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
+    case 6: k_circ_residual_df<3, false><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
+    case 7: k_circ_residual_df<3, true><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
+    case 8: k_circ_residual_df<4, false><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
+    case 9: k_circ_residual_df<4, true><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
+    default: return cudaErrorInvalidValue;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_circ_residual(const Ctx &c, const float *z, double *y, int transpose,
                                  cudaStream_t s, const double *sub) {
   return matvec_dispatch<float, true>(c, z, y, transpose, s, sub);

@@ -437,6 +437,29 @@ int refresh_constants(Ctx &c) {
                              : c.equation == AAO_HEAT_LITERAL ? 1.0 / c.h
                                                               : c.tau * c.kappa / c.h);
   AAO_CK(c, upload((void **)&c.beta_p, beta_p));
+  // the same circulant's stencil per time lag, FP32 hi + lo pairs
+  {
+    const double bp = beta_p.empty() ? 0.0 : beta_p[0];
+    double a[4] = {1.0, -1.0, 0.0, 0.0};
+    int taps = 2;
+    switch (c.equation) {
+      case AAO_WAVE_BD2: a[0] = 1.0; a[1] = -2.0; a[2] = 1.0; taps = 3; break;
+      case AAO_WAVE_BD4: a[0] = 2.0; a[1] = -5.0; a[2] = 4.0; a[3] = -1.0; taps = 4; break;
+      case AAO_HEAT_LITERAL: a[0] = c.tau; break;
+      default: break;
+    }
+    aao::CircDF cf{};
+    cf.taps = taps;
+    for (int j = 0; j < 4; j++) {
+      const double cc[2] = {a[j] * 4.0 * mh + (j == 0 ? 2.0 * bp : 0.0),
+                            a[j] * mh - (j == 0 ? bp : 0.0)};
+      for (int q = 0; q < 2; q++) {
+        cf.hi[j][q] = (float)cc[q];
+        cf.lo[j][q] = (float)(cc[q] - (double)cf.hi[j][q]);
+      }
+    }
+    c.circ_df = cf;
+  }
   // fixed-point matvec output stages for A (per step) and P (constant step)
   auto mvrow = [&](double b) {
     aao::MvRow r{};
@@ -572,16 +595,17 @@ cudaError_t precond_once(Ctx &c, const double *x, const YT *yprev, YT *y, int tr
   });
 }
 
-// Refined FP32 apply: z0 = P32^{-1} x, r = P z0 - x (exact fixed-point
-// circulant product), y = z0 - P32^{-1} r.  The error of y is the product of
-// two FP32 apply errors.  x and y may not overlap the refinement scratch.
+// Refined FP32 apply: z0 = P32^{-1} x, r = P z0 - x (compensated FP32
+// circulant product, accurate to FP32 relative to r), y = z0 - P32^{-1} r.
+// The error of y is the product of two FP32 apply errors.  x and y may not
+// overlap the refinement scratch.
 cudaError_t precond_refined(Ctx &c, const double *x, double *y, int tr, cudaStream_t s) {
   const aao::WsLayout L = aao::ws_layout(c, 0);
   float *z0 = reinterpret_cast<float *>(c.ws + L.rf32);
   double *r = reinterpret_cast<double *>(c.ws + L.rf64);
   cudaError_t e = precond_once<float>(c, x, nullptr, z0, tr, s);
   if (e != cudaSuccess) return e;
-  e = run(c, AAO_K_REFINE, s, [&] { return aao::launch_circ_residual(c, z0, r, tr, s, x); });
+  e = run(c, AAO_K_REFINE, s, [&] { return aao::launch_circ_residual_df(c, z0, x, r, tr, s); });
   if (e != cudaSuccess) return e;
   return precond_once<double>(c, r, nullptr, y, tr, s, z0);
 }
