@@ -394,6 +394,13 @@ cudaError_t fft_inverse_f64(const Ctx &c, const void *spec, double *y, cudaStrea
 // preconditioned basis of the mixed solver).
 cudaError_t fft_forward_f32_yf(const Ctx &c, const double *x, const float *yprev, void *spec,
                                cudaStream_t s, void *inter = nullptr);
+// Does the four-step FP32 transform serve this context's ell (a power of
+// two, 256 ... 4096, and the kernels built in)?
+bool fft_four_supported(const Ctx &c);
+// FP32 block vector -> FP32 half spectrum by the four-step kernels
+// (cudaErrorNotSupported for other lengths or without scratch).
+cudaError_t fft_forward_f32_from_f32(const Ctx &c, const float *x, void *spec, cudaStream_t s,
+                                     void *inter);
 cudaError_t fft_inverse_f32_to_f32(const Ctx &c, const void *spec, float *y, cudaStream_t s,
                                    void *inter = nullptr);
 cudaError_t launch_tridiag(const Ctx &c, void *spec, int prec, int transpose,
@@ -425,6 +432,8 @@ cudaError_t launch_matvec(const Ctx &c, const float *x, double *y, int transpose
 // (FMA), Sum2 summation, x split into two FP32 halves; r to FP32 relative
 // accuracy plus 2^-40 of the terms, written in FP64.  On the FP32 pipe.
 cudaError_t launch_circ_residual_df(const Ctx &c, const float *z, const double *x, double *r,
+                                    int transpose, cudaStream_t s);
+cudaError_t launch_circ_residual_df(const Ctx &c, const float *z, const double *x, float *r,
                                     int transpose, cudaStream_t s);
 cudaError_t launch_circ_residual(const Ctx &c, const float *z, double *y, int transpose,
                                  cudaStream_t s, const double *sub);

@@ -627,10 +627,13 @@ __device__ __forceinline__ double widen_f32(float v) {
   return __hiloint2double((int)hi, (int)(u << 29));
 }
 
-template <int NB, bool TR>
+__device__ __forceinline__ void store_r(double *p, float v) { *p = widen_f32(v); }
+__device__ __forceinline__ void store_r(float *p, float v) { *p = v; }
+
+template <int NB, bool TR, typename RT>
 __global__ void __launch_bounds__(kMvCols)
 k_circ_residual_df(const float *__restrict__ z, const double *__restrict__ x,
-                   double *__restrict__ r, int n, int ell, CircDF cf) {
+                   RT *__restrict__ r, int n, int ell, CircDF cf) {
   const int i = blockIdx.x * kMvCols + threadIdx.x;
   if (i >= n) return;                  // no barriers in this kernel
   const int c0 = blockIdx.y * kMvRows;
@@ -643,7 +646,7 @@ k_circ_residual_df(const float *__restrict__ z, const double *__restrict__ x,
   };
   // lag[j]: the step j behind in walk order (time wrapped around: P)
   float lag[NB][3];
-  const int first = TR ? c1 - 1 : c0, stp = TR ? -1 : 1;
+  const int first = TR ? c1 - 1 : c0, stp = TR ? -1 : 1, cnt = c1 - c0;
 #pragma unroll
   for (int j = 1; j < NB; j++) {
     int tj = first - j * stp;
@@ -660,12 +663,24 @@ k_circ_residual_df(const float *__restrict__ z, const double *__restrict__ x,
     s = s1;
     e = __fadd_rn(e, __fadd_rn(er, __fmaf_rn(clo, v, pe)));
   };
-  for (int k = 0; k < c1 - c0; k++) {
+  // the next step's values are requested before this step's arithmetic
+  float cur[3];
+  double xc;
+  load(first, cur);
+  xc = __ldg(&x[(int64_t)first * n + i]);
+  for (int k = 0; k < cnt; k++) {
     const int t = first + k * stp;
-    load(t, lag[0]);
-    const int64_t g = (int64_t)t * n + i;
+    float nxt[3] = {0.f, 0.f, 0.f};
+    double xn = 0.0;
+    if (k + 1 < cnt) {
+      load(t + stp, nxt);
+      xn = __ldg(&x[(int64_t)(t + stp) * n + i]);
+    }
+    lag[0][0] = cur[0];
+    lag[0][1] = cur[1];
+    lag[0][2] = cur[2];
     float xh, xl;
-    split_f64(__ldg(&x[g]), xh, xl);
+    split_f64(xc, xh, xl);
     s = -xh;
     e = -xl;
 #pragma unroll
@@ -674,32 +689,47 @@ k_circ_residual_df(const float *__restrict__ z, const double *__restrict__ x,
       add(cf.hi[j][1], cf.lo[j][1], lag[j][1]);
       add(cf.hi[j][1], cf.lo[j][1], lag[j][2]);
     }
-    r[g] = widen_f32(__fadd_rn(s, e));   // r to FP32: all the apply that follows reads
+    store_r(r + (int64_t)t * n + i, __fadd_rn(s, e));   // r to FP32: all the apply reads
 #pragma unroll
     for (int j = NB - 1; j >= 1; j--) {
       lag[j][0] = lag[j - 1][0];
       lag[j][1] = lag[j - 1][1];
       lag[j][2] = lag[j - 1][2];
     }
+    cur[0] = nxt[0];
+    cur[1] = nxt[1];
+    cur[2] = nxt[2];
+    xc = xn;
   }
 }
 
-cudaError_t launch_circ_residual_df(const Ctx &c, const float *z, const double *x, double *r,
-                                    int transpose, cudaStream_t s) {
+template <typename RT>
+static cudaError_t circ_residual_df_any(const Ctx &c, const float *z, const double *x, RT *r,
+                                        int transpose, cudaStream_t s) {
   const dim3 grid((unsigned)((c.n + kMvCols - 1) / kMvCols),
                   (unsigned)((c.ell + kMvRows - 1) / kMvRows));
   const int n = (int)c.n, ell = (int)c.ell;
   switch (c.circ_df.taps * 2 + (transpose ? 1 : 0)) {
-    case 4: k_circ_residual_df<2, false><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
-    case 5: k_circ_residual_df<2, true><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
-    case 6: k_circ_residual_df<3, false><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
-    case 7: k_circ_residual_df<3, true><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
-    case 8: k_circ_residual_df<4, false><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
-    case 9: k_circ_residual_df<4, true><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
+    case 4: k_circ_residual_df<2, false, RT><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
+    case 5: k_circ_residual_df<2, true, RT><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
+    case 6: k_circ_residual_df<3, false, RT><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
+    case 7: k_circ_residual_df<3, true, RT><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
+    case 8: k_circ_residual_df<4, false, RT><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
+    case 9: k_circ_residual_df<4, true, RT><<<grid, kMvCols, 0, s>>>(z, x, r, n, ell, c.circ_df); break;
     default: return cudaErrorInvalidValue;
   }
   note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_circ_residual_df(const Ctx &c, const float *z, const double *x, double *r,
+                                    int transpose, cudaStream_t s) {
+  return circ_residual_df_any(c, z, x, r, transpose, s);
+}
+
+cudaError_t launch_circ_residual_df(const Ctx &c, const float *z, const double *x, float *r,
+                                    int transpose, cudaStream_t s) {
+  return circ_residual_df_any(c, z, x, r, transpose, s);
 }
 
 cudaError_t launch_circ_residual(const Ctx &c, const float *z, double *y, int transpose,

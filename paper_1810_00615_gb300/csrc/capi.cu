@@ -605,6 +605,20 @@ cudaError_t precond_refined(Ctx &c, const double *x, double *y, int tr, cudaStre
   double *r = reinterpret_cast<double *>(c.ws + L.rf64);
   cudaError_t e = precond_once<float>(c, x, nullptr, z0, tr, s);
   if (e != cudaSuccess) return e;
+  // where the four-step transform serves, r stays FP32 (its precision) and
+  // the correction's forward transform reads it directly
+  void *inter = L.inter_bytes ? c.ws + L.inter : nullptr;
+  if (inter && aao::fft_four_supported(c)) {
+    float *r32 = reinterpret_cast<float *>(r);
+    void *spec = c.ws + L.spec;
+    e = run(c, AAO_K_REFINE, s, [&] { return aao::launch_circ_residual_df(c, z0, x, r32, tr, s); });
+    if (e != cudaSuccess) return e;
+    e = run(c, AAO_K_FFT_FORWARD, s, [&] { return aao::fft_forward_f32_from_f32(c, r32, spec, s, inter); });
+    if (e != cudaSuccess) return e;
+    e = run(c, AAO_K_TRIDIAG, s, [&] { return aao::launch_tridiag(c, spec, c.prec, tr, s); });
+    if (e != cudaSuccess) return e;
+    return run(c, AAO_K_FFT_INVERSE, s, [&] { return aao::fft_inverse_f32(c, spec, y, s, inter, z0); });
+  }
   e = run(c, AAO_K_REFINE, s, [&] { return aao::launch_circ_residual_df(c, z0, x, r, tr, s); });
   if (e != cudaSuccess) return e;
   return precond_once<double>(c, r, nullptr, y, tr, s, z0);

@@ -132,6 +132,22 @@ cudaError_t forward_any(int64_t ell, int64_t n, int64_t n_pad, const double *x, 
   }
 }
 
+// The four-step forward transform of an FP32 block vector (FP32 spectrum);
+// cudaErrorNotSupported where ell is not a four-step length.
+inline cudaError_t forward_four_f32_input(int64_t ell, int64_t n, int64_t n_pad, const float *x,
+                                          cx<float> *spec, const cx<float> *tw, cudaStream_t s,
+                                          void *inter) {
+  if (!AAO_FFT_FOUR || !inter) return cudaErrorNotSupported;
+  switch (ell) {
+    case 256: return four_forward<256, float>(n, n_pad, x, spec, tw, s, inter);
+    case 512: return four_forward<512, float>(n, n_pad, x, spec, tw, s, inter);
+    case 1024: return four_forward<1024, float>(n, n_pad, x, spec, tw, s, inter);
+    case 2048: return four_forward<2048, float>(n, n_pad, x, spec, tw, s, inter);
+    case 4096: return four_forward<4096, float>(n, n_pad, x, spec, tw, s, inter);
+    default: return cudaErrorNotSupported;
+  }
+}
+
 template <typename R>
 size_t inter_bytes_any(int64_t ell, int64_t n) {
   switch (ell) {

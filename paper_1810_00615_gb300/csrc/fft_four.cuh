@@ -104,9 +104,10 @@ __device__ __forceinline__ void dft_columns(cx<float> *S, const cx<float> *__res
 }
 
 // Forward 1.  grid (ncx / W, L2 = t2); L1 W complex of dynamic shared memory.
-template <int L, int W>
+// XT: FP64 input (converted to FP32 on the way in) or FP32 input.
+template <int L, int W, typename XT = double>
 __global__ void __launch_bounds__(kFourT)
-k_fft4_forward1(const double *__restrict__ x, cx<float> *__restrict__ inter, int n, int ncx,
+k_fft4_forward1(const XT *__restrict__ x, cx<float> *__restrict__ inter, int n, int ncx,
                 const cx<float> *__restrict__ tw) {
   constexpr int L1 = Four<L>::L1, L2 = Four<L>::L2;
   extern __shared__ __align__(16) unsigned char four_smem[];
@@ -125,15 +126,21 @@ k_fft4_forward1(const double *__restrict__ x, cx<float> *__restrict__ inter, int
   // column q = thread % 2W, the same for every u
   const int q = threadIdx.x % (2 * W), i = i0 + q;
   const bool in = i < n;
-  const double *px = x + (size_t)(L2 * (threadIdx.x / (2 * W)) + t2) * n + i;
+  const XT *px = x + (size_t)(L2 * (threadIdx.x / (2 * W)) + t2) * n + i;
   const size_t ustride = (size_t)RPU * L2 * n;
 #pragma unroll
   for (int b0 = 0; b0 < NE; b0 += B) {
-    double d[B];
+    XT d[B];
 #pragma unroll
-    for (int u = 0; u < B; u++) d[u] = in ? ld_hint(px + (b0 + u) * ustride, pol_stream) : 0.0;
+    for (int u = 0; u < B; u++) {
+      if constexpr (sizeof(XT) == 8) d[u] = in ? ld_hint(px + (b0 + u) * ustride, pol_stream) : 0.0;
+      else d[u] = in ? __ldg(px + (b0 + u) * ustride) : 0.f;
+    }
 #pragma unroll
-    for (int u = 0; u < B; u++) Sf[(b0 + u) * kFourT + threadIdx.x] = to_f32(d[u]);
+    for (int u = 0; u < B; u++) {
+      if constexpr (sizeof(XT) == 8) Sf[(b0 + u) * kFourT + threadIdx.x] = to_f32(d[u]);
+      else Sf[(b0 + u) * kFourT + threadIdx.x] = d[u];
+    }
   }
   __syncthreads();
   dft_columns<L1, W, L, -1>(S, tw);
@@ -379,18 +386,18 @@ inline bool four_discard_ok(const void *inter, const void *spec, int64_t n_pad) 
          (reinterpret_cast<uintptr_t>(spec) & 255) == 0 && (n_pad % 16) == 0;
 }
 
-template <int L>
-cudaError_t four_forward(int64_t n, int64_t n_pad, const double *x, cx<float> *spec,
+template <int L, typename XT = double>
+cudaError_t four_forward(int64_t n, int64_t n_pad, const XT *x, cx<float> *spec,
                          const cx<float> *tw, cudaStream_t s, void *inter) {
   constexpr int L1 = Four<L>::L1, L2 = Four<L>::L2, W = kFourW;
   constexpr size_t sm1 = (size_t)L1 * W * sizeof(cx<float>);
   constexpr size_t sm2 = 2 * (size_t)L2 * W * sizeof(cx<float>);
   const int ncx = (int)four_ncx(n);
   cx<float> *ip = static_cast<cx<float> *>(inter);
-  cudaError_t e = kernel_setup((const void *)k_fft4_forward1<L, W>, kFourT, sm1);
+  cudaError_t e = kernel_setup((const void *)k_fft4_forward1<L, W, XT>, kFourT, sm1);
   if (e == cudaSuccess) e = kernel_setup((const void *)k_fft4_forward2<L, W>, kFourT, sm2);
   if (e != cudaSuccess) return e;
-  k_fft4_forward1<L, W><<<dim3((unsigned)(ncx / W), L2), kFourT, sm1, s>>>(x, ip, (int)n, ncx, tw);
+  k_fft4_forward1<L, W, XT><<<dim3((unsigned)(ncx / W), L2), kFourT, sm1, s>>>(x, ip, (int)n, ncx, tw);
   note_launch();
   k_fft4_forward2<L, W><<<dim3((unsigned)(ncx / W), L1 / 2 + 1), kFourT, sm2, s>>>(
       ip, spec, (int)n, ncx, n_pad, tw, four_discard_ok(ip, spec, n_pad) ? 1 : 0);
