@@ -612,9 +612,9 @@ def run_gpu(args):
                      for k, v in prof.items() if v[1]}
     # The dominant kernel is the one with the largest total time in the ncu
     # launch list of the timed region (profiles/launches_bench_timed_region_*):
-    # the fixed-point matvec with fused dots (DK = 0), ahead of the circulant
-    # residual of the refined apply.  (The profiling classes group several
-    # kernels, so a class total is not one kernel.)
+    # the fixed-point matvec with the second Arnoldi step's dots fused
+    # (DK = 1).  (The profiling classes group several kernels, so a class
+    # total is not one kernel.)
     dom = "matvec_dots"
     sm_mhz = clk.get("sm_mhz") or 2070.0
 
@@ -625,13 +625,14 @@ def run_gpu(args):
                     "peak_kind": peak_kind}
     elif dom == "matvec_dots":
         # The largest single kernel of the timed region (launch list in
-        # profiles/): the fixed-point matvec with its dots fused,
-        # k_matvec_fx<..., DK = 0> (Arnoldi step 0, w = A z - b, and the
-        # true residual r = A x - b with ||r||^2).  Timed here through
-        # aao_residual with the library's per-class CUDA events (kernel plus
-        # the 5 us fixed-order finish of its block partials).  Integer-ALU
-        # bound: 64 ALU lanes per clock per SM; achieved = ALU-pipe
-        # instructions per launch (ncu, committed summary) / event time.
+        # profiles/): the fixed-point matvec with its Arnoldi dots fused for
+        # the second step, k_matvec_fx<..., DK = 1> (w = A z_1 - v_1 with
+        # v_0 . w, v_1 . w, w . w).  Timed here through aao_matvec_dots with
+        # the library's per-class CUDA events (kernel plus the 5 us
+        # fixed-order finish of its block partials).  Integer-ALU bound: 64
+        # ALU lanes per clock per SM; achieved = ALU-pipe instructions per
+        # launch (ncu, committed summary) / event time.
+        v0 = torch.randn_like(xs[0])
         solver.profile_read(reset=True)
         solver.profile(True)
         nres = 20
@@ -639,18 +640,19 @@ def run_gpu(args):
             flush.fill_(float(k))
             if k == 3:
                 solver.profile_read(reset=True)
-            solver.residual(xs[0], xs[1], out=ys[0])
+            solver.matvec_dots(xs[0], xs[1], v0, out=ys[0])
         torch.cuda.synchronize()
         rp = solver.profile_read(reset=True)
         solver.profile(False)
+        del v0
         mv_s = rp["matvec"][0] * 1e-3 / nres
-        key = "matvec_dots0_double"
+        key = "matvec_dots1_double"
         alu = _profile_value("alu_inst_per_launch", key)
         alu_peak = 152 * 64 * sm_mhz * 1e6 / 1e9                 # Gop/s
-        mv_bytes = Nel * (8 + 8 + 8)                              # x, b, r
+        mv_bytes = Nel * (8 + 8 + 8 + 8)                          # z, v, v0, w
         achieved = alu / mv_s / 1e9 if alu else None
         roofline = {"bound": "alu",
-                    "kernel": "matvec_dots0: r = A x - b with r.r fused, fixed point",
+                    "kernel": "matvec_dots1: w = A z - v with v0.w, v.w, w.w fused, fixed point",
                     "achieved": round(achieved, 1) if achieved else None,
                     "peak": round(alu_peak, 1), "unit": "Gop/s",
                     "frac": round(achieved / alu_peak, 4) if achieved else None,

@@ -210,6 +210,16 @@ int aao_matvec_sub(aao_ctx *ctx, const double *x, const double *sub, double *y, 
 int aao_matvec_f32(aao_ctx *ctx, const float *x, const double *sub, double *y, int transpose,
                    void *stream);
 
+/* w = A x - v (or A^T x - v) with the Arnoldi dots of w in the same pass
+ * (Section 2's matvec as the shifted Arnoldi step forms it): dots[0] = v0 . w
+ * (when v0 is not NULL), then v . w and w . w.  Fixed-point stencil as
+ * aao_matvec; block and grid sums in a fixed order (deterministic).  Not for
+ * the literal heat form (AAO_EUNSUPPORTED).  x, v, v0, w: device, N
+ * doubles, w overlaps none of them; dots: host, 3 doubles (2 without v0),
+ * written before return (synchronises `stream`).  Needs the workspace. */
+int aao_matvec_dots(aao_ctx *ctx, const double *x, const double *v, const double *v0, double *w,
+                    int transpose, double *dots, void *stream);
+
 /* r = A x - b (or A^T x - b) and its squared norm, in one pass: the true
  * residual the solves check at every restart (Section 2).  The matvec is
  * the fixed-point stencil of aao_matvec; each thread accumulates r . r (and

@@ -182,6 +182,20 @@ class AllAtOnce:
               "aao_matvec_f32", self._ctx)
         return y
 
+    def matvec_dots(self, x, v, v0=None, transpose=False, out=None, stream=None):
+        """w = A x - v (or A^T x - v) and its Arnoldi dots in one pass:
+        returns (w, [v0 . w,] v . w, w . w) (synchronises)."""
+        self.ensure_workspace(self._restart)
+        x = _dev_f64(x, self.N, "x")
+        v = _dev_f64(v, self.N, "v")
+        v0p = _dev_f64(v0, self.N, "v0").data_ptr() if v0 is not None else None
+        w = self._out(out)
+        d = (C.c_double * 3)()
+        check(self.lib.aao_matvec_dots(self._ctx, x.data_ptr(), v.data_ptr(), v0p, w.data_ptr(),
+                                       int(bool(transpose)), d, _stream(stream)),
+              "aao_matvec_dots", self._ctx)
+        return w, [d[q] for q in range(3 if v0 is not None else 2)]
+
     def residual(self, x, b, transpose=False, out=None, stream=None):
         """r = A x - b (or A^T x - b) and ||r||^2 in one pass (synchronises)."""
         self.ensure_workspace(self._restart)

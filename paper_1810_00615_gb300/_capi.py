@@ -57,6 +57,8 @@ SIGNATURES = {
                                              C.c_int, C.c_void_p]),
     "aao_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                C.POINTER(C.c_double), C.c_void_p]),
+    "aao_matvec_dots": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "aao_build_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "aao_gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                   C.c_int, C.c_int, C.POINTER(SolveInfo), C.c_void_p]),

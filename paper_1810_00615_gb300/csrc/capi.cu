@@ -1203,6 +1203,30 @@ int aao_matvec_f32(aao_ctx *ctx, const float *x, const double *sub, double *y, i
   return AAO_OK;
 }
 
+int aao_matvec_dots(aao_ctx *ctx, const double *x, const double *v, const double *v0, double *w,
+                    int transpose, double *dots, void *stream) {
+  if (!ctx || !x || !v || !w || !dots) return AAO_EINVAL;
+  Ctx &c = ctx->c;
+  if (c.equation == AAO_HEAT_LITERAL) return AAO_EUNSUPPORTED;
+  const size_t vb = (size_t)c.N * sizeof(double);
+  if (overlap(x, w, vb) || overlap(v, w, vb) || (v0 && overlap(v0, w, vb))) return AAO_EINVAL;
+  if (check_ws(c, 0) != AAO_OK) return AAO_EINVAL;
+  const aao::WsLayout L = aao::ws_layout(c, 0);
+  double *red = reinterpret_cast<double *>(c.ws + L.red);
+  double *dpart = reinterpret_cast<double *>(c.ws + L.dots);
+  double *out = red + kPartials + 972;   // 3 doubles of the small-result area
+  cudaStream_t s = as_stream(stream);
+  const int nd = v0 ? 3 : 2;
+  AAO_CK(c, run(c, AAO_K_MATVEC, s, [&] {
+    return aao::launch_matvec_dots(c, x, w, transpose ? 1 : 0, s, v, v0, dpart, out);
+  }));
+  AAO_CK(c, cudaMemcpyAsync(c.host_small + 972, out, nd * sizeof(double), cudaMemcpyDeviceToHost,
+                            s));
+  AAO_CK(c, cudaStreamSynchronize(s));
+  for (int q = 0; q < nd; q++) dots[q] = c.host_small[972 + q];
+  return AAO_OK;
+}
+
 int aao_residual(aao_ctx *ctx, const double *x, const double *b, double *r, int transpose,
                  double *norm2, void *stream) {
   if (!ctx || !x || !b || !r || !norm2) return AAO_EINVAL;

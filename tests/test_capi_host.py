@@ -66,6 +66,7 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.aao_set_space_solver(None, K.AAO_SPACE_DST) == K.AAO_EINVAL
     assert lib.aao_circulant_residual_f32(None, None, None, None, 0, None) == K.AAO_EINVAL
     assert lib.aao_residual(None, None, None, None, 0, None, None) == K.AAO_EINVAL
+    assert lib.aao_matvec_dots(None, None, None, None, None, 0, None, None) == K.AAO_EINVAL
     assert lib.aao_set_initial_guess(None, 0) == K.AAO_EINVAL
     assert lib.aao_workspace_bytes(None, 30) == 0
     lib.aao_destroy(None)

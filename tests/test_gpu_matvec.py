@@ -102,3 +102,29 @@ def test_residual_and_fused_norm(kind, transpose, n, ell):
     assert rel_max(to_host(r), want) <= 1e-13
     ref = float(np.sum(want * want))
     assert abs(nrm2 - ref) <= 1e-12 * ref
+
+
+@pytest.mark.parametrize("kind", ["heat", "wave_bd2", "wave_bd4", "steps"])
+@pytest.mark.parametrize("transpose", [False, True])
+@pytest.mark.parametrize("with_v0", [False, True])
+def test_matvec_dots(kind, transpose, with_v0):
+    """aao_matvec_dots: w = A x - v with [v0 . w,] v . w, w . w from the same
+    pass, against the oracle's A x - v and numpy's dots of it."""
+    torch = need_gpu()
+    from paper_1810_00615_gb300 import AllAtOnce
+    n, ell = 130, 64
+    taus = syn.time_steps(ell, 0.6, syn.rng(ell)) if kind == "steps" else None
+    S = oracle_system("heat" if kind == "steps" else kind, n, ell, kappa=1.0, taus=taus)
+    a = AllAtOnce(n, ell, 1.0 / ell, equation="heat" if kind == "steps" else kind, restart=1)
+    if taus is not None:
+        a.set_steps(taus)
+    X, V, V0 = rand_block(n, ell, 21), rand_block(n, ell, 22), rand_block(n, ell, 23)
+    want = (system.matvec_T(S, X) if transpose else system.matvec(S, X)) - V
+    w, d = a.matvec_dots(to_dev(torch, X), to_dev(torch, V),
+                         to_dev(torch, V0) if with_v0 else None, transpose=transpose)
+    assert rel_max(to_host(w), want) <= 1e-13
+    ref = ([float(np.sum(V0 * want))] if with_v0 else []) + [float(np.sum(V * want)),
+                                                              float(np.sum(want * want))]
+    scale = float(np.sqrt(np.sum(want * want)) * max(np.sqrt(np.sum(V * V)), np.sqrt(np.sum(V0 * V0))))
+    for got, r in zip(d, ref):
+        assert abs(got - r) <= 1e-12 * max(scale, abs(r))
