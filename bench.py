@@ -752,7 +752,7 @@ def run_gpu(args):
                               "bytes": bytes_apply, "peak_GB_s": hbm_peak,
                               "peak_kind": peak_kind, "kernels": per_kernel},
             "precond_apply_refined": {"us": round(1e3 * refined_ms, 2),
-                                      "note": "FP32 apply, exact circulant residual, FP32 "
+                                      "note": "FP32 apply, compensated FP32 circulant residual, FP32 "
                                               "correction; FP64 output"},
             "kernel_share": shares, "solve_kernels": solve_kernels, "roofline": roofline,
             "cpu_baseline": cpu,

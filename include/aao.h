@@ -117,9 +117,11 @@ int aao_set_steps(aao_ctx *ctx, const double *tau_steps_host);
 
 /* Precision of the preconditioner apply: AAO_PREC_FP64 (FFTs and solves in
  * FP64), AAO_PREC_FP32 (in FP32), or AAO_PREC_FP32_REFINED: the FP32 apply
- * followed by one refinement sweep z = z0 - P^{-1}(P z0 - x), where P z0 is
- * formed exactly (fixed point, or FP64 for the literal heat form) and the
- * correction applied in FP32 again.  The refined apply is as accurate as the
+ * followed by one refinement sweep z = z0 - P^{-1}(P z0 - x), where the
+ * residual P z0 - x is formed in compensated FP32 arithmetic (exact FMA
+ * products, Sum2 summation: FP32 accuracy relative to the residual itself,
+ * which is all the FP32 apply of the correction uses) and the correction
+ * applied in FP32 again.  The refined apply is as accurate as the
  * product of two FP32 errors (about 1e-9 relative where FP32 alone gives
  * 3e-7), so FGMRES needs the iterations of the FP64 preconditioner at about
  * twice the cost of an FP32 apply.  The paper has no counterpart: it is a
