@@ -268,8 +268,11 @@ __device__ __forceinline__ void dots_commit(double (&acc)[ND], double (*s_dot)[N
 //   DK = 0: v . w, w . w
 //   DK = 1: v0 . w, v . w, w . w
 //   DK = 2: v . w, w . w, v . v   (the first step from x0 = 0, v = b: ||b||^2)
+#ifndef AAO_MVFX_DOTS_MINB
+#define AAO_MVFX_DOTS_MINB 8   // fused-dots variants: 64 registers, no spills
+#endif
 template <int NB, bool TR, bool SUB, typename XT, bool CIRC, int DK = -1>
-__global__ void __launch_bounds__(kMvCols, AAO_MVFX_MINB)
+__global__ void __launch_bounds__(kMvCols, DK >= 0 ? AAO_MVFX_DOTS_MINB : AAO_MVFX_MINB)
 k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
             const MvRow *__restrict__ rows, const double *__restrict__ sub,
             const double *__restrict__ dv0 = nullptr, double *__restrict__ dpart = nullptr) {
