@@ -43,6 +43,8 @@ HEADLINE_PREC = "fp32_refined"
 PREC_LABEL = {"fp32_refined": "fp32 circulant + one refinement sweep",
               "fp32": "fp32 circulant", "fp64": "fp64 circulant"}
 L2_BYTES = 135528448
+# ncu summary key of the dominant kernel (the roofline line)
+ROOFLINE_KEY = "matvec_dots1_double"
 
 
 def _peaks():
@@ -612,96 +614,46 @@ def run_gpu(args):
                      for k, v in prof.items() if v[1]}
     # The dominant kernel is the one with the largest total time in the ncu
     # launch list of the timed region (profiles/launches_bench_timed_region_*):
-    # the fixed-point matvec with the second Arnoldi step's dots fused
-    # (DK = 1).  (The profiling classes group several kernels, so a class
-    # total is not one kernel.)
-    dom = "matvec_dots"
+    # the fixed-point matvec with the second Arnoldi step's dots fused,
+    # k_matvec_fx<..., DK = 1> (w = A z_1 - v_1 with v_0 . w, v_1 . w, w . w).
+    # (The profiling classes group several kernels, so a class total is not
+    # one kernel.)  It is timed here through aao_matvec_dots with the
+    # library's per-class CUDA events (kernel plus the 5 us fixed-order finish
+    # of its block partials).  Integer-ALU bound: 64 ALU lanes per clock per
+    # SM; achieved = ALU-pipe instructions per launch (ncu, committed summary)
+    # / event time.
     sm_mhz = clk.get("sm_mhz") or 2070.0
-
-    if dom in per_kernel:
-        pk = per_kernel[dom]
-        roofline = {"bound": "hbm", "kernel": dom, "achieved": pk["GB_s"], "peak": hbm_peak,
-                    "unit": "GB/s", "frac": pk["frac"], "traffic": _traffic(dom),
-                    "peak_kind": peak_kind}
-    elif dom == "matvec_dots":
-        # The largest single kernel of the timed region (launch list in
-        # profiles/): the fixed-point matvec with its Arnoldi dots fused for
-        # the second step, k_matvec_fx<..., DK = 1> (w = A z_1 - v_1 with
-        # v_0 . w, v_1 . w, w . w).  Timed here through aao_matvec_dots with
-        # the library's per-class CUDA events (kernel plus the 5 us
-        # fixed-order finish of its block partials).  Integer-ALU bound: 64
-        # ALU lanes per clock per SM; achieved = ALU-pipe instructions per
-        # launch (ncu, committed summary) / event time.
-        v0 = torch.randn_like(xs[0])
-        solver.profile_read(reset=True)
-        solver.profile(True)
-        nres = 20
-        for k in range(nres + 3):
-            flush.fill_(float(k))
-            if k == 3:
-                solver.profile_read(reset=True)
-            solver.matvec_dots(xs[0], xs[1], v0, out=ys[0])
-        torch.cuda.synchronize()
-        rp = solver.profile_read(reset=True)
-        solver.profile(False)
-        del v0
-        mv_s = rp["matvec"][0] * 1e-3 / nres
-        key = "matvec_dots1_double"
-        alu = _profile_value("alu_inst_per_launch", key)
-        alu_peak = 152 * 64 * sm_mhz * 1e6 / 1e9                 # Gop/s
-        mv_bytes = Nel * (8 + 8 + 8 + 8)                          # z, v, v0, w
-        achieved = alu / mv_s / 1e9 if alu else None
-        roofline = {"bound": "alu",
-                    "kernel": "matvec_dots1: w = A z - v with v0.w, v.w, w.w fused, fixed point",
-                    "achieved": round(achieved, 1) if achieved else None,
-                    "peak": round(alu_peak, 1), "unit": "Gop/s",
-                    "frac": round(achieved / alu_peak, 4) if achieved else None,
-                    "traffic": _traffic(key), "us": round(mv_s * 1e6, 1),
-                    "algorithmic_bytes": mv_bytes,
-                    "hbm_GB_s": round(mv_bytes / mv_s / 1e9, 1),
-                    "hbm_frac": round(mv_bytes / mv_s / 1e9 / hbm_peak, 3),
-                    "note": "integer ALU pipe bound; peak = 152 SMs x 64 ALU lanes/clk x "
-                            "sampled SM clock; achieved = ncu ALU-pipe instructions per "
-                            "launch / event time (kernel + partials finish)"}
-    elif dom == "refine":
-        # The largest single kernel of the timed region (launch list in
-        # profiles/): the fixed-point circulant residual r = P z0 - x of the
-        # refined preconditioner, twice per solve.  Integer-ALU bound: the
-        # GB300 ALU pipe issues 64 lanes per clock per SM; achieved = ALU-pipe
-        # instructions per launch (ncu, committed summary) / event time here.
-        z = xs[0].float()
-        ts = []
-        for k in range(23):
-            flush.fill_(float(k))
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            solver.circulant_residual_f32(z, xs[1], out=ys[0])
-            a1.record(stream)
-            torch.cuda.synchronize()
-            if k >= 3:
-                ts.append(a0.elapsed_time(a1) * 1e-3)
-        mv_s = float(np.median(ts))
-        key = "circ_residual"
-        alu = _profile_value("alu_inst_per_launch", key)
-        alu_peak = 152 * 64 * sm_mhz * 1e6 / 1e9                 # Gop/s
-        mv_bytes = Nel * (4 + 8 + 8)                              # z (FP32), x, r
-        achieved = alu / mv_s / 1e9 if alu else None
-        roofline = {"bound": "alu",
-                    "kernel": "circ_residual: r = P z0 - x, fixed point (refined apply)",
-                    "achieved": round(achieved, 1) if achieved else None,
-                    "peak": round(alu_peak, 1), "unit": "Gop/s",
-                    "frac": round(achieved / alu_peak, 4) if achieved else None,
-                    "traffic": _traffic(key), "us": round(mv_s * 1e6, 1),
-                    "algorithmic_bytes": mv_bytes,
-                    "hbm_GB_s": round(mv_bytes / mv_s / 1e9, 1),
-                    "hbm_frac": round(mv_bytes / mv_s / 1e9 / hbm_peak, 3),
-                    "note": "integer ALU pipe bound; peak = 152 SMs x 64 ALU lanes/clk x "
-                            "sampled SM clock; achieved = ncu ALU-pipe instructions per "
-                            "launch / event time"}
-    else:
-        roofline = {"bound": "alu", "kernel": dom, "achieved": None, "peak": None,
-                    "unit": "TFLOP/s", "frac": None, "traffic": _traffic(dom),
-                    "note": "FP64 pipe bound Arnoldi kernel"}
+    v0 = torch.randn_like(xs[0])
+    solver.profile_read(reset=True)
+    solver.profile(True)
+    nres = 20
+    for k in range(nres + 3):
+        flush.fill_(float(k))
+        if k == 3:
+            solver.profile_read(reset=True)
+        solver.matvec_dots(xs[0], xs[1], v0, out=ys[0])
+    torch.cuda.synchronize()
+    rp = solver.profile_read(reset=True)
+    solver.profile(False)
+    del v0
+    mv_s = rp["matvec"][0] * 1e-3 / nres
+    key = ROOFLINE_KEY
+    alu = _profile_value("alu_inst_per_launch", key)
+    alu_peak = 152 * 64 * sm_mhz * 1e6 / 1e9                 # Gop/s
+    mv_bytes = Nel * (8 + 8 + 8 + 8)                          # z, v, v0, w
+    achieved = alu / mv_s / 1e9 if alu else None
+    roofline = {"bound": "alu",
+                "kernel": "matvec_dots1: w = A z - v with v0.w, v.w, w.w fused, fixed point",
+                "achieved": round(achieved, 1) if achieved else None,
+                "peak": round(alu_peak, 1), "unit": "Gop/s",
+                "frac": round(achieved / alu_peak, 4) if achieved else None,
+                "traffic": _traffic(key), "us": round(mv_s * 1e6, 1),
+                "algorithmic_bytes": mv_bytes,
+                "hbm_GB_s": round(mv_bytes / mv_s / 1e9, 1),
+                "hbm_frac": round(mv_bytes / mv_s / 1e9 / hbm_peak, 3),
+                "note": "integer ALU pipe bound; peak = 152 SMs x 64 ALU lanes/clk x "
+                        "sampled SM clock; achieved = ncu ALU-pipe instructions per "
+                        "launch / event time (kernel + partials finish)"}
 
     # ---- end to end through the C ABI with host buffers (u0 in, U out)
     u0_h = torch.from_numpy(u0).pin_memory()
@@ -757,7 +709,8 @@ def run_gpu(args):
             "kernel_share": shares, "solve_kernels": solve_kernels, "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_v, "unit": "s", "h2d_bytes_per_step": 8 * N_SPACE,
-                    "d2h_bytes_per_step": 8 * Nel},
+                    "d2h_bytes_per_step": 8 * Nel, "iters": inf_h["iters"],
+                    "relres_true": inf_h["relres_true"]},
             "gpu_launches": launches, "wall_s": wall, "clocks": clk,
             "rows": extra,
         }
