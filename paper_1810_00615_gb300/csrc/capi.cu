@@ -806,6 +806,7 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
     g[0] = beta;
     int jd = 0;
     bool numeric_fail = false;
+    double e_prev = relres_true, e_prev2 = 0.0;   // the last two residual estimates
     for (int j = 0; j < m; j++) {
       if (zf) {
         if (precond == 1)
@@ -840,34 +841,11 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
         }));
       }
       for (int i = 0; i < nv; i++) sc2[(size_t)i] = sc[(size_t)i] * sc[(size_t)i];
-      // deferred ||b||: the projection on V_0 = b divides by b . b on the
-      // device (d_h1[2]), so the update needs no round trip to the host
-      AAO_CK(c, run(c, AAO_K_UPDATE, s, [&] {
-        return aao::launch_update_dots(V.data(), nv, d_h1, w, N, false, red, d_nr, s, sc2.data(),
-                                       defer_b ? d_h1 + 2 : nullptr);
-      }));
-      AAO_CK(c, fetch(d_h1, defer_b ? 3 : nv + 1));
-      AAO_CK(c, fetch(d_nr + nv, 1));
-      AAO_CK(c, cudaStreamSynchronize(s));
-      if (defer_b) {
-        bnorm = std::sqrt(hs[2]);
-        if (!std::isfinite(bnorm)) return AAO_ENUMERIC;
-        if (bnorm == 0.0) return zero_answer();
-        defer_b = false;
-        beta = bnorm;
-        sc[0] = 1.0 / beta;
-        sc2[0] = sc[0] * sc[0];   // for a second Gram-Schmidt pass
-        g[0] = beta;
-        relres_true = 1.0;
-        best = 1.0;
-      }
-      const double before = hs[nv];          // ||w~||^2 before the projection (unscaled)
-      double after = hs[320 + nv];           // after
-      for (int i = 0; i < nv; i++) Hij(i, j) = sc[(size_t)i] * sc[(size_t)j] * hs[i];
-      // The residual estimate this column would give as it stands: the second
-      // Gram-Schmidt pass only matters if the iteration continues, so it is
-      // skipped when this step already meets the tolerance (the true residual
-      // is checked before returning in any case).
+      // The residual estimate this column would give with ||w~ - V h||^2 =
+      // after_sq (Hij(0..j, j) set).  The second Gram-Schmidt pass only
+      // matters if the iteration continues, so it is skipped when this step
+      // already meets the tolerance (the true residual is checked before
+      // returning in any case).
       auto trial_est = [&](double after_sq) {
         std::vector<double> col((size_t)j + 2);
         for (int i = 0; i <= j; i++) col[(size_t)i] = Hij(i, j);
@@ -882,7 +860,62 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
         const double snj = (rr == 0.0) ? 0.0 : col[(size_t)j + 1] / rr;
         return std::fabs(snj * g[(size_t)j]) / bnorm;
       };
-      const bool last_step = trial_est(after) <= rtol || iters + 1 >= maxit || j + 1 == m;
+      // Where the last two estimates extrapolate to (near) convergence at this
+      // step, the dots are read before the projection pass.  For an
+      // orthonormal basis the projected norm is ||w~||^2 - sum_i sc_i^2 d_i^2,
+      // exact up to a rounding error of a few ulps of ||w~||^2 (bounded here
+      // by 1e-14 ||w~||^2 and added, so the test is conservative).  If that
+      // bound already meets the tolerance, this is the cycle's last step,
+      // v_{j+1} is never used, and the pass is skipped; the bound then stands
+      // for h_{j+1,j}, whose exact value barely moves y at convergence
+      // (h_{j+1,j} << h_{j,j}).
+      const bool decide_first =
+          j >= 1 && e_prev2 > 0.0 && e_prev * e_prev <= 1e4 * rtol * e_prev2;
+      bool skipped = false;
+      double before = 0.0, after = 0.0;   // ||w~||^2 before / after the projection (unscaled)
+      if (decide_first) {
+        AAO_CK(c, fetch(d_h1, nv + 1));
+        AAO_CK(c, cudaStreamSynchronize(s));
+        before = hs[nv];
+        double proj = 0.0;
+        for (int i = 0; i < nv; i++) proj += sc2[(size_t)i] * hs[i] * hs[i];
+        const double err = 1e-14 * before;
+        const double after_f = before - proj;
+        for (int i = 0; i < nv; i++) Hij(i, j) = sc[(size_t)i] * sc[(size_t)j] * hs[i];
+        if (std::isfinite(after_f) && after_f >= -err && trial_est(after_f + err) <= rtol) {
+          skipped = true;
+          after = after_f + err;
+        }
+      }
+      if (!skipped) {
+        // deferred ||b||: the projection on V_0 = b divides by b . b on the
+        // device (d_h1[2]), so the update needs no round trip to the host
+        AAO_CK(c, run(c, AAO_K_UPDATE, s, [&] {
+          return aao::launch_update_dots(V.data(), nv, d_h1, w, N, false, red, d_nr, s,
+                                         sc2.data(), defer_b ? d_h1 + 2 : nullptr);
+        }));
+        AAO_CK(c, fetch(d_h1, defer_b ? 3 : nv + 1));
+        AAO_CK(c, fetch(d_nr + nv, 1));
+        AAO_CK(c, cudaStreamSynchronize(s));
+        if (defer_b) {
+          bnorm = std::sqrt(hs[2]);
+          if (!std::isfinite(bnorm)) return AAO_ENUMERIC;
+          if (bnorm == 0.0) return zero_answer();
+          defer_b = false;
+          beta = bnorm;
+          sc[0] = 1.0 / beta;
+          sc2[0] = sc[0] * sc[0];   // for a second Gram-Schmidt pass
+          g[0] = beta;
+          relres_true = 1.0;
+          best = 1.0;
+          e_prev = 1.0;
+        }
+        before = hs[nv];
+        after = hs[320 + nv];
+        for (int i = 0; i < nv; i++) Hij(i, j) = sc[(size_t)i] * sc[(size_t)j] * hs[i];
+      }
+      const bool last_step =
+          skipped || trial_est(after) <= rtol || iters + 1 >= maxit || j + 1 == m;
       if (after < 0.5 * before && !last_step) {
         // DGKS: lost more than half the norm, orthogonalise once more
         AAO_CK(c, run(c, AAO_K_DOTS, s, [&] {
@@ -909,7 +942,7 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
       // P, e.g. R_BD4), scale the stored vector to unit norm: the squared
       // norms must stay finite and the FP32 preconditioner must see its input
       // inside the FP32 range.
-      if (!breakdown) {
+      if (!breakdown && !skipped) {
         const double sa = std::fabs(sc[(size_t)j + 1]);
         if (sa > 0x1p60 || sa < 0x1p-60) {
           double *d_s = small + 950;
@@ -937,9 +970,11 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
       iters++;
       jd = j + 1;
       est = std::fabs(g[(size_t)j + 1]) / bnorm;
+      e_prev2 = e_prev;
+      e_prev = est;
       if (info && info->history && info->history_len < info->history_cap)
         info->history[info->history_len++] = est;
-      if (est <= rtol || iters >= maxit || breakdown) break;
+      if (skipped || est <= rtol || iters >= maxit || breakdown) break;
     }
     if (numeric_fail) { status = AAO_ENUMERIC; break; }
     // y = R^{-1} g, then x += Z y
