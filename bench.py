@@ -164,6 +164,25 @@ def _oracle_solve_seconds():
     return time.perf_counter() - t0, info
 
 
+def _cpu_references():
+    """More host-core references for the same workload (rank 0, N = 1): the
+    oracle's forward substitution (exact time stepping on one core, the
+    sequential method an all-at-once solve competes with) and a
+    multithreaded FFT + Thomas FGMRES in plain C with OpenMP
+    (oracle/cbaseline.c).  They run in a child process with a time limit,
+    so their OpenMP runtime never shares this process; a failure there is
+    reported in the line, not raised."""
+    cmd = [sys.executable, "-m", "oracle.cbaseline", "--n", str(N_SPACE), "--ell", str(ELL),
+           "--restart", str(RESTART), "--rtol", str(RTOL), "--reps", "3"]
+    try:
+        r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+        if r.returncode != 0:
+            return {"error": f"exit {r.returncode}: {r.stderr.strip()[-300:]}"}
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:  # noqa: BLE001 - a reference that fails must not end the bench
+        return {"error": repr(e)[:300]}
+
+
 def _blas_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -679,11 +698,13 @@ def run_gpu(args):
 
     # ---- CPU oracle on the host cores (rank 0, N = 1 only)
     cpu = None
+    cpu_refs = None
     if rank == 0 and world == 1 and not args.no_cpu:
         dt, cinfo = _oracle_solve_seconds()
         cpu = {"value": dt, "unit": "s", "cores": _blas_threads(), "kind": "oracle",
                "sample": "one full solve of the same workload: oracle right-preconditioned "
                          f"GMRES(30), dense-DFT circulant, FP64 ({cinfo.iters} iterations)"}
+        cpu_refs = _cpu_references()
 
     if rank == 0:
         line = {
@@ -708,6 +729,7 @@ def run_gpu(args):
                                               "correction; FP64 output"},
             "kernel_share": shares, "solve_kernels": solve_kernels, "roofline": roofline,
             "cpu_baseline": cpu,
+            "cpu_references": cpu_refs,
             "e2e": {"value": e2e_v, "unit": "s", "h2d_bytes_per_step": 8 * N_SPACE,
                     "d2h_bytes_per_step": 8 * Nel, "iters": inf_h["iters"],
                     "relres_true": inf_h["relres_true"]},

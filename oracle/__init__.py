@@ -23,6 +23,12 @@ Contents (each function cites the passage it follows):
                (flexible) preconditioned.
 * ``adjoint``  the loss 1/2||U - U_obs||^2 and its gradients with respect to
                u0 and the diffusion coefficient by the adjoint system.
+* ``cbaseline`` a multithreaded C baseline of the heat solve (radix-2 FFT
+               along time, Thomas per frequency, GMRES; OpenMP) that the
+               benchmark times on the host cores beside the GPU solve.  It
+               is not an oracle: ``tests/test_oracle_cbaseline.py`` checks it
+               against the functions above.  It is imported on demand, not
+               here.
 
 Readings of the paper where it is silent or garbled (all stated again where
 they are used):
@@ -37,7 +43,7 @@ they are used):
 * sigma_t = tau_t - tau for t = 1..ell with tau = T/ell.
 
 Parity pins: every function is checked in ``tests/test_oracle_pins.py``
-against closed forms, brute-force dense algebra or invariants.  The one
-function with no such pin is marked "parity unpinned" in its docstring.
+against closed forms, brute-force dense algebra or invariants; none is
+without such a pin.
 """
 from . import fem, system, precond, gmres, adjoint  # noqa: F401
