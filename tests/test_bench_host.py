@@ -82,3 +82,29 @@ def test_reference_arm_is_silent_on_other_ranks(monkeypatch):
     with redirect_stdout(out):
         assert bench.run_reference(args) == 0
     assert out.getvalue() == ""
+
+
+def test_reference_arm_prints_one_contract_line(monkeypatch):
+    """Rank 0 of the reference arm times the oracle solve (here on a tiny
+    workload) and prints one JSON line with the contract's keys."""
+    import json
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    monkeypatch.setattr(bench, "N_SPACE", 31)
+    monkeypatch.setattr(bench, "ELL", 32)
+    args = argparse.Namespace(gpus=1, steps=3, warmup=3, impl="reference")
+    out = io.StringIO()
+    with redirect_stdout(out):
+        assert bench.run_reference(args) == 0
+    lines = [ln for ln in out.getvalue().splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["higher_is_better"] is False
+    assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["cpu_baseline"]["value"] == d["value"] == d["e2e"]["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["iters"] <= 2
