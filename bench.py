@@ -183,6 +183,21 @@ def _cpu_references():
         return {"error": repr(e)[:300]}
 
 
+def _solution_error(u0, U):
+    """max |U - U_ts| / max |U_ts| of a solution of the benchmark workload
+    against the oracle's exact time stepping U_ts (FP64, banded LU per
+    step); reported, never raised."""
+    try:
+        from oracle import system
+        S = system.heat(N_SPACE, ELL, 1.0 / ELL)
+        ref = system.forward_substitution(S, system.rhs_heat(S, u0))
+        U = np.asarray(U, dtype=np.float64).reshape(ref.shape)
+        return {"rel_max_err": float(np.max(np.abs(U - ref)) / np.max(np.abs(ref))),
+                "bound": 1e-8}
+    except Exception as e:  # noqa: BLE001 - a failing check must not end the bench
+        return {"error": repr(e)[:300]}
+
+
 def _blas_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -705,6 +720,7 @@ def run_gpu(args):
                "sample": "one full solve of the same workload: oracle right-preconditioned "
                          f"GMRES(30), dense-DFT circulant, FP64 ({cinfo.iters} iterations)"}
         cpu_refs = _cpu_references()
+        cpu_refs["gpu_solution_vs_time_stepping"] = _solution_error(u0, U_h.numpy())
 
     if rank == 0:
         line = {

@@ -108,3 +108,17 @@ def test_reference_arm_prints_one_contract_line(monkeypatch):
     assert d["cpu_baseline"]["value"] == d["value"] == d["e2e"]["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["iters"] <= 2
+
+
+def test_solution_error_against_time_stepping(monkeypatch):
+    import synthetic as syn
+    from oracle import system
+    monkeypatch.setattr(bench, "N_SPACE", 31)
+    monkeypatch.setattr(bench, "ELL", 16)
+    u0 = syn.heat_initial(31, modes=8)
+    S = system.heat(31, 16, 1.0 / 16)
+    U = system.forward_substitution(S, system.rhs_heat(S, u0))
+    assert bench._solution_error(u0, U)["rel_max_err"] == 0.0
+    got = bench._solution_error(u0, U * (1 + 1e-9))
+    assert 0.5e-9 <= got["rel_max_err"] <= 2e-9
+    assert "error" in bench._solution_error(u0, U[:3])       # wrong shape: reported
