@@ -5,6 +5,7 @@ work on ranks other than 0."""
 import argparse
 import io
 import os
+import tempfile
 from contextlib import redirect_stdout
 
 import pytest
@@ -34,37 +35,40 @@ class _FakeProc:
         return 0
 
 
-def _sampler_with(tmp_path, lines):
-    path = tmp_path / "clocks.csv"
-    path.write_text("".join(line + "\n" for line in lines))
+def _sampler_with(lines):
+    # a sample file beside this test; ClockSampler.stop() deletes it
+    fd, path = tempfile.mkstemp(suffix=".csv", dir=os.path.dirname(os.path.abspath(__file__)))
+    with os.fdopen(fd, "w") as f:
+        f.write("".join(line + "\n" for line in lines))
     s = bench.ClockSampler(0)
     s.proc = _FakeProc()
-    s.path = str(path)
+    s.path = path
     return s
 
 
-def test_clock_samples_give_median_and_reasons(tmp_path):
+def test_clock_samples_give_median_and_reasons():
     row = "0, {sm}, 2070, 900.1, 0x{act:x}, {hw}, Not Active, Not Active, {pc}"
     lines = [row.format(sm=sm, act=0, hw="Not Active", pc="Not Active")
              for sm in (2070, 2055, 2040)]
     lines.append(row.format(sm=1965, act=4, hw="Not Active", pc="Active"))
     lines.append("garbage line")
-    got = _sampler_with(tmp_path, lines).stop()
+    sampler = _sampler_with(lines)
+    got = sampler.stop()
     assert got["samples"] == 4
     assert got["sm_mhz"] == pytest.approx((2040 + 2055) / 2)
     assert got["sm_max_mhz"] == 2070
     assert got["reasons"] == ["sw_power_cap"]
-    assert not os.path.exists(tmp_path / "clocks.csv")
+    assert not os.path.exists(sampler.path)
 
 
-def test_clock_samples_flag_hardware_slowdown(tmp_path):
+def test_clock_samples_flag_hardware_slowdown():
     lines = ["0, 1500, 2070, 1300, 0x8, Active, Not Active, Active, Not Active"]
-    got = _sampler_with(tmp_path, lines).stop()
+    got = _sampler_with(lines).stop()
     assert got["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
 
 
-def test_clock_sampler_without_samples(tmp_path):
-    got = _sampler_with(tmp_path, []).stop()
+def test_clock_sampler_without_samples():
+    got = _sampler_with([]).stop()
     assert got["sm_mhz"] is None and got["reasons"] == ["no samples"]
     assert bench.ClockSampler(0).stop()["reasons"] == ["nvidia-smi unavailable"]
 
