@@ -23,7 +23,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -493,7 +492,6 @@ def run_gpu(args):
     import torch
     import synthetic as syn
     from paper_1810_00615_gb300 import AllAtOnce
-    from paper_1810_00615_gb300._capi import KERNEL_CLASSES
 
     world, rank, local = _dist_env()
     dist_on = world > 1

@@ -37,7 +37,6 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=1)
     a = ap.parse_args(argv)
 
-    import numpy as np
     import synthetic as syn
     from paper_1810_00615_gb300 import AllAtOnce
 

@@ -25,7 +25,7 @@ import pytest
 
 import synthetic as syn
 from oracle import precond
-from tests._helpers import EQ, need_gpu, oracle_system, rand_block, rel_max, to_dev, to_host
+from tests._helpers import need_gpu, oracle_system, rand_block, rel_max, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 

@@ -12,7 +12,6 @@ file is named so that pytest collects it last.
 """
 import ctypes as C
 
-import numpy as np
 import pytest
 
 from tests._helpers import need_gpu, rand_block, rel_max, to_dev, to_host
