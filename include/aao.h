@@ -92,7 +92,11 @@ typedef struct {
 /* Create a context for an n x ell all-at-once system with constant step tau
  * (Section 2; tau = T/ell with T = 1 in the paper).  ell = 2^a 3^b 5^c,
  * 1 <= ell <= 4096 (powers of two use radix-16 time FFTs, the other lengths,
- * e.g. the paper's 768 and 1440, mixed-radix ones); 1 <= n <= 16383.  Computes the per-frequency
+ * e.g. the paper's 768 and 1440, mixed-radix ones).  Any 1 <= n <= 16383;
+ * above that, where one frequency row is longer than one CTA can hold and is
+ * split over a thread-block cluster, n + 1 must be 16 P with P = 2048, 3072
+ * or 4096 chunks (n = 32767, 49151, 65535; other n give AAO_EUNSUPPORTED).
+ * Computes the per-frequency
  * tridiagonal symbols A0 + w_k A1 (+ w_k^2 A2), w_k = exp(-2 pi i k/ell),
  * k = 0..ell/2 (Section 3, Fourier diagonalisation of P), in FP64 on the
  * host and uploads them; the context owns that device memory.
@@ -337,6 +341,22 @@ int64_t aao_kernel_launches(const aao_ctx *ctx);
  *     mode this call returns AAO_EINVAL. */
 int aao_precond_apply_static(aao_ctx *ctx, const double *x, double *y, int transpose,
                              void *stream);
+
+/* Conversion self-test (not in the paper).  On this part the hardware
+ * FP64 <-> FP32 conversions issue at the FP64 rate, so the FP32
+ * preconditioner converts with integer bit operations instead (IEEE
+ * round-to-nearest-even for double -> float, exact widening for
+ * float -> double).  This call runs those conversions next to CUDA's own
+ * (__double2float_rn and the widening cast) so that a test can compare
+ * them bit for bit:
+ *   lib32[i] = library(x64[i]), ref32[i] = __double2float_rn(x64[i]), i < n64;
+ *   lib64[i] = library(x32[i]), ref64[i] = (double)x32[i],            i < n32.
+ * All arrays are device memory owned by the caller; asynchronous on
+ * `stream`.  AAO_EINVAL for negative sizes or a missing array, AAO_ECUDA
+ * if the launch fails.  No context is needed. */
+int aao_check_conversions(const double *x64, int64_t n64, float *lib32, float *ref32,
+                          const float *x32, int64_t n32, double *lib64, double *ref64,
+                          void *stream);
 
 /* Text for a status code, and the last CUDA error seen by ctx ("" if none). */
 const char *aao_strerror(int status);

@@ -75,6 +75,9 @@ SIGNATURES = {
     "aao_kernel_launches": (C.c_int64, [C.c_void_p]),
     "aao_precond_apply_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                            C.c_void_p]),
+    "aao_check_conversions": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                        C.c_void_p]),
     "aao_strerror": (C.c_char_p, [C.c_int]),
     "aao_last_error": (C.c_char_p, [C.c_void_p]),
 }

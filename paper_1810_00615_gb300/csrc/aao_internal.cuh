@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <stddef.h>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/aao.h"
@@ -368,6 +369,17 @@ struct WsLayout {
 };
 WsLayout ws_layout(const Ctx &c, int restart);
 
+// Run a launcher attributed to kernel class `cls` (AAO_K_*): its launches
+// are added to the context's counts and, while profiling is on, bracketed
+// by events on stream s.
+cudaError_t run_class_fn(Ctx &c, int cls, cudaStream_t s, cudaError_t (*f)(void *), void *arg);
+template <class F>
+cudaError_t run_class(Ctx &c, int cls, cudaStream_t s, F &&f) {
+  using Fn = typename std::remove_reference<F>::type;
+  return run_class_fn(c, cls, s, [](void *p) -> cudaError_t { return (*static_cast<Fn *>(p))(); },
+                      const_cast<void *>(static_cast<const void *>(&f)));
+}
+
 // Once per (kernel, device, block size, dynamic shared memory): opt the kernel
 // in to that much dynamic shared memory and count the CTAs the device holds
 // at once (SMs x resident CTAs per SM).  Later calls are a cached lookup, so
@@ -473,6 +485,11 @@ cudaError_t launch_scale(const double *x, double *y, const double *a, int64_t N,
 cudaError_t launch_sub_from(const double *b, double *r, int64_t N, cudaStream_t s);
 cudaError_t launch_adjoint_grads(const Ctx &c, const double *lam, const double *U,
                                  double *g_u0, double *partials, double *out,
+                                 cudaStream_t s);
+// Conversion self-test: to_f32 / to_f64 beside __double2float_rn and the
+// widening cast, element by element (device arrays).
+cudaError_t launch_convert_check(const double *x64, int64_t n64, float *lib32, float *ref32,
+                                 const float *x32, int64_t n32, double *lib64, double *ref64,
                                  cudaStream_t s);
 
 }  // namespace aao

@@ -1108,4 +1108,38 @@ cudaError_t launch_adjoint_grads(const Ctx &c, const double *lam, const double *
   return cudaGetLastError();
 }
 
+// The library's integer-built conversions next to CUDA's own, element by
+// element, for the conversion self-test.
+__global__ void __launch_bounds__(kThreads)
+k_convert_check(const double *__restrict__ x64, int64_t n64, float *__restrict__ lib32,
+                float *__restrict__ ref32, const float *__restrict__ x32, int64_t n32,
+                double *__restrict__ lib64, double *__restrict__ ref64) {
+  const int64_t m = n64 > n32 ? n64 : n32;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * kThreads) {
+    if (i < n64) {
+      const double v = x64[i];
+      lib32[i] = to_f32(v);
+      ref32[i] = __double2float_rn(v);
+    }
+    if (i < n32) {
+      const float f = x32[i];
+      lib64[i] = to_f64(f);
+      ref64[i] = (double)f;
+    }
+  }
+}
+
+cudaError_t launch_convert_check(const double *x64, int64_t n64, float *lib32, float *ref32,
+                                 const float *x32, int64_t n32, double *lib64, double *ref64,
+                                 cudaStream_t s) {
+  const int64_t m = n64 > n32 ? n64 : n32;
+  if (m <= 0) return cudaSuccess;
+  const int64_t nb = (m + kThreads - 1) / kThreads;
+  k_convert_check<<<(unsigned)(nb < 1024 ? nb : 1024), kThreads, 0, s>>>(x64, n64, lib32, ref32,
+                                                                          x32, n32, lib64, ref64);
+  note_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace aao

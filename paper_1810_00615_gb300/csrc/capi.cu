@@ -300,6 +300,17 @@ cudaError_t collect(Ctx &c) {
   return cudaSuccess;
 }
 
+}  // namespace
+
+namespace aao {
+cudaError_t run_class_fn(Ctx &c, int cls, cudaStream_t s, cudaError_t (*f)(void *), void *arg) {
+  if (cls < 0 || cls >= AAO_K_COUNT) return cudaErrorInvalidValue;
+  return run(c, cls, s, [&] { return f(arg); });
+}
+}  // namespace aao
+
+namespace {
+
 // Tables of the DST-in-space solver: the twiddles of the length-2(n+1)
 // transform, cM_k (k < nk) and (m_j, cK k_j) for the sine modes j = 1..n
 // with m_j = (h/6)(4 + 2 cos th) = h (1 - (2/3) sin^2(th/2)) and k_j =
@@ -1399,6 +1410,17 @@ int aao_solve_host(aao_ctx *ctx, const double *u0_host, const double *v0_host, d
   const int st = solve_core(c, 0, db, dx, restart, rtol, maxit, precond, info, s, U_host);
   c.guess = guess;
   return st;
+}
+
+int aao_check_conversions(const double *x64, int64_t n64, float *lib32, float *ref32,
+                          const float *x32, int64_t n32, double *lib64, double *ref64,
+                          void *stream) {
+  if (n64 < 0 || n32 < 0) return AAO_EINVAL;
+  if (n64 > 0 && (!x64 || !lib32 || !ref32)) return AAO_EINVAL;
+  if (n32 > 0 && (!x32 || !lib64 || !ref64)) return AAO_EINVAL;
+  const cudaError_t e = aao::launch_convert_check(x64, n64, lib32, ref32, x32, n32, lib64, ref64,
+                                                  as_stream(stream));
+  return e == cudaSuccess ? AAO_OK : AAO_ECUDA;
 }
 
 }  // extern "C"

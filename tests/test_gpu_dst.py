@@ -15,25 +15,19 @@ import pytest
 
 import synthetic as syn
 from oracle import precond, system
-from tests._helpers import need_gpu, oracle_system, rand_block, rel_max, to_dev, to_host
+from tests._helpers import (U32, U64, backward_error, bw_tol, fp32_tol, kappa, need_gpu,
+                            oracle_system, rand_block, refined_bw_tol, rel_max, to_dev, to_host)
 
 pytestmark = pytest.mark.gpu
 
-
-def fp32_tol(n, ell):
-    return 4 * (2 * math.log2(max(ell, 2)) + 16 + 2 * math.log2(max(n, 2)) + 8) * 2.0 ** -24
-
-
-def kappa(S):
-    lam = np.abs(precond.sine_fourier_symbols(S))
-    return float(lam.max() / lam.min())
+ELEMENTWISE_MAX = 1e-2   # element-wise tolerances at or above this pin nothing
 
 
 def tol_for(S, kind, prec, n, ell):
     if prec == "fp64":
-        return max(1e-10, 4 * kappa(S) * 2.0 ** -53)
+        return max(1e-10, 4 * kappa(S) * U64)
     if kind.startswith("wave"):
-        return max(fp32_tol(n, ell), kappa(S) * 2.0 ** -24)
+        return max(fp32_tol(n, ell), kappa(S) * U32)
     return fp32_tol(n, ell)
 
 
@@ -54,7 +48,10 @@ def test_dst_apply_matches_oracle(n, ell, kind, prec, transpose):
             else precond.circulant_inverse_spectral(S, X, transpose=transpose))
     a = AllAtOnce(n, ell, 1.0 / ell, equation=kind, precision=prec, restart=1, space="dst")
     got = to_host(a.precond_apply(to_dev(torch, X), transpose=transpose))
-    assert rel_max(got, want) <= tol_for(S, kind, prec, n, ell)
+    assert backward_error(S, X, got, transpose) <= bw_tol(n, ell, U64 if prec == "fp64" else U32)
+    tol = tol_for(S, kind, prec, n, ell)
+    if tol < ELEMENTWISE_MAX:
+        assert rel_max(got, want) <= tol
 
 
 @pytest.mark.parametrize("kind", ["heat", "wave_bd2", "wave_bd4"])
@@ -73,7 +70,7 @@ def test_dst_single_mode_is_divided_by_its_symbol(kind, transpose):
     a = AllAtOnce(n, ell, 1.0 / ell, equation=kind, precision="fp32", restart=1, space="dst")
     t = np.arange(ell)
     xs = syn.grid(n)
-    tol = (8 * math.log2(2 * (n + 1)) + 16) * 2.0 ** -24
+    tol = (8 * math.log2(2 * (n + 1)) + 16) * U32
     picks = [np.unravel_index(np.argmin(half), half.shape),
              np.unravel_index(np.argmax(half), half.shape), (ell // 8, n // 3)]
     for k, j0 in picks:
@@ -105,7 +102,11 @@ def test_dst_neumann_and_refined(transpose):
     a.set_precision("fp32_refined")
     got = to_host(a.precond_apply(to_dev(torch, X), transpose=transpose))
     t = fp32_tol(n, ell)
-    assert rel_max(got, want) <= 32 * t * t + 4 * kappa(S0) * 2.0 ** -53
+    assert rel_max(got, want) <= 32 * t * t + 4 * kappa(S0) * U64
+    a.set_precision("fp32")
+    z0 = to_host(a.precond_apply(to_dev(torch, X), transpose=transpose))
+    d = np.linalg.norm(z0 - got) / np.linalg.norm(got)
+    assert backward_error(S0, X, got, transpose) <= refined_bw_tol(n, ell, d)
 
 
 @pytest.mark.parametrize("kind", ["heat", "wave_bd2"])

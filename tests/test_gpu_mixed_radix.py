@@ -2,35 +2,27 @@
 the preconditioner applies with the oracle's dense-DFT circulant inverse
 (Section 3, any ell), in both precisions, both orientations, the refined
 mode and a Neumann term; tolerances as in test_gpu_precond."""
-import math
-
 import numpy as np
 import pytest
 
 import synthetic as syn
 from oracle import precond, system
-from tests._helpers import need_gpu, oracle_system, rand_block, rel_max, to_dev, to_host
+from tests._helpers import (U32, U64, backward_error, bw_tol, fp32_tol, kappa, need_gpu,
+                            oracle_system, rand_block, refined_bw_tol, rel_max, to_dev, to_host)
 
 pytestmark = pytest.mark.gpu
 
-
-def fp32_tol(n, ell):
-    return 4 * (2 * math.log2(max(ell, 2)) + 16 + 2 * math.log2(max(n, 2)) + 8) * 2.0 ** -24
-
-
-def kappa(S):
-    lam = np.abs(precond.sine_fourier_symbols(S))
-    return float(lam.max() / lam.min())
+ELEMENTWISE_MAX = 1e-2   # element-wise tolerances at or above this pin nothing
 
 
 def tol_for(S, kind, prec, n, ell):
     t32 = fp32_tol(n, ell)
     if kind == "wave_bd2":
-        t32 = max(t32, kappa(S) * 2.0 ** -24)
+        t32 = max(t32, kappa(S) * U32)
     if prec == "fp64":
-        return max(1e-10, 4 * kappa(S) * 2.0 ** -53)
+        return max(1e-10, 4 * kappa(S) * U64)
     if prec == "fp32_refined":
-        return 32 * t32 * t32 + 4 * kappa(S) * 2.0 ** -53
+        return 32 * t32 * t32 + 4 * kappa(S) * U64
     return t32
 
 
@@ -50,7 +42,17 @@ def test_mixed_radix_precond_matches_oracle(ell, kind, prec, transpose):
     want = precond.circulant_inverse(S, X, transpose=transpose)
     a = AllAtOnce(n, ell, 1.0 / ell, equation=kind, precision=prec, restart=1)
     got = to_host(a.precond_apply(to_dev(torch, X), transpose=transpose))
-    assert rel_max(got, want) <= tol_for(S, kind, prec, n, ell)
+    tol = tol_for(S, kind, prec, n, ell)
+    if tol < ELEMENTWISE_MAX:
+        assert rel_max(got, want) <= tol
+    eta = backward_error(S, X, got, transpose)
+    if prec == "fp32_refined":
+        a.set_precision("fp32")
+        z0 = to_host(a.precond_apply(to_dev(torch, X), transpose=transpose))
+        d = np.linalg.norm(z0 - got) / np.linalg.norm(got)
+        assert eta <= refined_bw_tol(n, ell, d)
+    else:
+        assert eta <= bw_tol(n, ell, U64 if prec == "fp64" else U32)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
