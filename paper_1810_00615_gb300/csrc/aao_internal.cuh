@@ -81,6 +81,58 @@ __device__ __forceinline__ double to_f64(float f) {
   return __hiloint2double((int)hi, (int)(u << 29));
 }
 
+// ------------------------------------------------- programmatic dependent launch
+// The kernels of one preconditioner apply form a chain on one stream.  Each
+// is launched with programmatic stream serialisation: it may be scheduled
+// while its predecessor's last CTAs still run, does what does not depend on
+// the predecessor (table loads, index set-up), and waits in pdl_wait() until
+// the predecessor grid has completed and its writes are visible.  pdl_trigger()
+// lets the successor be scheduled once every CTA of this grid has issued its
+// main loads.  Neither spins: both are grid-dependency instructions handled
+// by the hardware, and pdl_wait() returns at once when the kernel was
+// launched without the attribute or after any other stream operation.
+// pdl_wait(p, q, ...) takes the pointers to the predecessor's data and
+// redefines them after the wait: loads through them then depend on the wait
+// and cannot be scheduled above it (a memory clobber alone does not stop the
+// compiler from hoisting loads through const __restrict__ pointers, which it
+// may treat as read-only for the whole kernel).
+#ifndef AAO_PDL
+#define AAO_PDL 1
+#endif
+template <typename P>
+__device__ __forceinline__ void pdl_dep(P &p) {
+  static_assert(sizeof(P) == 8, "a pointer");
+  asm volatile("" : "+l"(p));
+}
+template <typename... P>
+__device__ __forceinline__ void pdl_wait(P &...ps) {
+#if AAO_PDL
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  (pdl_dep(ps), ...);
+#endif
+}
+__device__ __forceinline__ void pdl_trigger() {
+#if AAO_PDL
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+// Launch `kern` on stream s with programmatic stream serialisation.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = AAO_PDL;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // ------------------------------------------------- L2 residency hints
 // The preconditioner's half spectrum (67 MB at n = 4095, ell = 4096) is
 // written by the forward FFT, read and rewritten by the tridiagonal solves
@@ -258,6 +310,20 @@ struct RecTab {
   cx<R> e[kRecLevels];
 };
 
+// Factor L1 of the four-step FP32 time transform, ell = L1 L2 (ell = 256 ...
+// 4096, L1 >= L2, both in {16, 32, 64}).
+__host__ __device__ constexpr int four_l1(int64_t ell) {
+  return ell >= 2048 ? 64 : (ell >= 512 ? 32 : 16);
+}
+
+// Level-0 coefficients of the recursive form (RecTab level 0, FP32) for the
+// fused four-step apply, as float4 pairs in structure-of-arrays order: pair j
+// of frequency k at fuse32[j * ell + (k mod L1) L2 + k / L1], so that the
+// frequencies k = k1 + L1 k2 (k1 fixed) that one CTA of the transform holds
+// are adjacent.  Pairs 0-7: (invp_0, invp_1) ... (invp_14, e); pairs 8-14:
+// (bp_0, bp_1) ... (bp_12, bp_13); pairs 15-22: (fc_0, fc_1) ... (fc_14, 0).
+constexpr int kFusePairs = 23;
+
 // Stencil of the block circulant P (Section 3) for the compensated
 // residual: block A_j (time lag j, j < taps) is c0_j on the diagonal and c1_j
 // beside it, each stored as an FP32 pair hi + lo (c = hi + lo to 2^-48).
@@ -288,6 +354,7 @@ struct Ctx {
   void *tab64 = nullptr;   // TriTab<double, ch64>[nk]
   void *rec32 = nullptr;   // RecTab<float, ch32>[nk] when the recursive form applies
   void *rec64 = nullptr;   // RecTab<double, ch64>[nk]
+  void *fuse32 = nullptr;  // float4[kFusePairs][ell]: level-0 tables of the fused apply
   int lev32 = 0, lev64 = 0;             // levels of the recursive form (0: not applicable)
   int clu32 = 1, clu64 = 1;             // CTAs per row (cluster size) for rows beyond one CTA
   int cta32 = 0, cta64 = 0;             // threads per CTA in the cluster form
@@ -417,6 +484,25 @@ cudaError_t fft_inverse_f32_to_f32(const Ctx &c, const void *spec, float *y, cud
                                    void *inter = nullptr);
 cudaError_t launch_tridiag(const Ctx &c, void *spec, int prec, int transpose,
                            cudaStream_t s);
+// The FP32 apply with the tridiagonal solves folded into the four-step
+// transform (ell = 256 ... 4096 a power of two, the recursive form of the
+// solve, n + 1 = 16 P): forward transform + level-0 chunk solves into spec
+// and the chunks' separator data into sep, the separator system per
+// frequency (into sep as well), corrections + inverse transform.  sep
+// (fused_sep_bytes) lies fused_sep_offset(c) bytes after spec: the spectrum
+// region is sized for complex128 and FP32 uses its first half.  Exactly one
+// of x / x32 and of y / y32 is given; base (FP64 y only): y = base - result.
+bool fft_fused_supported(const Ctx &c);
+size_t fused_sep_offset(const Ctx &c);
+size_t fused_sep_bytes(const Ctx &c);
+cudaError_t fft_forward_f32_solve(const Ctx &c, const double *x, const float *x32, void *spec,
+                                  void *sep, int transpose, cudaStream_t s, void *inter);
+cudaError_t launch_tridiag_reduced_fused(const Ctx &c, void *sep, int transpose, cudaStream_t s);
+cudaError_t launch_tridiag_reduced(const Ctx &c, const void *sepbuf, void *sepsol, int transpose,
+                                   cudaStream_t s);
+cudaError_t fft_inverse_f32_correct(const Ctx &c, const void *spec, void *sep, double *y,
+                                    float *y32, int transpose, cudaStream_t s, void *inter,
+                                    const float *base);
 // The same solves by DST-I in space (AAO_SPACE_DST), in place on the spectrum.
 constexpr int64_t kDstMaxL = 4096;   // n + 1 <= kDstMaxL, a power of two
 bool dst_supported(int64_t n);

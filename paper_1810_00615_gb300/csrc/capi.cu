@@ -382,6 +382,26 @@ int refresh_constants(Ctx &c) {
     std::vector<aao::RecTab<float, 16>> r32;
     build_rec_tables<float, 16>(c, c.lev32, r32);
     AAO_CK(c, upload(&c.rec32, r32));
+    // level 0 again, in the layout of the fused four-step apply
+    if (c.lev32 >= 2 && c.ell >= 256 && c.ell <= 4096 && (c.ell & (c.ell - 1)) == 0) {
+      const int64_t L1 = aao::four_l1(c.ell), L2 = c.ell / L1;
+      std::vector<float4> ft((size_t)aao::kFusePairs * (size_t)c.ell, make_float4(0, 0, 0, 0));
+      auto pack = [](const cx<float> &a, const cx<float> &b) {
+        return make_float4(a.re, a.im, b.re, b.im);
+      };
+      const cx<float> zero = aao::mk(0.f, 0.f);
+      for (int64_t k = 0; k < c.nk; k++) {
+        const auto &T = r32[(size_t)k];
+        const size_t pos = (size_t)((k % L1) * L2 + k / L1);
+        auto at = [&](int j) -> float4 & { return ft[(size_t)j * (size_t)c.ell + pos]; };
+        for (int j = 0; j < 7; j++) at(j) = pack(T.invp[0][2 * j], T.invp[0][2 * j + 1]);
+        at(7) = pack(T.invp[0][14], T.e[0]);
+        for (int j = 0; j < 7; j++) at(8 + j) = pack(T.bp[0][2 * j], T.bp[0][2 * j + 1]);
+        for (int j = 0; j < 7; j++) at(15 + j) = pack(T.fc[0][2 * j], T.fc[0][2 * j + 1]);
+        at(22) = pack(T.fc[0][14], zero);
+      }
+      AAO_CK(c, upload(&c.fuse32, ft));
+    }
   }
   choose_form(c.n, c.ch64, sizeof(cx<double>), 512, c.lev64, c.lsz64, c.clu64, c.cta64);
   if (c.lev64 > 0) {
@@ -580,7 +600,31 @@ int check_ws(const Ctx &c, int restart) {
   return AAO_OK;
 }
 
-// One application of P^{-1} (or P^{-T}); with yprev, of P^{-1}(x - E yprev).
+// The FP32 apply with the tridiagonal solves folded into the four-step
+// transform: forward transform + chunk solves (class FFT_FORWARD), the
+// separator systems (TRIDIAG), corrections + inverse transform
+// (FFT_INVERSE).  Input x (FP64) or x32 (FP32); output YT, with base
+// (FP64 output) y = base - P^{-1} x.
+template <typename YT>
+cudaError_t precond_fused(Ctx &c, const double *x, const float *x32, YT *y, int tr,
+                          cudaStream_t s, const float *base = nullptr) {
+  const aao::WsLayout L = aao::ws_layout(c, 0);
+  void *spec = c.ws + L.spec;
+  void *inter = c.ws + L.inter;
+  void *sep = static_cast<char *>(spec) + aao::fused_sep_offset(c);
+  cudaError_t e = run(c, AAO_K_FFT_FORWARD, s, [&] {
+    return aao::fft_forward_f32_solve(c, x, x32, spec, sep, tr, s, inter);
+  });
+  if (e != cudaSuccess) return e;
+  e = run(c, AAO_K_TRIDIAG, s, [&] { return aao::launch_tridiag_reduced_fused(c, sep, tr, s); });
+  if (e != cudaSuccess) return e;
+  return run(c, AAO_K_FFT_INVERSE, s, [&] {
+    if constexpr (sizeof(YT) == 4) return aao::fft_inverse_f32_correct(c, spec, sep, nullptr, y, tr, s, inter, nullptr);
+    else return aao::fft_inverse_f32_correct(c, spec, sep, y, nullptr, tr, s, inter, base);
+  });
+}
+
+// One application of P^{-1} (or P^{-T}); with yprev, of P^{-1}(x - E yprev).// One application of P^{-1} (or P^{-T}); with yprev, of P^{-1}(x - E yprev).
 // YT = float stores an FP32 result (FP32 preconditioner only): the values
 // the FP32 inverse transform produces are then kept as they are.  With base
 // (FP32 preconditioner, FP64 result) the result is base - P^{-1} x.
@@ -591,6 +635,8 @@ cudaError_t precond_once(Ctx &c, const double *x, const YT *yprev, YT *y, int tr
   void *spec = c.ws + L.spec;
   void *inter = L.inter_bytes ? c.ws + L.inter : nullptr;
   const bool f32 = c.prec == AAO_PREC_FP32;
+  if (f32 && !yprev && inter && aao::fft_fused_supported(c))
+    return precond_fused<YT>(c, x, nullptr, y, tr, s, base);
   cudaError_t e = run(c, AAO_K_FFT_FORWARD, s, [&] {
     if constexpr (sizeof(YT) == 4) return aao::fft_forward_f32_yf(c, x, yprev, spec, s, inter);
     else return f32 ? aao::fft_forward_f32(c, x, yprev, spec, s, inter)
@@ -624,6 +670,7 @@ cudaError_t precond_refined(Ctx &c, const double *x, double *y, int tr, cudaStre
     void *spec = c.ws + L.spec;
     e = run(c, AAO_K_REFINE, s, [&] { return aao::launch_circ_residual_df(c, z0, x, r32, tr, s); });
     if (e != cudaSuccess) return e;
+    if (aao::fft_fused_supported(c)) return precond_fused<double>(c, nullptr, r32, y, tr, s, z0);
     e = run(c, AAO_K_FFT_FORWARD, s, [&] { return aao::fft_forward_f32_from_f32(c, r32, spec, s, inter); });
     if (e != cudaSuccess) return e;
     e = run(c, AAO_K_TRIDIAG, s, [&] { return aao::launch_tridiag(c, spec, c.prec, tr, s); });
@@ -1118,7 +1165,7 @@ int aao_create(int64_t n, int64_t ell, double tau, int equation, aao_ctx **out) 
 void aao_destroy(aao_ctx *ctx) {
   if (!ctx) return;
   Ctx &c = ctx->c;
-  void *ptrs[] = {c.tab32, c.tab64, c.rec32, c.rec64, c.tw32, c.tw64, c.beta, c.beta_p,
+  void *ptrs[] = {c.tab32, c.tab64, c.rec32, c.rec64, c.fuse32, c.tw32, c.tw64, c.beta, c.beta_p,
                   c.mv_rows, c.mv_rows_p, c.mv_d0, c.mv_o0,
                   c.sigk, c.sigk32, c.dtw32, c.dtw64, c.dst_cm32, c.dst_cm64,
                   c.dst_mk32, c.dst_mk64};

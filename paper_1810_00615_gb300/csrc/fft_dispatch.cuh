@@ -4,6 +4,7 @@
 #include "fft_time.cuh"
 #include "fft_mixed.cuh"
 #include "fft_four.cuh"
+#include "fft_four_fused.cuh"
 
 namespace aao {
 namespace fft {

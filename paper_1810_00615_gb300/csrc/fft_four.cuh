@@ -46,18 +46,18 @@ inline size_t four_inter_bytes(int64_t ell, int64_t n) {
 // The factors of ell: L1 >= L2, both in {16, 32, 64}.
 template <int L> struct Four {
   static constexpr bool OK = L >= 256 && L <= 4096;
-  static constexpr int L1 = L >= 2048 ? 64 : (L >= 512 ? 32 : 16);
+  static constexpr int L1 = four_l1(L);
   static constexpr int L2 = OK ? L / L1 : 16;
 };
 
 // In-place N-point DFTs (N = 8 R, R in {2, 4, 8}) down the N rows of each of
-// the W columns of S (row r at S + r W).  With t = j + 8 r and k = a + R b:
+// the W columns of S (row r at S + r SW, SW >= W the row stride).  With t = j + 8 r and k = a + R b:
 // pass 1 takes, per (column, j < 8), the R-point DFT over r and multiplies
 // output a by e^{DIR 2 pi i j a/N} = tw[(ell/N) j a] (tw: the length-ell
 // table e^{-2 pi i m/ell}); pass 2 takes, per (column, a < R), the 8-point
 // DFT over j, output b being X[a + R b].  Natural order in and out.  All
 // threads must call it.
-template <int N, int W, int ELL, int DIR>
+template <int N, int W, int ELL, int DIR, int SW = W>
 __device__ __forceinline__ void dft_columns(cx<float> *S, const cx<float> *__restrict__ tw) {
   constexpr int R = N / 8;
   constexpr int T1 = 8 * W / kFourT;                // pass-1 tasks per thread
@@ -67,7 +67,7 @@ __device__ __forceinline__ void dft_columns(cx<float> *S, const cx<float> *__res
   for (int h = 0; h < T1; h++) {
     const int e = threadIdx.x + h * kFourT, c = e % W, j = e / W;
 #pragma unroll
-    for (int r = 0; r < R; r++) v[h][r] = S[(j + 8 * r) * W + c];
+    for (int r = 0; r < R; r++) v[h][r] = S[(j + 8 * r) * SW + c];
   }
   __syncthreads();
 #pragma unroll
@@ -77,7 +77,7 @@ __device__ __forceinline__ void dft_columns(cx<float> *S, const cx<float> *__res
 #pragma unroll
     for (int a = 1; a < R; a++) v[h][a] = twiddle<float, DIR>(v[h][a], tw[(ELL / N) * j * a]);
 #pragma unroll
-    for (int a = 0; a < R; a++) S[(8 * a + j) * W + c] = v[h][a];   // pass-2 input of a
+    for (int a = 0; a < R; a++) S[(8 * a + j) * SW + c] = v[h][a];   // pass-2 input of a
   }
   __syncthreads();
   constexpr int T2 = (R * W + kFourT - 1) / kFourT;  // pass-2 tasks per thread
@@ -87,7 +87,7 @@ __device__ __forceinline__ void dft_columns(cx<float> *S, const cx<float> *__res
     const int e = threadIdx.x + h * kFourT, c = e % W, a = e / W;
     if (a < R) {
 #pragma unroll
-      for (int j = 0; j < 8; j++) u[h][j] = S[(8 * a + j) * W + c];
+      for (int j = 0; j < 8; j++) u[h][j] = S[(8 * a + j) * SW + c];
     }
   }
   __syncthreads();
@@ -97,7 +97,7 @@ __device__ __forceinline__ void dft_columns(cx<float> *S, const cx<float> *__res
     if (a < R) {
       dft<float, DIR, 8>(u[h]);
 #pragma unroll
-      for (int b = 0; b < 8; b++) S[(a + R * b) * W + c] = u[h][b];   // X[a + R b]
+      for (int b = 0; b < 8; b++) S[(a + R * b) * SW + c] = u[h][b];   // X[a + R b]
     }
   }
   __syncthreads();
@@ -126,6 +126,7 @@ k_fft4_forward1(const XT *__restrict__ x, cx<float> *__restrict__ inter, int n, 
   // column q = thread % 2W, the same for every u
   const int q = threadIdx.x % (2 * W), i = i0 + q;
   const bool in = i < n;
+  pdl_wait(x);   // x is the previous kernel's output
   const XT *px = x + (size_t)(L2 * (threadIdx.x / (2 * W)) + t2) * n + i;
   const size_t ustride = (size_t)RPU * L2 * n;
 #pragma unroll
@@ -142,6 +143,7 @@ k_fft4_forward1(const XT *__restrict__ x, cx<float> *__restrict__ inter, int n, 
       else Sf[(b0 + u) * kFourT + threadIdx.x] = d[u];
     }
   }
+  pdl_trigger();
   __syncthreads();
   dft_columns<L1, W, L, -1>(S, tw);
   // row k1 = DFT output; times w^{t2 k1}.  Element (h, thread): k1 =
@@ -158,8 +160,9 @@ k_fft4_forward1(const XT *__restrict__ x, cx<float> *__restrict__ inter, int n, 
   }
 }
 
-// Load the L2 rows inter[k1][0..L2) of W columns from cb into S (L2 x W).
-template <int L2, int W>
+// Load the L2 rows inter[k1][0..L2) of W columns from cb into S (L2 x W,
+// row stride SW).
+template <int L2, int W, int SW = W>
 __device__ __forceinline__ void load_rows(const cx<float> *__restrict__ inter, int k1, int ncx,
                                           int cb, cx<float> *S, unsigned long long pol) {
   constexpr int U = L2 * W / kFourT, RPU = kFourT / W;
@@ -170,7 +173,10 @@ __device__ __forceinline__ void load_rows(const cx<float> *__restrict__ inter, i
 #pragma unroll
   for (int u = 0; u < U; u++) v[u] = ld_hintc(pr + u * ustride, pol);
 #pragma unroll
-  for (int u = 0; u < U; u++) S[u * kFourT + threadIdx.x] = v[u];
+  for (int u = 0; u < U; u++) {
+    if constexpr (SW == W) S[u * kFourT + threadIdx.x] = v[u];
+    else S[(RPU * u + threadIdx.x / W) * SW + threadIdx.x % W] = v[u];
+  }
 }
 
 // The W-column segments (two 128-byte lines each, W = 32) of the
@@ -327,6 +333,7 @@ k_fft4_inverseB(const cx<float> *__restrict__ inter, OT *__restrict__ y, int n, 
   const int t2 = blockIdx.y;
   const int cb = W * blockIdx.x, i0 = 2 * cb;
   const unsigned long long pol_done = l2_evict_first();
+  pdl_wait(inter, base);   // the intermediate and base come from earlier kernels
   // rows k1 = 0..L1-1 of this t2 (stride L2 rows in the intermediate)
   {
     constexpr int U = L1 * W / kFourT, RPU = kFourT / W;
@@ -340,6 +347,7 @@ k_fft4_inverseB(const cx<float> *__restrict__ inter, OT *__restrict__ y, int n, 
 #pragma unroll
     for (int u = 0; u < U; u++) S[u * kFourT + threadIdx.x] = v[u];
   }
+  pdl_trigger();
   __syncthreads();
   if (discard) discard_rows<L1, W>(inter, t2, -1, L2, ncx, cb);
   dft_columns<L1, W, L, +1>(S, tw);

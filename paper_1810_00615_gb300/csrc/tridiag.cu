@@ -382,17 +382,24 @@ k_tridiag_rec(cx<R> *__restrict__ spec, int n, int64_t n_pad,
 
 // Levels 1 .. levels-1 of the recursive form on shared-memory buffers:
 // B[1] holds the level-1 right-hand sides on entry and the level-1 solution
-// (the level-0 separator values) on exit.  Called by all threads of one CTA.
-template <typename R, int CH>
+// (the level-0 separator values) on exit.  Called by all threads of one CTA
+// (WARP = false) or by the 32 lanes of one warp (WARP = true, p = lane).
+template <bool WARP>
+__device__ __forceinline__ void rec_sync() {
+  if constexpr (WARP) __syncwarp();
+  else __syncthreads();
+}
+template <typename R, int CH, bool WARP = false>
 __device__ __forceinline__ void rec_upper(cx<R> *const *B, const int *lsz, int levels,
                                           const cx<R> (*s_invp)[CH], const cx<R> (*s_bp)[CH],
                                           const cx<R> (*s_fc)[CH], const cx<R> *s_e, int p) {
+  const int nthr = WARP ? 32 : (int)blockDim.x;
   for (int l = 1; l < levels - 1; l++) {
     const int nl = lsz[l];
     const int Pl = (nl + 1) / CH, Ml = Pl - 1;
     cx<R> *Bl = B[l];
     const cx<R> el = s_e[l];
-    for (int q = p; q < Pl; q += blockDim.x) {
+    for (int q = p; q < Pl; q += nthr) {
       cx<R> w[CH];
 #pragma unroll
       for (int i = 0; i < CH; i++) w[i] = (q * CH + i < nl) ? Bl[rpos<CH>(q * CH + i)] : mk((R)0, (R)0);
@@ -404,14 +411,14 @@ __device__ __forceinline__ void rec_upper(cx<R> *const *B, const int *lsz, int l
 #pragma unroll
       for (int i = 0; i < CH - 1; i++) Bl[rpos<CH>(q * CH + i)] = w[i];
     }
-    __syncthreads();
-    for (int q = p; q < Ml; q += blockDim.x) {
+    rec_sync<WARP>();
+    for (int q = p; q < Ml; q += nthr) {
       const cx<R> sep = Bl[rpos<CH>(q * CH + CH - 1)];
       const cx<R> lastl = Bl[rpos<CH>(q * CH + CH - 2)];
       const cx<R> firstr = Bl[rpos<CH>((q + 1) * CH)];
       B[l + 1][rpos<CH>(q)] = cfnms(sep, el, lastl + firstr);
     }
-    __syncthreads();
+    rec_sync<WARP>();
   }
   {
     const int L = levels - 1;
@@ -433,14 +440,14 @@ __device__ __forceinline__ void rec_upper(cx<R> *const *B, const int *lsz, int l
       for (int i = 0; i < CH; i++)
         if (i < nl) Bl[rpos<CH>(i)] = w[i];
     }
-    __syncthreads();
+    rec_sync<WARP>();
   }
   for (int l = levels - 2; l >= 1; l--) {
     const int nl = lsz[l];
     const int Pl = (nl + 1) / CH, Ml = Pl - 1;
     cx<R> *Bl = B[l];
     const cx<R> *Bu = B[l + 1];
-    for (int q = p; q < Pl; q += blockDim.x) {
+    for (int q = p; q < Pl; q += nthr) {
       const cx<R> sl = (q > 0) ? Bu[rpos<CH>(q - 1)] : mk((R)0, (R)0);
       const cx<R> sr = (q < Ml) ? Bu[rpos<CH>(q)] : mk((R)0, (R)0);
 #pragma unroll
@@ -450,7 +457,7 @@ __device__ __forceinline__ void rec_upper(cx<R> *const *B, const int *lsz, int l
       }
       if (q < Ml) Bl[rpos<CH>(q * CH + CH - 1)] = sr;
     }
-    __syncthreads();
+    rec_sync<WARP>();
   }
 }
 
@@ -559,6 +566,215 @@ k_tridiag_cluster(cx<R> *__restrict__ spec, int n, int64_t n_pad,
       for (int u = 0; q * EPC + u < nseg; u++) row[q * EPC + u] = z[u];
     }
   }
+}
+
+// The separator system of the fused four-step apply (fft_four_fused.cuh):
+// one warp per frequency k.  The forward kernel left, for each chunk p of
+// row k, its first local value v_0 and its separator's partial right-hand
+// side x_sep - e v_14 in sepbuf[k P + p]; the level-1 right-hand side of
+// separator p is that partial value minus e times the first local value of
+// chunk p + 1.  Levels 1 .. levels-1 of the recursive form are solved as in
+// k_tridiag_rec (by one warp) and the separator values go to
+// sep[k sstride + p].  Per warp, wbytes of shared memory: the frequency's
+// RecTab (conjugated for the transpose), then the level buffers.
+template <int CH>
+__global__ void __launch_bounds__(256)
+k_tridiag_reduced(const float4 *__restrict__ sepbuf, cx<float> *__restrict__ sep,
+                  int64_t sstride, const RecTab<float, CH> *__restrict__ tabs, int conj_sym,
+                  int levels, int4 lsz_lo, int2 lsz_hi, int nk, int wbytes) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int k = blockIdx.x * (blockDim.x >> 5) + w;
+  if (k >= nk) return;   // whole warps only; nothing below synchronises the CTA
+  const int lsz[kRecLevels] = {lsz_lo.x, lsz_lo.y, lsz_lo.z, lsz_lo.w, lsz_hi.x, lsz_hi.y};
+  extern __shared__ __align__(16) unsigned char smraw[];
+  unsigned char *mine = smraw + (size_t)w * wbytes;
+  RecTab<float, CH> *st = reinterpret_cast<RecTab<float, CH> *>(mine);
+  {
+    static_assert(sizeof(RecTab<float, CH>) % 16 == 0, "whole float4 copies");
+    constexpr int NV = (int)(sizeof(RecTab<float, CH>) / 16);
+    const float4 *src = reinterpret_cast<const float4 *>(tabs + k);
+    float4 *dst = reinterpret_cast<float4 *>(st);
+    const float sg = conj_sym ? -1.f : 1.f;   // every entry is complex: (re, im) pairs
+    for (int i = lane; i < NV; i += 32) {
+      const float4 q = __ldg(src + i);
+      dst[i] = make_float4(q.x, sg * q.y, q.z, sg * q.w);
+    }
+  }
+  cx<float> *B[kRecLevels];
+  size_t off = 0;
+  for (int l = 1; l < levels; l++) {
+    B[l] = reinterpret_cast<cx<float> *>(mine + sizeof(RecTab<float, CH>)) + off;
+    off += (size_t)rpos<CH>(lsz[l]) + 1;
+  }
+  __syncwarp();
+  pdl_wait(sepbuf);   // the previous kernel's output
+  const float4 *row = sepbuf + (size_t)k * sstride;
+  const cx<float> e0 = st->e[0];
+  const int M = lsz[1];
+  for (int q0 = 0; q0 < M; q0 += 8 * 32) {
+    float4 a[8];
+    float2 b[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const int q = q0 + lane + 32 * u;
+      if (q < M) {
+        a[u] = row[q];                                         // (v0_q, partial_q)
+        b[u] = *reinterpret_cast<const float2 *>(row + q + 1);  // v0_{q+1}
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const int q = q0 + lane + 32 * u;
+      if (q < M) B[1][rpos<CH>(q)] = cfnms(mk(a[u].z, a[u].w), e0, mk(b[u].x, b[u].y));
+    }
+  }
+  __syncwarp();
+  rec_upper<float, CH, true>(B, lsz, levels, st->invp, st->bp, st->fc, st->e, lane);
+  cx<float> *out = sep + (size_t)k * sstride;
+  for (int q = lane; q < M; q += 32) out[q] = B[1][rpos<CH>(q)];
+}
+
+// The same separator system when the recursive form has exactly three
+// levels and at most 32 level-1 chunks (n + 1 = 16 * 16 * P2 with P2 <= 16,
+// e.g. n = 1023 or 4095), in registers: lane L of the warp of frequency k
+// owns level-1 chunk L (separators 16L .. 16L+15), forms their right-hand
+// sides from sepbuf, solves the chunk (level-1 pivots), hands the level-2
+// right-hand side of its separator to lane 0 through shared memory, lane 0
+// solves level 2 (at most 15 unknowns) in one sweep, and every lane
+// corrects its chunk with the two level-2 values around it.  No level
+// buffer round trips: the chain of dependent steps is two Thomas sweeps.
+template <int CH>
+__global__ void __launch_bounds__(256)
+k_tridiag_reduced3(const float4 *__restrict__ sepbuf, cx<float> *__restrict__ sep,
+                   int64_t sstride, const RecTab<float, CH> *__restrict__ tabs, int conj_sym,
+                   int M1, int nk) {
+  constexpr int WPB = 8;
+  constexpr int NV = (int)(sizeof(RecTab<float, CH>) / 16);   // float4 per table
+  constexpr int UV = (NV + 31) / 32;
+  static_assert(sizeof(RecTab<float, CH>) % 16 == 0, "whole float4 copies");
+  __shared__ __align__(16) RecTab<float, CH> s_tab[WPB];   // per warp, conjugated if transposed
+  __shared__ cx<float> s2[WPB][CH + 1];                     // level-2 right-hand sides / solution
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int k = blockIdx.x * WPB + w;
+  if (k >= nk) return;   // whole warps only; nothing below synchronises the CTA
+  const int P1 = (M1 + 1) / CH;           // level-1 chunks (<= 32)
+  const int M2 = P1 - 1;                  // level-2 unknowns (<= 15)
+  const int q0 = CH * lane;               // first level-1 unknown of this lane's chunk
+  const bool own = lane < P1;
+  // every global load of the warp first: its frequency's table and the
+  // chunk's sepbuf entries (P = M1 + 1 per frequency)
+  float4 tv[UV];
+  {
+    const float4 *src = reinterpret_cast<const float4 *>(tabs + k);
+#pragma unroll
+    for (int u = 0; u < UV; u++)
+      if (lane + 32 * u < NV) tv[u] = __ldg(src + lane + 32 * u);
+  }
+  pdl_wait(sepbuf);   // the previous kernel's output
+  const float4 *row = sepbuf + (size_t)k * sstride;
+  float4 a[CH];
+  float2 nxt = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < CH; j++) {
+    a[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (own && q0 + j <= M1) a[j] = row[q0 + j];
+  }
+  if (own && q0 + CH <= M1) nxt = *reinterpret_cast<const float2 *>(row + q0 + CH);
+  pdl_trigger();
+  {
+    const float sg = conj_sym ? -1.f : 1.f;   // every entry is complex: (re, im) pairs
+    float4 *dst = reinterpret_cast<float4 *>(&s_tab[w]);
+#pragma unroll
+    for (int u = 0; u < UV; u++)
+      if (lane + 32 * u < NV) dst[lane + 32 * u] = make_float4(tv[u].x, sg * tv[u].y, tv[u].z, sg * tv[u].w);
+  }
+  __syncwarp();
+  const RecTab<float, CH> &T = s_tab[w];
+  const cx<float> e0 = T.e[0], e1 = T.e[1];
+  cx<float> wv[CH];
+  // level-1 right-hand sides: partial_q - e0 first_{q+1}
+#pragma unroll
+  for (int j = 0; j < CH; j++) {
+    const cx<float> first_next = (j + 1 < CH) ? mk(a[j + 1].x, a[j + 1].y) : mk(nxt.x, nxt.y);
+    wv[j] = (q0 + j < M1) ? cfnms(mk(a[j].z, a[j].w), e0, first_next) : mk(0.f, 0.f);
+  }
+  // level 1: the chunk's CH-1 unknowns, its separator value aside
+  const cx<float> sep1 = wv[CH - 1];
+  wv[0] = wv[0] * T.invp[1][0];
+#pragma unroll
+  for (int i = 1; i < CH - 1; i++) wv[i] = cfnms(wv[i], e1, wv[i - 1]) * T.invp[1][i];
+#pragma unroll
+  for (int i = CH - 3; i >= 0; i--) wv[i] = cfnms(wv[i], T.bp[1][i], wv[i + 1]);
+  // level-2 right-hand side of separator L: sep - e1 (last of chunk L + first of chunk L+1)
+  const cx<float> firstr = mk(__shfl_down_sync(0xffffffffu, wv[0].re, 1),
+                              __shfl_down_sync(0xffffffffu, wv[0].im, 1));
+  if (lane < M2) s2[w][lane] = cfnms(sep1, e1, wv[CH - 2] + firstr);
+  __syncwarp();
+  if (lane == 0 && M2 > 0) {
+    const cx<float> e2 = T.e[2];
+    cx<float> z[CH];
+#pragma unroll
+    for (int i = 0; i < CH; i++) z[i] = (i < M2) ? s2[w][i] : mk(0.f, 0.f);
+    z[0] = z[0] * T.invp[2][0];
+#pragma unroll
+    for (int i = 1; i < CH; i++)
+      if (i < M2) z[i] = cfnms(z[i], e2, z[i - 1]) * T.invp[2][i];
+#pragma unroll
+    for (int i = CH - 2; i >= 0; i--)
+      if (i < M2 - 1) z[i] = cfnms(z[i], T.bp[2][i], z[i + 1]);
+#pragma unroll
+    for (int i = 0; i < CH; i++)
+      if (i < M2) s2[w][i] = z[i];
+  }
+  __syncwarp();
+  if (!own) return;
+  const cx<float> sl = lane > 0 ? s2[w][lane - 1] : mk(0.f, 0.f);
+  const cx<float> sr = lane < M2 ? s2[w][lane] : mk(0.f, 0.f);
+  cx<float> *out = sep + (size_t)k * sstride + q0;
+#pragma unroll
+  for (int i = 0; i < CH - 1; i++) {
+    const cx<float> val = cfma(cfma(wv[i], sl, T.fc[1][i]), sr, T.fc[1][CH - 2 - i]);
+    if (q0 + i < M1) out[i] = val;
+  }
+  if (q0 + CH - 1 < M1) out[CH - 1] = sr;
+}
+
+cudaError_t launch_tridiag_reduced(const Ctx &c, const void *sepbuf, void *sep, int transpose,
+                                   cudaStream_t s) {
+  if (c.lev32 < 2 || c.ch32 != 16) return cudaErrorNotSupported;
+  constexpr int CH = 16;
+  const int levels = c.lev32;
+  const int *lsz = c.lsz32;
+  if (levels == 3 && (lsz[1] + 1) / CH <= 32) {
+    constexpr int WPB = 8;   // warps (frequencies) per CTA, as in the kernel
+    const cudaError_t e = launch_pdl(k_tridiag_reduced3<CH>, dim3((unsigned)((c.nk + WPB - 1) / WPB)),
+                                     dim3(32 * WPB), 0, s, static_cast<const float4 *>(sepbuf),
+                                     static_cast<cx<float> *>(sep), (int64_t)c.P32,
+                                     static_cast<const RecTab<float, CH> *>(c.rec32), transpose,
+                                     lsz[1], (int)c.nk);
+    note_launch();
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
+  size_t off = 0;
+  for (int l = 1; l < levels; l++) off += (size_t)(lsz[l] + lsz[l] / CH) + 1;
+  const size_t wbytes = (sizeof(RecTab<float, CH>) + off * sizeof(cx<float>) + 15) & ~(size_t)15;
+  int wpb = (int)((200 * 1024) / wbytes);
+  wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
+  if (wbytes > 200 * 1024) return cudaErrorNotSupported;
+  const size_t smem = (size_t)wpb * wbytes;
+  auto kern = k_tridiag_reduced<CH>;
+  cudaError_t e = kernel_setup((const void *)kern, 32 * wpb, smem);
+  if (e != cudaSuccess) { cudaGetLastError(); return e; }
+  const int4 lo = make_int4(lsz[0], lsz[1], lsz[2], lsz[3]);
+  const int2 hi = make_int2(lsz[4], lsz[5]);
+  const unsigned grid = (unsigned)((c.nk + wpb - 1) / wpb);
+  kern<<<grid, 32 * wpb, smem, s>>>(static_cast<const float4 *>(sepbuf),
+                                     static_cast<cx<float> *>(sep), (int64_t)c.P32,
+                                     static_cast<const RecTab<float, CH> *>(c.rec32), transpose,
+                                     levels, lo, hi, (int)c.nk, (int)wbytes);
+  note_launch();
+  return cudaGetLastError();
 }
 
 template <typename R, int CH>
