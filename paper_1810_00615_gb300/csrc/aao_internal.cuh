@@ -451,7 +451,10 @@ cudaError_t run_class(Ctx &c, int cls, cudaStream_t s, F &&f) {
 // in to that much dynamic shared memory and count the CTAs the device holds
 // at once (SMs x resident CTAs per SM).  Later calls are a cached lookup, so
 // launch paths stay free of driver queries.
-cudaError_t kernel_setup(const void *kern, int threads, size_t smem, int *resident = nullptr);
+// prefer_smem: also ask for the whole L1 / shared-memory array as shared
+// memory (for kernels whose resident-CTA count is set by shared memory).
+cudaError_t kernel_setup(const void *kern, int threads, size_t smem, int *resident = nullptr,
+                         bool prefer_smem = false);
 
 // ------------------------------------------------------------ launchers
 // All return cudaGetLastError() of the launch.

@@ -535,7 +535,8 @@ cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
 }  // namespace
 
 namespace aao {
-cudaError_t kernel_setup(const void *kern, int threads, size_t smem, int *resident) {
+cudaError_t kernel_setup(const void *kern, int threads, size_t smem, int *resident,
+                         bool prefer_smem) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -548,6 +549,13 @@ cudaError_t kernel_setup(const void *kern, int threads, size_t smem, int *reside
   if (smem > have || have == 0) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) { cudaGetLastError(); return e; }
+    if (prefer_smem) {
+      // all of the unified L1 / shared-memory array as shared memory, so that
+      // the CTA count the kernel is compiled for fits
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) { cudaGetLastError(); return e; }
+    }
     have = smem > have ? smem : have;
   }
   const auto key = std::make_tuple(kern, dev, threads, smem);

@@ -37,6 +37,10 @@ namespace fft {
 namespace {   // included by both precision units: one private copy each
 
 constexpr int kFuseCH = 16;   // chunk length of the recursive form: 15 unknowns + separator
+// Resident CTAs per SM the two middle kernels are compiled for (register cap).
+#ifndef AAO_FUSE_MINB
+#define AAO_FUSE_MINB 4
+#endif
 
 // Row stride (complex values) of the DFT buffers: two values of padding per
 // row, so that the 16-byte reads of eight consecutive rows at one column fall
@@ -127,7 +131,7 @@ constexpr int kInvSeps = 5;     // separators p0-1 .. p0+3 around the CTA's four
 // bytes of dynamic shared memory.  nchunks = P; spec rows have n_pad >= 16 P
 // elements; sepbuf: P float4 per frequency.
 template <int L, int W>
-__global__ void __launch_bounds__(kFourT, 3)
+__global__ void __launch_bounds__(kFourT, AAO_FUSE_MINB)
 k_fft4_forward2_solve(const cx<float> *__restrict__ inter, cx<float> *__restrict__ spec,
                       float4 *__restrict__ sepbuf, int ncx, int64_t n_pad, int nchunks,
                       const cx<float> *__restrict__ tw, int discard, const float4 *__restrict__ ft,
@@ -242,7 +246,7 @@ k_fft4_forward2_solve(const cx<float> *__restrict__ inter, cx<float> *__restrict
 // solutions of k_fft4_forward2_solve; sep: the separator values s_p of
 // frequency k at sep[k sstride + p], p < P - 1 (k_tridiag_reduced).
 template <int L, int W>
-__global__ void __launch_bounds__(kFourT, 3)
+__global__ void __launch_bounds__(kFourT, AAO_FUSE_MINB)
 k_fft4_inverseA_correct(const cx<float> *__restrict__ spec, const cx<float> *__restrict__ sep,
                         cx<float> *__restrict__ inter, int ncx, int64_t n_pad, int nchunks,
                         int64_t sstride, const cx<float> *__restrict__ tw, int discard,
@@ -388,7 +392,8 @@ cudaError_t four_forward_solve(int64_t n, int64_t n_pad, int nchunks, const XT *
   const int ncx = (int)four_ncx(n);
   cx<float> *ip = static_cast<cx<float> *>(inter);
   cudaError_t e = kernel_setup((const void *)k_fft4_forward1<L, W, XT>, kFourT, sm1);
-  if (e == cudaSuccess) e = kernel_setup((const void *)k_fft4_forward2_solve<L, W>, kFourT, sm2);
+  if (e == cudaSuccess)
+    e = kernel_setup((const void *)k_fft4_forward2_solve<L, W>, kFourT, sm2, nullptr, true);
   if (e != cudaSuccess) return e;
   e = launch_pdl(k_fft4_forward1<L, W, XT>, dim3((unsigned)(ncx / W), L2), dim3(kFourT), sm1, s,
                  x, ip, (int)n, ncx, tw);
@@ -413,7 +418,8 @@ cudaError_t four_inverse_correct(int64_t n, int64_t n_pad, int nchunks, const cx
   constexpr size_t sm2 = fuse_smem<L, kInvPairs, kInvSeps>();
   const int ncx = (int)four_ncx(n);
   cx<float> *ip = static_cast<cx<float> *>(inter);
-  cudaError_t e = kernel_setup((const void *)k_fft4_inverseA_correct<L, W>, kFourT, sm2);
+  cudaError_t e =
+      kernel_setup((const void *)k_fft4_inverseA_correct<L, W>, kFourT, sm2, nullptr, true);
   if (e == cudaSuccess) e = kernel_setup((const void *)k_fft4_inverseB<L, W, OT>, kFourT, sm1);
   if (e != cudaSuccess) return e;
   const int dis = four_discard_ok(ip, spec, n_pad) ? 1 : 0;
