@@ -1,7 +1,8 @@
-"""Host-side pieces of bench.py, no GPU: the roofline line's inputs exist in
-the committed ncu summaries, the nvidia-smi clock samples are parsed into a
-median clock and the set of throttle reasons, and the reference arm does no
-work on ranks other than 0."""
+"""Host-side pieces of bench.py, no GPU: figures from committed ncu summaries
+are used only for the kernel code they were measured on, the nvidia-smi
+clock samples are parsed into a median clock and the set of throttle
+reasons, and the reference arm does no work on ranks other than 0 and
+reports the steps it actually ran."""
 import argparse
 import io
 import os
@@ -13,18 +14,26 @@ import pytest
 import bench
 
 
-def test_roofline_inputs_are_in_the_committed_summaries():
-    # ALU-pipe instructions and DRAM bytes per launch of the dominant kernel
-    alu = bench._profile_value("alu_inst_per_launch", bench.ROOFLINE_KEY)
-    dram = bench._traffic(bench.ROOFLINE_KEY)
-    assert alu is not None and alu > 0
-    assert dram is not None and dram > 0
-    # the fused matvec reads z, v, v0 and writes w (32 B per element of the
-    # 4095 x 4096 workload); its DRAM traffic cannot be below that by more
-    # than what L2 keeps between launches, nor far above it
-    algo = 32 * bench.N_SPACE * bench.ELL
-    assert 0.5 * algo <= dram <= 1.5 * algo
-    assert bench._profile_value("alu_inst_per_launch", "no_such_kernel") is None
+def test_profile_figures_are_taken_only_for_the_current_kernel_code(tmp_path, monkeypatch):
+    """A figure from an ncu summary is used only when the summary's
+    source_digest line names the library sources built now; a summary of
+    other kernel code gives None (no stale traffic in the bench line)."""
+    from paper_1810_00615_gb300 import _build
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    digest = _build._digest()
+    (prof / "current.md").write_text(
+        f"source_digest: {digest}\n\ndram_bytes_per_launch: kern_a 123456\n"
+        "busiest_pipe_name: kern_a fp64\n")
+    (prof / "stale.md").write_text(
+        "source_digest: 0123abcd\n\ndram_bytes_per_launch: kern_b 999\n")
+    (prof / "unstamped.md").write_text("dram_bytes_per_launch: kern_c 777\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._traffic("kern_a") == 123456.0
+    assert bench._profile_value_text("busiest_pipe_name", "kern_a") == "fp64"
+    assert bench._traffic("kern_b") is None
+    assert bench._traffic("kern_c") is None
+    assert bench._profile_value("dram_bytes_per_launch", "no_such_kernel") is None
 
 
 class _FakeProc:
@@ -112,6 +121,10 @@ def test_reference_arm_prints_one_contract_line(monkeypatch):
     assert d["cpu_baseline"]["value"] == d["value"] == d["e2e"]["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["iters"] <= 2
+    # the steps and warm-up actually run (at most 5 and 1), and what was asked
+    assert d["steps"] == 3 and d["warmup"] == 1
+    assert d["steps_requested"] == 3 and d["warmup_requested"] == 3
+    assert "preconditioner" in d["config"]
 
 
 def test_solution_error_against_time_stepping(monkeypatch):

@@ -239,23 +239,35 @@ def test_autograd_function_matches_oracle_and_finite_differences():
     assert abs(fd - k_t.grad.item()) <= 1e-6 * abs(k_t.grad.item())
 
 
-@pytest.mark.parametrize("ell", [512])
-def test_heat_n65535_large_workload(ell):
+@pytest.mark.parametrize("ell", [512, 1024])
+@pytest.mark.parametrize("prec", ["fp32", "fp32_refined"])
+def test_heat_n65535_large_workload(ell, prec):
     """The large workload's spatial size (n = 65535, 2.7e8 unknowns at
-    ell = 4096; here ell = 512 to keep the oracle's time stepping short):
-    FGMRES(20) with the FP32 circulant.  The FP64 representation floor of the
-    solution is 8.8e-9 here (extended-precision residual of the oracle's
-    solution), so the solve runs to 2e-8 and is checked for residual and for
-    solution error against time stepping."""
+    ell = 4096; here ell = 512 and 1024 to keep the oracle's time stepping
+    short): FGMRES(20) with the FP32 circulant, plain and refined.
+
+    The true relative residual of any FP64 iterate has a floor of about
+    eps64 ||A|| ||U|| / ||b|| (8.8e-9 here at ell = 512, measured as the
+    extended-precision residual of the oracle's FP64 solution), so the solve
+    stops at 2e-8.  That floor bounds the residual, not the solution, whose
+    FP64 rounding is ~1e-16.  The solution is checked at the mixed form's
+    accuracy target, relative error <= 1e-8, against the oracle's sine-mode
+    closed form: at this n, time stepping itself is only good to ~2e-8 (each
+    banded step solve loses eps 4 tau / h^2 on the smooth modes)."""
     torch = need_gpu()
     from paper_1810_00615_gb300 import AllAtOnce
     n = 65535
     S = oracle_system("heat", n, ell)
     u0 = syn.heat_initial(n, modes=8)
-    a = AllAtOnce(n, ell, 1.0 / ell, precision="fp32", restart=20)
+    a = AllAtOnce(n, ell, 1.0 / ell, precision=prec, restart=20)
     x, info = a.solve(a.build_rhs(to_dev(torch, u0)), restart=20, rtol=2e-8)
     assert info["converged"], info
-    _check(S, system.rhs_heat(S, u0), to_host(x), rtol=2e-8, errtol=1e-6)
+    X = to_host(x)
+    B = system.rhs_heat(S, u0)
+    relres = np.linalg.norm(B - system.matvec(S, X)) / np.linalg.norm(B)
+    assert relres <= 2e-8, relres
+    U = system.heat_modal_solution(n, np.full(ell, 1.0 / ell), u0)
+    assert rel_max(X, U) <= 1e-8, rel_max(X, U)
 
 
 def test_zero_initial_guess_never_reads_x():
