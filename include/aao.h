@@ -159,7 +159,10 @@ size_t aao_workspace_bytes(const aao_ctx *ctx, int restart);
 /* Hand the context a caller-allocated device workspace (256-byte aligned,
  * at least aao_workspace_bytes bytes for the restart lengths used later).
  * The caller keeps ownership and must keep it alive while the context uses
- * it.  AAO_EINVAL on NULL or misalignment. */
+ * it.  Writes the workspace's guard words (see aao_workspace_check) and
+ * synchronises the device.  AAO_EINVAL on NULL, misalignment or fewer bytes
+ * than aao_workspace_bytes(ctx, 0); every later call that needs more (a
+ * longer restart) returns AAO_EINVAL before launching anything. */
 int aao_set_workspace(aao_ctx *ctx, void *dev_ptr, size_t bytes);
 
 /* y = P^{-1} x (transpose = 0) or P^{-T} x (transpose = 1), Section 3:
@@ -315,6 +318,15 @@ int aao_profile_read(aao_ctx *ctx, double *ms, int64_t *launches, int reset);
 
 /* Total kernel launches made through this context since it was created. */
 int64_t aao_kernel_launches(const aao_ctx *ctx);
+
+/* Guard-word check of the workspace (not in the paper; a memory-safety aid).
+ * aao_set_workspace writes a guard of 256 bytes (pattern 0xA5) before every
+ * region of the workspace and after every basis vector of the largest restart
+ * length the workspace holds; this call waits for the device, reads them back
+ * and stores in *damaged the number of 8-byte guard words that no longer hold
+ * the pattern (0: no kernel wrote outside its region).  AAO_EINVAL without a
+ * workspace or with damaged == NULL; AAO_ECUDA if a copy fails. */
+int aao_workspace_check(aao_ctx *ctx, int64_t *damaged);
 
 /* y = P^{-1} x (or P^{-T} x) exactly like aao_precond_apply, but without a
  * caller workspace: the frequency-domain scratch is a fixed array of 32 MiB

@@ -13,6 +13,7 @@ the preconditioners, Section 3 the Fourier diagonalisation applied here.
 from __future__ import annotations
 
 import ctypes as C
+import weakref
 from typing import Optional
 
 import numpy as np
@@ -62,6 +63,9 @@ class AllAtOnce:
     preconditioner; the outer GMRES is FP64 either way.
     """
 
+    # every live instance (for workspace guard checks after a test or a run)
+    _live: "weakref.WeakSet[AllAtOnce]" = weakref.WeakSet()
+
     def __init__(self, n: int, ell: int, tau: Optional[float] = None, equation="heat",
                  kappa: float = 1.0, precision: str = "fp32", restart: int = 30,
                  device=None, space: str = "tridiag"):
@@ -85,6 +89,7 @@ class AllAtOnce:
         self._ws = None
         self._restart = 0
         self.ensure_workspace(restart)
+        AllAtOnce._live.add(self)
 
     # ------------------------------------------------------------ settings
     def __del__(self):
@@ -297,6 +302,19 @@ class AllAtOnce:
 
     def kernel_launches(self) -> int:
         return int(self.lib.aao_kernel_launches(self._ctx))
+
+    def workspace_check(self) -> int:
+        """Number of damaged 8-byte guard words around the workspace's regions
+        and basis vectors (0: no kernel wrote outside its region)."""
+        bad = C.c_int64(0)
+        with torch.cuda.device(self.device):
+            check(self.lib.aao_workspace_check(self._ctx, C.byref(bad)), "aao_workspace_check",
+                  self._ctx)
+        return int(bad.value)
+
+    @classmethod
+    def live_instances(cls):
+        return list(cls._live)
 
     def solve_host(self, u0: torch.Tensor, v0: Optional[torch.Tensor] = None, out=None,
                    restart=30, rtol=1e-10, maxit=300, precond=1, stream=None):

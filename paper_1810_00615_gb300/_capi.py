@@ -78,6 +78,7 @@ SIGNATURES = {
     "aao_check_conversions": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                         C.c_void_p]),
+    "aao_workspace_check": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "aao_strerror": (C.c_char_p, [C.c_int]),
     "aao_last_error": (C.c_char_p, [C.c_void_p]),
 }

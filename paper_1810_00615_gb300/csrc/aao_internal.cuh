@@ -387,6 +387,7 @@ struct Ctx {
   // caller workspace
   char *ws = nullptr;
   size_t ws_bytes = 0;
+  int ws_restart = 0;     // largest restart length the workspace holds (its guards)
 
   std::string last_error;
 
@@ -431,10 +432,12 @@ struct WsLayout {
   size_t rf64 = 0;        // refined apply: residual, Neumann right-hand side (2 x N doubles)
   size_t dots = 0;        // block partials of the matvec with fused dots
   size_t vecs = 0;        // first FP64 vector (V_0 ...)
-  size_t vec_bytes = 0;   // bytes per vector (rounded)
+  size_t vec_bytes = 0;   // bytes per vector (rounded, with the guard that follows it)
+  int nvec = 0;           // vectors
   size_t total = 0;
 };
 WsLayout ws_layout(const Ctx &c, int restart);
+std::vector<size_t> ws_guards(const WsLayout &L);
 
 // Run a launcher attributed to kernel class `cls` (AAO_K_*): its launches
 // are added to the context's counts and, while profiling is on, bracketed

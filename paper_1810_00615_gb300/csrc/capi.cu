@@ -28,6 +28,8 @@ constexpr int64_t kMaxEll = 4096;
 constexpr int64_t kMaxN = 65535;
 constexpr int64_t kMaxNAnyShape = 16383;   // beyond this the row must split into clusters
 constexpr size_t kAlign = 256;
+constexpr size_t kGuard = 256;               // workspace guard bytes (pattern kGuardByte)
+constexpr unsigned char kGuardByte = 0xA5;
 constexpr int kPartials = 152 * 8 * 16;      // doubles for block partials
 constexpr int kSmall = 1024;                 // doubles for device-side small results
 
@@ -578,21 +580,33 @@ cudaError_t kernel_setup(const void *kern, int threads, size_t smem, int *reside
 }
 
 WsLayout ws_layout(const Ctx &c, int restart) {
+  // every region is preceded by a guard of kGuard bytes and every basis
+  // vector followed by one (guard words, checked by aao_workspace_check)
   WsLayout L;
-  L.spec = 0;
+  L.spec = kGuard;
   L.spec_bytes = round_up((size_t)c.nk * (size_t)c.n_pad * sizeof(cx<double>), kAlign);
-  L.inter = L.spec + L.spec_bytes;
+  L.inter = L.spec + L.spec_bytes + kGuard;
   L.inter_bytes = round_up(std::max(fft_inter_bytes_f32(c), fft_inter_bytes_f64(c)), kAlign);
-  L.red = L.inter + L.inter_bytes;
+  L.red = L.inter + L.inter_bytes + kGuard;
   L.red_bytes = round_up((size_t)(kPartials + kSmall) * sizeof(double), kAlign);
-  L.rf32 = L.red + L.red_bytes;
-  L.rf64 = L.rf32 + round_up((size_t)c.N * sizeof(float), kAlign);
-  L.dots = L.rf64 + 2 * round_up((size_t)c.N * sizeof(double), kAlign);
-  L.vecs = L.dots + round_up(aao::matvec_dot_partials(c) * sizeof(double), kAlign);
-  L.vec_bytes = round_up((size_t)c.N * sizeof(double), kAlign);
+  L.rf32 = L.red + L.red_bytes + kGuard;
+  L.rf64 = L.rf32 + round_up((size_t)c.N * sizeof(float), kAlign) + kGuard;
+  L.dots = L.rf64 + 2 * round_up((size_t)c.N * sizeof(double), kAlign) + kGuard;
+  L.vecs = L.dots + round_up(aao::matvec_dot_partials(c) * sizeof(double), kAlign) + kGuard;
+  L.vec_bytes = round_up((size_t)c.N * sizeof(double), kAlign) + kGuard;   // vector + guard
   const int nvec = restart > 0 ? (restart + 1) + restart + 2 : 0;
+  L.nvec = nvec;
   L.total = L.vecs + (size_t)nvec * L.vec_bytes;
   return L;
+}
+
+// Offsets of the guards of a layout: before each region and after each
+// vector, kGuard bytes each.
+std::vector<size_t> ws_guards(const WsLayout &L) {
+  std::vector<size_t> g = {L.spec - kGuard, L.inter - kGuard, L.red - kGuard, L.rf32 - kGuard,
+                           L.rf64 - kGuard, L.dots - kGuard, L.vecs - kGuard};
+  for (int j = 0; j < L.nvec; j++) g.push_back(L.vecs + (size_t)(j + 1) * L.vec_bytes - kGuard);
+  return g;
 }
 }  // namespace aao
 
@@ -613,10 +627,43 @@ int check_ws(const Ctx &c, int restart) {
 // separator systems (TRIDIAG), corrections + inverse transform
 // (FFT_INVERSE).  Input x (FP64) or x32 (FP32); output YT, with base
 // (FP64 output) y = base - P^{-1} x.
+// Extent checks of the apply's launches (on by default; -DAAO_DEBUG_BOUNDS=0
+// drops them): the bytes each kernel's grid reads or writes in a workspace
+// region, from the launch geometry, against the region's size.  A failure
+// returns cudaErrorInvalidValue before anything is launched.
+#ifndef AAO_DEBUG_BOUNDS
+#define AAO_DEBUG_BOUNDS 1
+#endif
+bool apply_extents_ok(const Ctx &c, const aao::WsLayout &L, bool fused) {
+#if AAO_DEBUG_BOUNDS
+  if (c.prec == AAO_PREC_FP32) {
+    // spectrum rows k < nk of n_pad complex64, then (fused) the separator data
+    size_t need = (size_t)c.nk * (size_t)c.n_pad * sizeof(cx<float>);
+    if (fused) {
+      if (aao::fused_sep_offset(c) < need) return false;
+      need = aao::fused_sep_offset(c) + aao::fused_sep_bytes(c);
+      // the forward kernels write 16 P values of every row (n_pad >= 16 P)
+      if ((size_t)c.n_pad < (size_t)16 * (size_t)c.P32) return false;
+    }
+    if (need > L.spec_bytes) return false;
+    if (aao::fft_inter_bytes_f32(c) > L.inter_bytes) return false;
+  } else {
+    if ((size_t)c.nk * (size_t)c.n_pad * sizeof(cx<double>) > L.spec_bytes) return false;
+    if (aao::fft_inter_bytes_f64(c) > L.inter_bytes) return false;
+  }
+  if (L.spec + L.spec_bytes > L.inter || L.inter + L.inter_bytes > L.red) return false;
+  if (L.total > c.ws_bytes) return false;
+#else
+  (void)c; (void)L; (void)fused;
+#endif
+  return true;
+}
+
 template <typename YT>
 cudaError_t precond_fused(Ctx &c, const double *x, const float *x32, YT *y, int tr,
                           cudaStream_t s, const float *base = nullptr) {
   const aao::WsLayout L = aao::ws_layout(c, 0);
+  if (!apply_extents_ok(c, L, true)) return cudaErrorInvalidValue;
   void *spec = c.ws + L.spec;
   void *inter = c.ws + L.inter;
   void *sep = static_cast<char *>(spec) + aao::fused_sep_offset(c);
@@ -645,6 +692,7 @@ cudaError_t precond_once(Ctx &c, const double *x, const YT *yprev, YT *y, int tr
   const bool f32 = c.prec == AAO_PREC_FP32;
   if (f32 && !yprev && inter && aao::fft_fused_supported(c))
     return precond_fused<YT>(c, x, nullptr, y, tr, s, base);
+  if (!apply_extents_ok(c, L, false)) return cudaErrorInvalidValue;
   cudaError_t e = run(c, AAO_K_FFT_FORWARD, s, [&] {
     if constexpr (sizeof(YT) == 4) return aao::fft_forward_f32_yf(c, x, yprev, spec, s, inter);
     else return f32 ? aao::fft_forward_f32(c, x, yprev, spec, s, inter)
@@ -1246,8 +1294,35 @@ size_t aao_workspace_bytes(const aao_ctx *ctx, int restart) {
 int aao_set_workspace(aao_ctx *ctx, void *dev_ptr, size_t bytes) {
   if (!ctx || !dev_ptr || (reinterpret_cast<uintptr_t>(dev_ptr) % kAlign) != 0) return AAO_EINVAL;
   if (bytes < aao::ws_layout(ctx->c, 0).total) return AAO_EINVAL;
-  ctx->c.ws = static_cast<char *>(dev_ptr);
-  ctx->c.ws_bytes = bytes;
+  Ctx &c = ctx->c;
+  c.ws = static_cast<char *>(dev_ptr);
+  c.ws_bytes = bytes;
+  // guard words of the largest layout that fits: the restart length is the
+  // largest one the bytes hold
+  int m = 0;
+  while (m < kMaxRestart && aao::ws_layout(c, m + 1).total <= bytes) m++;
+  c.ws_restart = m;
+  for (size_t g : aao::ws_guards(aao::ws_layout(c, m)))
+    AAO_CK(c, cudaMemset(c.ws + g, kGuardByte, kGuard));
+  AAO_CK(c, cudaDeviceSynchronize());
+  return AAO_OK;
+}
+
+int aao_workspace_check(aao_ctx *ctx, int64_t *damaged) {
+  if (!ctx || !damaged) return AAO_EINVAL;
+  Ctx &c = ctx->c;
+  *damaged = 0;
+  if (!c.ws) return AAO_EINVAL;
+  AAO_CK(c, cudaDeviceSynchronize());
+  unsigned char buf[kGuard];
+  for (size_t g : aao::ws_guards(aao::ws_layout(c, c.ws_restart))) {
+    AAO_CK(c, cudaMemcpy(buf, c.ws + g, kGuard, cudaMemcpyDeviceToHost));
+    for (size_t w = 0; w < kGuard; w += 8) {
+      bool ok = true;
+      for (size_t q = 0; q < 8; q++) ok = ok && buf[w + q] == kGuardByte;
+      if (!ok) ++*damaged;
+    }
+  }
   return AAO_OK;
 }
 

@@ -261,3 +261,29 @@ def test_wave_apply_backward_error_at_scale(kind, n, ell, prec):
             assert eta <= bw_tol(n, ell, U64 if prec == "fp64" else U32), (tr, eta)
         if n * ell > 4_000_000:
             break
+
+
+def test_short_workspace_is_rejected_before_any_launch():
+    """A workspace shorter than the layout needs is refused by
+    aao_set_workspace, and a solve asking for a longer restart than the
+    workspace holds returns AAO_EINVAL without launching a kernel; the guard
+    words of the workspace stay intact throughout."""
+    torch = need_gpu()
+    import ctypes as C
+    from paper_1810_00615_gb300 import AllAtOnce, _capi
+    lib = _capi.lib()
+    n, ell = 63, 64
+    a = AllAtOnce(n, ell, 1.0 / ell, restart=2)
+    need0 = a.workspace_bytes(0)
+    buf = torch.empty(need0, dtype=torch.uint8, device="cuda")
+    base = buf.data_ptr() + (-buf.data_ptr()) % 256
+    assert lib.aao_set_workspace(a._ctx, C.c_void_p(base), need0 - 4096) == _capi.AAO_EINVAL
+    b = a.build_rhs(to_dev(torch, syn.heat_initial(n)))
+    x = torch.zeros_like(b)
+    before = a.kernel_launches()
+    st = lib.aao_gmres_solve(a._ctx, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), 20,
+                             1e-10, 100, 1, None,
+                             C.c_void_p(int(torch.cuda.current_stream().cuda_stream)))
+    assert st == _capi.AAO_EINVAL
+    assert a.kernel_launches() == before
+    assert a.workspace_check() == 0
