@@ -298,19 +298,27 @@ int aao_solve_host(aao_ctx *ctx, const double *u0_host, const double *v0_host,
                    double *U_host, int restart, double rtol, int maxit,
                    int precond, aao_solve_info *info, void *stream);
 
-/* Kernel classes for aao_profile_read: the three stages of a preconditioner
- * apply, the matvec, the Arnoldi kernels, and the residual P z0 - x (or the
- * Neumann right-hand side) of the refined FP32 apply. */
+/* Kernel classes for aao_profile_read: the stages of a preconditioner apply,
+ * the matvec, the Arnoldi kernels, and the residual P z0 - x (or the Neumann
+ * right-hand side) of the refined FP32 apply.  Where the FP32 apply folds the
+ * tridiagonal solves into its transform (ell = 256 ... 4096 a power of two,
+ * n + 1 = 16 P), FFT_FORWARD is its first forward kernel, FFT_FORWARD_SOLVE
+ * the second forward kernel with the chunk solves, TRIDIAG the separator
+ * systems, FFT_INVERSE_SOLVE the first inverse kernel with the chunk
+ * corrections and FFT_INVERSE the last inverse kernel; elsewhere the two
+ * *_SOLVE classes stay empty. */
 enum {
   AAO_K_FFT_FORWARD = 0, AAO_K_TRIDIAG = 1, AAO_K_FFT_INVERSE = 2, AAO_K_MATVEC = 3,
   AAO_K_DOTS = 4, AAO_K_UPDATE = 5, AAO_K_COMBINE = 6, AAO_K_OTHER = 7, AAO_K_REFINE = 8,
-  AAO_K_COUNT = 9
+  AAO_K_FFT_FORWARD_SOLVE = 9, AAO_K_FFT_INVERSE_SOLVE = 10,
+  AAO_K_COUNT = 11
 };
 
 /* Profiling (not in the paper): while on != 0 every kernel the context
  * launches is bracketed by two CUDA events on its stream.  aao_profile_read
- * waits for the recorded events, adds their durations per class to ms[9]
- * (milliseconds) and the number of kernel launches per class to launches[9]
+ * waits for the recorded events, adds their durations per class to
+ * ms[AAO_K_COUNT] (milliseconds) and the number of kernel launches per class
+ * to launches[AAO_K_COUNT]
  * (either may be NULL), and clears the totals if reset != 0.  Launches are
  * counted whether or not timing is on. */
 int aao_profile_enable(aao_ctx *ctx, int on);

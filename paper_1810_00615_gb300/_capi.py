@@ -19,7 +19,8 @@ AAO_GUESS_GIVEN, AAO_GUESS_ZERO = 0, 1
 AAO_OK, AAO_ENOCONV = 0, 1
 AAO_EINVAL, AAO_ENOMEM, AAO_ECUDA, AAO_ENUMERIC, AAO_EUNSUPPORTED = -1, -2, -3, -4, -5
 KERNEL_CLASSES = ["fft_forward", "tridiag", "fft_inverse", "matvec", "dots", "update",
-                  "combine", "other", "refine"]
+                  "combine", "other", "refine", "fft_forward_solve",
+                  "fft_inverse_solve"]
 
 
 class SolveInfo(C.Structure):

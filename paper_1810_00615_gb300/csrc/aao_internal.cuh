@@ -501,14 +501,16 @@ cudaError_t launch_tridiag(const Ctx &c, void *spec, int prec, int transpose,
 bool fft_fused_supported(const Ctx &c);
 size_t fused_sep_offset(const Ctx &c);
 size_t fused_sep_bytes(const Ctx &c);
+// part: 0 both kernels of the half, 1 the first, 2 the second.
 cudaError_t fft_forward_f32_solve(const Ctx &c, const double *x, const float *x32, void *spec,
-                                  void *sep, int transpose, cudaStream_t s, void *inter);
+                                  void *sep, int transpose, cudaStream_t s, void *inter,
+                                  int part = 0);
 cudaError_t launch_tridiag_reduced_fused(const Ctx &c, void *sep, int transpose, cudaStream_t s);
 cudaError_t launch_tridiag_reduced(const Ctx &c, const void *sepbuf, void *sepsol, int transpose,
                                    cudaStream_t s);
 cudaError_t fft_inverse_f32_correct(const Ctx &c, const void *spec, void *sep, double *y,
                                     float *y32, int transpose, cudaStream_t s, void *inter,
-                                    const float *base);
+                                    const float *base, int part = 0);
 // The same solves by DST-I in space (AAO_SPACE_DST), in place on the spectrum.
 constexpr int64_t kDstMaxL = 4096;   // n + 1 <= kDstMaxL, a power of two
 bool dst_supported(int64_t n);

@@ -667,16 +667,31 @@ cudaError_t precond_fused(Ctx &c, const double *x, const float *x32, YT *y, int 
   void *spec = c.ws + L.spec;
   void *inter = c.ws + L.inter;
   void *sep = static_cast<char *>(spec) + aao::fused_sep_offset(c);
+  // with profiling on, each kernel gets its own class (and its own events,
+  // which serialise the chain); otherwise each half is one launcher call
+  const bool each = c.prof_on;
   cudaError_t e = run(c, AAO_K_FFT_FORWARD, s, [&] {
-    return aao::fft_forward_f32_solve(c, x, x32, spec, sep, tr, s, inter);
+    return aao::fft_forward_f32_solve(c, x, x32, spec, sep, tr, s, inter, each ? 1 : 0);
   });
   if (e != cudaSuccess) return e;
+  if (each) {
+    e = run(c, AAO_K_FFT_FORWARD_SOLVE, s, [&] {
+      return aao::fft_forward_f32_solve(c, x, x32, spec, sep, tr, s, inter, 2);
+    });
+    if (e != cudaSuccess) return e;
+  }
   e = run(c, AAO_K_TRIDIAG, s, [&] { return aao::launch_tridiag_reduced_fused(c, sep, tr, s); });
   if (e != cudaSuccess) return e;
-  return run(c, AAO_K_FFT_INVERSE, s, [&] {
-    if constexpr (sizeof(YT) == 4) return aao::fft_inverse_f32_correct(c, spec, sep, nullptr, y, tr, s, inter, nullptr);
-    else return aao::fft_inverse_f32_correct(c, spec, sep, y, nullptr, tr, s, inter, base);
-  });
+  auto inverse = [&](int part) {
+    if constexpr (sizeof(YT) == 4) return aao::fft_inverse_f32_correct(c, spec, sep, nullptr, y, tr, s, inter, nullptr, part);
+    else return aao::fft_inverse_f32_correct(c, spec, sep, y, nullptr, tr, s, inter, base, part);
+  };
+  if (each) {
+    e = run(c, AAO_K_FFT_INVERSE_SOLVE, s, [&] { return inverse(1); });
+    if (e != cudaSuccess) return e;
+    return run(c, AAO_K_FFT_INVERSE, s, [&] { return inverse(2); });
+  }
+  return run(c, AAO_K_FFT_INVERSE, s, [&] { return inverse(0); });
 }
 
 // One application of P^{-1} (or P^{-T}); with yprev, of P^{-1}(x - E yprev).// One application of P^{-1} (or P^{-T}); with yprev, of P^{-1}(x - E yprev).

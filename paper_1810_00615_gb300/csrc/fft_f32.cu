@@ -55,7 +55,8 @@ static cx<float> *sepsol_of(const Ctx &c, void *sep) {
   return reinterpret_cast<cx<float> *>(static_cast<float4 *>(sep) + (size_t)c.nk * c.P32);
 }
 cudaError_t fft_forward_f32_solve(const Ctx &c, const double *x, const float *x32, void *spec,
-                                  void *sep, int transpose, cudaStream_t s, void *inter) {
+                                  void *sep, int transpose, cudaStream_t s, void *inter,
+                                  int part) {
   if (!fft_fused_supported(c) || !inter || (!x == !x32)) return cudaErrorNotSupported;
   auto *sp = static_cast<cx<float> *>(spec);
   auto *sb = sepbuf_of(sep);
@@ -64,9 +65,9 @@ cudaError_t fft_forward_f32_solve(const Ctx &c, const double *x, const float *x3
 #define AAO_FS(L)                                                                                  \
   case L:                                                                                          \
     return x ? fft::four_forward_solve<L, double>(c.n, c.n_pad, P, x, sp, sb, c.tw32, s, inter,   \
-                                                  tb, tr)                                          \
+                                                  tb, tr, part)                                    \
              : fft::four_forward_solve<L, float>(c.n, c.n_pad, P, x32, sp, sb, c.tw32, s, inter,  \
-                                                 tb, tr);
+                                                 tb, tr, part);
   switch (c.ell) {
     AAO_FS(256) AAO_FS(512) AAO_FS(1024) AAO_FS(2048) AAO_FS(4096)
     default: return cudaErrorNotSupported;
@@ -78,7 +79,7 @@ cudaError_t launch_tridiag_reduced_fused(const Ctx &c, void *sep, int transpose,
 }
 cudaError_t fft_inverse_f32_correct(const Ctx &c, const void *spec, void *sep, double *y,
                                     float *y32, int transpose, cudaStream_t s, void *inter,
-                                    const float *base) {
+                                    const float *base, int part) {
   if (!fft_fused_supported(c) || !inter || (!y == !y32) || (y32 && base))
     return cudaErrorNotSupported;
   auto *sp = static_cast<const cx<float> *>(spec);
@@ -88,9 +89,9 @@ cudaError_t fft_inverse_f32_correct(const Ctx &c, const void *spec, void *sep, d
 #define AAO_IC(L)                                                                               \
   case L:                                                                                       \
     return y ? fft::four_inverse_correct<L, double>(c.n, c.n_pad, P, sp, sv, P, y, c.tw32, s,  \
-                                                    inter, base, tb, tr)                        \
+                                                    inter, base, tb, tr, part)                  \
              : fft::four_inverse_correct<L, float>(c.n, c.n_pad, P, sp, sv, P, y32, c.tw32, s, \
-                                                   inter, nullptr, tb, tr);
+                                                   inter, nullptr, tb, tr, part);
   switch (c.ell) {
     AAO_IC(256) AAO_IC(512) AAO_IC(1024) AAO_IC(2048) AAO_IC(4096)
     default: return cudaErrorNotSupported;

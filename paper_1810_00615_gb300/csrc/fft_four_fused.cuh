@@ -381,57 +381,68 @@ k_fft4_inverseA_correct(const cx<float> *__restrict__ spec, const cx<float> *__r
 }
 
 // x (FP64 or FP32) -> local solutions in spec and the chunks' separator data
-// in sepbuf (forward 1, forward 2 + solves).
+// in sepbuf: forward 1 (part 1), forward 2 + solves (part 2), or both (0).
 template <int L, typename XT>
 cudaError_t four_forward_solve(int64_t n, int64_t n_pad, int nchunks, const XT *x, cx<float> *spec,
                                float4 *sepbuf, const cx<float> *tw, cudaStream_t s, void *inter,
-                               const float4 *tabs, int conj) {
+                               const float4 *tabs, int conj, int part = 0) {
   constexpr int L1 = Four<L>::L1, L2 = Four<L>::L2, W = kFourW;
   constexpr size_t sm1 = (size_t)L1 * W * sizeof(cx<float>);
   constexpr size_t sm2 = fuse_smem<L, kFwdPairs, 0>();
   const int ncx = (int)four_ncx(n);
   cx<float> *ip = static_cast<cx<float> *>(inter);
-  cudaError_t e = kernel_setup((const void *)k_fft4_forward1<L, W, XT>, kFourT, sm1);
-  if (e == cudaSuccess)
+  cudaError_t e = cudaSuccess;
+  if (part != 2) {
+    e = kernel_setup((const void *)k_fft4_forward1<L, W, XT>, kFourT, sm1);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(k_fft4_forward1<L, W, XT>, dim3((unsigned)(ncx / W), L2), dim3(kFourT), sm1, s,
+                   x, ip, (int)n, ncx, tw);
+    note_launch();
+    if (e != cudaSuccess) return e;
+  }
+  if (part != 1) {
     e = kernel_setup((const void *)k_fft4_forward2_solve<L, W>, kFourT, sm2, nullptr, true);
-  if (e != cudaSuccess) return e;
-  e = launch_pdl(k_fft4_forward1<L, W, XT>, dim3((unsigned)(ncx / W), L2), dim3(kFourT), sm1, s,
-                 x, ip, (int)n, ncx, tw);
-  note_launch();
-  if (e != cudaSuccess) return e;
-  e = launch_pdl(k_fft4_forward2_solve<L, W>, dim3((unsigned)(ncx / W), L1 / 2 + 1), dim3(kFourT),
-                 sm2, s, ip, spec, sepbuf, ncx, n_pad, nchunks, tw,
-                 four_discard_ok(ip, spec, n_pad) ? 1 : 0, tabs, conj);
-  note_launch();
-  if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(k_fft4_forward2_solve<L, W>, dim3((unsigned)(ncx / W), L1 / 2 + 1),
+                   dim3(kFourT), sm2, s, ip, spec, sepbuf, ncx, n_pad, nchunks, tw,
+                   four_discard_ok(ip, spec, n_pad) ? 1 : 0, tabs, conj);
+    note_launch();
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 
-// local solutions + separators -> y (corrections + inverse A, inverse B).
+// local solutions + separators -> y: corrections + inverse A (part 1),
+// inverse B (part 2), or both (0).
 template <int L, typename OT>
 cudaError_t four_inverse_correct(int64_t n, int64_t n_pad, int nchunks, const cx<float> *spec,
                                  const cx<float> *sep, int64_t sstride, OT *y, const cx<float> *tw,
                                  cudaStream_t s, void *inter, const float *base,
-                                 const float4 *tabs, int conj) {
+                                 const float4 *tabs, int conj, int part = 0) {
   constexpr int L1 = Four<L>::L1, L2 = Four<L>::L2, W = kFourW;
   constexpr size_t sm1 = (size_t)L1 * W * sizeof(cx<float>);
   constexpr size_t sm2 = fuse_smem<L, kInvPairs, kInvSeps>();
   const int ncx = (int)four_ncx(n);
   cx<float> *ip = static_cast<cx<float> *>(inter);
-  cudaError_t e =
-      kernel_setup((const void *)k_fft4_inverseA_correct<L, W>, kFourT, sm2, nullptr, true);
-  if (e == cudaSuccess) e = kernel_setup((const void *)k_fft4_inverseB<L, W, OT>, kFourT, sm1);
-  if (e != cudaSuccess) return e;
   const int dis = four_discard_ok(ip, spec, n_pad) ? 1 : 0;
-  e = launch_pdl(k_fft4_inverseA_correct<L, W>, dim3((unsigned)(ncx / W), L1 / 2 + 1),
-                 dim3(kFourT), sm2, s, spec, sep, ip, ncx, n_pad, nchunks, sstride, tw, dis, tabs,
-                 conj);
-  note_launch();
-  if (e != cudaSuccess) return e;
-  e = launch_pdl(k_fft4_inverseB<L, W, OT>, dim3((unsigned)(ncx / W), L2), dim3(kFourT), sm1, s, ip,
-                 y, (int)n, ncx, tw, base, dis);
-  note_launch();
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (part != 2) {
+    e = kernel_setup((const void *)k_fft4_inverseA_correct<L, W>, kFourT, sm2, nullptr, true);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(k_fft4_inverseA_correct<L, W>, dim3((unsigned)(ncx / W), L1 / 2 + 1),
+                   dim3(kFourT), sm2, s, spec, sep, ip, ncx, n_pad, nchunks, sstride, tw, dis,
+                   tabs, conj);
+    note_launch();
+    if (e != cudaSuccess) return e;
+  }
+  if (part != 1) {
+    e = kernel_setup((const void *)k_fft4_inverseB<L, W, OT>, kFourT, sm1);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(k_fft4_inverseB<L, W, OT>, dim3((unsigned)(ncx / W), L2), dim3(kFourT), sm1, s,
+                   ip, y, (int)n, ncx, tw, base, dis);
+    note_launch();
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 
