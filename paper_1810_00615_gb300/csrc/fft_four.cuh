@@ -148,15 +148,21 @@ k_fft4_forward1(const XT *__restrict__ x, cx<float> *__restrict__ inter, int n, 
   dft_columns<L1, W, L, -1>(S, tw);
   // row k1 = DFT output; times w^{t2 k1}.  Element (h, thread): k1 =
   // KPH h + thread / W, c = thread % W.
-  constexpr int KPH = kFourT / W;
-  cx<float> *pi = inter + ((size_t)(threadIdx.x / W) * L2 + t2) * ncx + W * blockIdx.x +
-                  threadIdx.x % W;
+  // two adjacent columns per thread: one 16-byte read, one twiddle, one
+  // 16-byte store.  Element (h, thread): k1 = KPH h + thread / (W/2),
+  // columns 2 (thread % (W/2)) and the next.
+  constexpr int HW = W / 2, KPH = kFourT / HW;
+  static_assert((L1 * HW) % kFourT == 0, "whole pairs per thread");
+  const int kr = threadIdx.x / HW, cp = 2 * (threadIdx.x % HW);
+  cx<float> *pi = inter + ((size_t)kr * L2 + t2) * ncx + W * blockIdx.x + cp;
   const size_t hstride = (size_t)KPH * L2 * ncx;
 #pragma unroll
-  for (int h = 0; h < L1 * W / kFourT; h++) {
-    const int k1 = KPH * h + threadIdx.x / W;
-    const cx<float> v = twiddle<float, -1>(S[h * kFourT + threadIdx.x], tw[t2 * k1]);
-    st_hint(pi + h * hstride, v, pol_keep);
+  for (int h = 0; h < L1 * HW / kFourT; h++) {
+    const int k1 = KPH * h + kr;
+    const float4 v2 = *reinterpret_cast<const float4 *>(S + k1 * W + cp);
+    const cx<float> w = tw[t2 * k1];
+    st_hint2(pi + h * hstride, twiddle<float, -1>(mk(v2.x, v2.y), w),
+             twiddle<float, -1>(mk(v2.z, v2.w), w), pol_keep);
   }
 }
 

@@ -115,6 +115,23 @@ __device__ __forceinline__ void unpair(const float4 q, cx<float> &a, cx<float> &
   b = mk(q.z, q.w);
 }
 
+// load_rows with two adjacent columns per thread (16-byte loads): the L2
+// rows inter[k1][0..L2) of W columns from cb into S (row stride SW, even).
+template <int L2, int W, int SW>
+__device__ __forceinline__ void load_rows2(const cx<float> *__restrict__ inter, int k1, int ncx,
+                                           int cb, cx<float> *S, unsigned long long pol) {
+  constexpr int HW = W / 2, U = L2 * HW / kFourT, RPU = kFourT / HW;
+  static_assert(U >= 1 && (L2 * HW) % kFourT == 0 && SW % 2 == 0, "whole pairs per thread");
+  const int rr = threadIdx.x / HW, cp = 2 * (threadIdx.x % HW);
+  const cx<float> *pr = inter + ((size_t)k1 * L2 + rr) * ncx + cb + cp;
+  const size_t ustride = (size_t)RPU * ncx;
+  float4 v[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) v[u] = ld_hint4(reinterpret_cast<const float4 *>(pr + u * ustride), pol);
+#pragma unroll
+  for (int u = 0; u < U; u++) *reinterpret_cast<float4 *>(S + (RPU * u + rr) * SW + cp) = v[u];
+}
+
 // Shared memory of the two middle kernels: the DFT buffers S0, S1 (L2 rows
 // of stride SW each; the staging rows reuse them), then NP table pairs per
 // frequency, then (inverse only) five separator values per frequency.
@@ -151,8 +168,8 @@ k_fft4_forward2_solve(const cx<float> *__restrict__ inter, cx<float> *__restrict
     TabStage<L, kFwdPairs> tab;
     tab.load(ft, 0, G);                                     // constant tables
     pdl_wait(inter);                                        // the previous kernel's output
-    load_rows<L2, W, SW>(inter, G.g, ncx, cb, S0, pol_done);
-    if (G.pair) load_rows<L2, W, SW>(inter, G.gb, ncx, cb, S1, pol_done);
+    load_rows2<L2, W, SW>(inter, G.g, ncx, cb, S0, pol_done);
+    if (G.pair) load_rows2<L2, W, SW>(inter, G.gb, ncx, cb, S1, pol_done);
     pdl_trigger();
     tab.store(sT, G, conj_sym);
   }
@@ -370,13 +387,19 @@ k_fft4_inverseA_correct(const cx<float> *__restrict__ spec, const cx<float> *__r
   __syncthreads();
   dft_columns<L2, W, L, +1, SW>(S0, tw);
   if (G.pair) dft_columns<L2, W, L, +1, SW>(S1, tw);
-  for (int e = threadIdx.x; e < 2 * L2 * W; e += kFourT) {
-    const int mm = e / (L2 * W);
+  // two adjacent columns per thread: one 16-byte read, one twiddle, one
+  // 16-byte store
+  constexpr int HW = W / 2;
+  for (int e = threadIdx.x; e < 2 * L2 * HW; e += kFourT) {
+    const int mm = e / (L2 * HW);
     if (mm == 1 && !G.pair) break;
-    const int r = e - mm * L2 * W, t2 = r / W, c = r - t2 * W;
+    const int r = e - mm * L2 * HW, t2 = r / HW, c = 2 * (r - t2 * HW);
     const int kk1 = mm ? G.gb : G.g;
-    const cx<float> val = twiddle<float, +1>((mm ? S1 : S0)[t2 * SW + c], tw[t2 * kk1]);
-    st_hint(inter + ((size_t)kk1 * L2 + t2) * ncx + cb + c, val, pol_keep);
+    const float4 v2 = *reinterpret_cast<const float4 *>((mm ? S1 : S0) + t2 * SW + c);
+    const cx<float> w = tw[t2 * kk1];
+    st_hint2(inter + ((size_t)kk1 * L2 + t2) * ncx + cb + c,
+             twiddle<float, +1>(mk(v2.x, v2.y), w), twiddle<float, +1>(mk(v2.z, v2.w), w),
+             pol_keep);
   }
 }
 
