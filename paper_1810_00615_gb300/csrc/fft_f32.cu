@@ -62,12 +62,13 @@ cudaError_t fft_forward_f32_solve(const Ctx &c, const double *x, const float *x3
   auto *sb = sepbuf_of(sep);
   auto *tb = static_cast<const float4 *>(c.fuse32);
   const int P = c.P32, tr = transpose ? 1 : 0;
+  const int rb = (int)sizeof(RecTab<float, fft::kFuseCH>);   // one frequency's table
 #define AAO_FS(L)                                                                                  \
   case L:                                                                                          \
     return x ? fft::four_forward_solve<L, double>(c.n, c.n_pad, P, x, sp, sb, c.tw32, s, inter,   \
-                                                  tb, tr, part)                                    \
+                                                  tb, tr, part, c.rec32, rb)                       \
              : fft::four_forward_solve<L, float>(c.n, c.n_pad, P, x32, sp, sb, c.tw32, s, inter,  \
-                                                 tb, tr, part);
+                                                 tb, tr, part, c.rec32, rb);
   switch (c.ell) {
     AAO_FS(256) AAO_FS(512) AAO_FS(1024) AAO_FS(2048) AAO_FS(4096)
     default: return cudaErrorNotSupported;

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kFourT, AAO_FUSE_MINB)
 k_fft4_forward2_solve(const cx<float> *__restrict__ inter, cx<float> *__restrict__ spec,
                       float4 *__restrict__ sepbuf, int ncx, int64_t n_pad, int nchunks,
                       const cx<float> *__restrict__ tw, int discard, const float4 *__restrict__ ft,
-                      int conj_sym) {
+                      int conj_sym, const char *__restrict__ rtab, int rtab_bytes) {
   constexpr int L1 = Four<L>::L1, L2 = Four<L>::L2;
   constexpr int SW = fuse_sw<W>(), TWS = fuse_tw<W>();
   constexpr int NQ = 2 * W / kFuseCH;                       // chunks per CTA
@@ -175,6 +175,15 @@ k_fft4_forward2_solve(const cx<float> *__restrict__ inter, cx<float> *__restrict
   }
   __syncthreads();
   if (discard) discard_rows<L2, W>(inter, G.g, G.pair ? G.gb : -1, 1, ncx, cb);
+  if (rtab && blockIdx.x == 0) {
+    // the first column block of each group brings its frequencies' tables of
+    // the separator levels into L2 for the separator kernel (128-byte lines)
+    const int lines = (rtab_bytes + 127) / 128;
+    for (int q = threadIdx.x; q < G.nf * lines; q += kFourT) {
+      const int fr = q / lines, ln = q - fr * lines;
+      prefetch_l2(rtab + (size_t)G.freq(fr) * rtab_bytes + 128 * ln);
+    }
+  }
   dft_columns<L2, W, L, -1, SW>(S0, tw);
   if (G.pair) dft_columns<L2, W, L, -1, SW>(S1, tw);
 
@@ -234,7 +243,9 @@ k_fft4_forward2_solve(const cx<float> *__restrict__ inter, cx<float> *__restrict
     // first local value and the separator's partial right-hand side (the
     // last chunk has no separator)
     const cx<float> part = (p + 1 < nchunks) ? cfnms(sep, e, v[kFuseCH - 2]) : mk(0.f, 0.f);
-    sepbuf[(size_t)k * nchunks + p] = make_float4(v[0].re, v[0].im, part.re, part.im);
+    // kept in L2 for the separator kernel that reads it next
+    st_hint4(&sepbuf[(size_t)k * nchunks + p], make_float4(v[0].re, v[0].im, part.re, part.im),
+             pol_keep);
     v[kFuseCH - 1] = mk(0.f, 0.f);
   }
   __syncthreads();   // every read of S0/S1 is done: they become the staging rows
@@ -408,7 +419,8 @@ k_fft4_inverseA_correct(const cx<float> *__restrict__ spec, const cx<float> *__r
 template <int L, typename XT>
 cudaError_t four_forward_solve(int64_t n, int64_t n_pad, int nchunks, const XT *x, cx<float> *spec,
                                float4 *sepbuf, const cx<float> *tw, cudaStream_t s, void *inter,
-                               const float4 *tabs, int conj, int part = 0) {
+                               const float4 *tabs, int conj, int part = 0,
+                               const void *rtab = nullptr, int rtab_bytes = 0) {
   constexpr int L1 = Four<L>::L1, L2 = Four<L>::L2, W = kFourW;
   constexpr size_t sm1 = (size_t)L1 * W * sizeof(cx<float>);
   constexpr size_t sm2 = fuse_smem<L, kFwdPairs, 0>();
@@ -428,7 +440,8 @@ cudaError_t four_forward_solve(int64_t n, int64_t n_pad, int nchunks, const XT *
     if (e != cudaSuccess) return e;
     e = launch_pdl(k_fft4_forward2_solve<L, W>, dim3((unsigned)(ncx / W), L1 / 2 + 1),
                    dim3(kFourT), sm2, s, ip, spec, sepbuf, ncx, n_pad, nchunks, tw,
-                   four_discard_ok(ip, spec, n_pad) ? 1 : 0, tabs, conj);
+                   four_discard_ok(ip, spec, n_pad) ? 1 : 0, tabs, conj,
+                   static_cast<const char *>(rtab), rtab_bytes);
     note_launch();
     if (e != cudaSuccess) return e;
   }
