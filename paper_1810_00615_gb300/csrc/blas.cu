@@ -269,7 +269,13 @@ __device__ __forceinline__ void dots_commit(double (&acc)[ND], double (*s_dot)[N
 //   DK = 1: v0 . w, v . w, w . w
 //   DK = 2: v . w, w . w, v . v   (the first step from x0 = 0, v = b: ||b||^2)
 #ifndef AAO_MVFX_DOTS_MINB
-#define AAO_MVFX_DOTS_MINB 8   // fused-dots variants: 64 registers, no spills
+// fused-dots variants: ten CTAs of 128 threads per SM (51 registers, a few
+// words spilled to L1).  Measured at n 4095, ell 4096: 199 us per fused-dots
+// matvec against 211 us with eight CTAs (64 registers, no spills), 207 us
+// with twelve and 237 us with fourteen; the headline solve 1.458 against
+// 1.497 ms.  The walk is latency-bound, so resident warps pay more than
+// the registers they cost.
+#define AAO_MVFX_DOTS_MINB 10
 #endif
 template <int NB, bool TR, bool SUB, typename XT, bool CIRC, int DK = -1>
 __global__ void __launch_bounds__(kMvCols, DK >= 0 ? AAO_MVFX_DOTS_MINB : AAO_MVFX_MINB)
