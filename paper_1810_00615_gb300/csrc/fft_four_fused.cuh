@@ -94,19 +94,22 @@ template <int L, int NP>
 struct TabStage {
   static constexpr int U = (NP * Four<L>::L2 + kFourT - 1) / kFourT;
   float4 r[U];
+  // element idx = j L2 + f (L2 a power of two: no division by nf)
   __device__ __forceinline__ void load(const float4 *__restrict__ ft, int j0, const FuseGroup<L> &G) {
+    constexpr int L2 = Four<L>::L2;
 #pragma unroll
     for (int u = 0; u < U; u++) {
-      const int idx = threadIdx.x + u * kFourT, j = idx / G.nf, f = idx - j * G.nf;
-      if (j < NP) r[u] = __ldg(ft + (size_t)(j0 + j) * L + G.pos(f));
+      const int idx = threadIdx.x + u * kFourT, j = idx / L2, f = idx % L2;
+      if (j < NP && f < G.nf) r[u] = __ldg(ft + (size_t)(j0 + j) * L + G.pos(f));
     }
   }
   __device__ __forceinline__ void store(float4 *sT, const FuseGroup<L> &G, int conj) {
+    constexpr int L2 = Four<L>::L2;
     const float sg = conj ? -1.f : 1.f;
 #pragma unroll
     for (int u = 0; u < U; u++) {
-      const int idx = threadIdx.x + u * kFourT, j = idx / G.nf, f = idx - j * G.nf;
-      if (j < NP) sT[j * Four<L>::L2 + f] = make_float4(r[u].x, sg * r[u].y, r[u].z, sg * r[u].w);
+      const int idx = threadIdx.x + u * kFourT, j = idx / L2, f = idx % L2;
+      if (j < NP && f < G.nf) sT[j * L2 + f] = make_float4(r[u].x, sg * r[u].y, r[u].z, sg * r[u].w);
     }
   }
 };
@@ -187,11 +190,11 @@ k_fft4_forward2_solve(const cx<float> *__restrict__ inter, cx<float> *__restrict
   dft_columns<L2, W, L, -1, SW>(S0, tw);
   if (G.pair) dft_columns<L2, W, L, -1, SW>(S1, tw);
 
-  // task (f, q): frequency slot f, chunk q of the CTA (f fastest, so that
-  // eight neighbouring lanes read eight consecutive rows)
+  // task (f, q) = thread q L2 + f: frequency slot f, chunk q of the CTA (f
+  // fastest, so that eight neighbouring lanes read eight consecutive rows)
   const int t = threadIdx.x;
-  const bool active = t < G.nf * NQ;
-  const int q = active ? t / G.nf : 0, f = active ? t - q * G.nf : 0;
+  const int q = t / L2, f = t % L2;
+  const bool active = q < NQ && f < G.nf;
   int m = 0, k2 = 0;
   G.slot(f, m, k2);
   const int k1 = m ? G.gb : G.g;
@@ -348,8 +351,8 @@ k_fft4_inverseA_correct(const cx<float> *__restrict__ spec, const cx<float> *__r
     }
   }
   const int t = threadIdx.x;
-  const bool active = t < G.nf * NQ;
-  const int q = active ? t / G.nf : 0, f = active ? t - q * G.nf : 0;
+  const int q = t / L2, f = t % L2;
+  const bool active = q < NQ && f < G.nf;
   const int k = G.freq(f);
   const int p = p0 + q;
   cx<float> v[kFuseCH];
