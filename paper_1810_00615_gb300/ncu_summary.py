@@ -98,9 +98,23 @@ def _bytes(rec, metric):
     return None if x is None else x * BYTES.get(u, 1.0)
 
 
+def _strip_params(name: str) -> str:
+    """Drop a trailing parameter list '(...)' (balanced, so that template
+    arguments such as '(int)-1' stay)."""
+    n = name.rstrip()
+    if not n.endswith(")"):
+        return n
+    depth = 0
+    for i in range(len(n) - 1, -1, -1):
+        depth += {")": 1, "(": -1}.get(n[i], 0)
+        if depth == 0:
+            return n[:i]
+    return n
+
+
 def short_name(name: str) -> str:
     """'void fft::<unnamed>::k_x<4096, 32>(...)' -> 'k_x<4096, 32>'."""
-    n = re.sub(r"\(.*$", "", name)
+    n = _strip_params(name)
     n = re.sub(r"^void\s+", "", n).replace("<unnamed>::", "")
     base = n[:n.index("<")] if "<" in n else n
     return base.split("::")[-1] + n[len(base):]

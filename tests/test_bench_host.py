@@ -36,6 +36,24 @@ def test_profile_figures_are_taken_only_for_the_current_kernel_code(tmp_path, mo
     assert bench._profile_value("dram_bytes_per_launch", "no_such_kernel") is None
 
 
+def test_roofline_kernel_is_read_from_the_current_launch_list(tmp_path, monkeypatch):
+    """The kernel shares that pick the roofline line come from a launch list
+    of the current kernel code only."""
+    from paper_1810_00615_gb300 import _build
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    table = ("| kernel | launches | total us | mean us | share |\n|---|---|---|---|---|\n"
+             "| `k_matvec_fx<2, 0, 1, double, 0, 1>` | 2 | 324.5 | 162.2 | 11.3% |\n"
+             "| `k_fft4_inverseA_correct<4096, 32>` | 8 | 318.8 | 39.8 | 11.1% |\n")
+    (prof / "launches_x.md").write_text(f"source_digest: {_build._digest()}\n\n" + table)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    got = bench._launch_list_shares()
+    assert got == {"k_matvec_fx<2, 0, 1, double, 0, 1>": pytest.approx(0.113),
+                   "k_fft4_inverseA_correct<4096, 32>": pytest.approx(0.111)}
+    (prof / "launches_x.md").write_text("source_digest: 0123abcd\n\n" + table)
+    assert bench._launch_list_shares() == {}
+
+
 class _FakeProc:
     def terminate(self):
         pass
