@@ -61,13 +61,17 @@ __device__ __forceinline__ float to_f32(double x) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
   const unsigned e = (hi >> 20) & 0x7ffu;
-  const unsigned sign = hi & 0x80000000u;
-  if (e == 0u) return __uint_as_float(sign);          // zero or FP64 subnormal
-  if (e - 897u > 253u) return __double2float_rn(x);   // outside FP32 normals
-  unsigned bits = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  if (e - 897u > 253u) {                              // outside FP32 normals
+    if (e == 0u) return __uint_as_float(hi & 0x80000000u);   // zero or FP64 subnormal
+    return __double2float_rn(x);
+  }
+  // exponent and top 23 mantissa bits: (hi:lo) << 3 keeps the exponent's
+  // low nine bits at 23..31, and subtracting 896 << 23 (mod 2^32) rebiases
+  // it (1 <= e - 896 <= 254 here, so bit 31 ends up clear)
+  unsigned bits = __funnelshift_l(lo, hi, 3) - 0xC0000000u;
   const unsigned rem = lo & 0x1fffffffu;              // 29 dropped bits
-  bits += (rem > 0x10000000u) | ((rem == 0x10000000u) & (bits & 1u));
-  return __uint_as_float(sign | bits);
+  bits += (rem + (bits & 1u)) > 0x10000000u ? 1u : 0u;   // to nearest, ties to even
+  return __uint_as_float(bits | (hi & 0x80000000u));
 }
 
 __device__ __forceinline__ double to_f64(float f) {

@@ -616,9 +616,10 @@ __device__ __forceinline__ void split_f64(double x, float &hi, float &lo) {
     lo = 0.f;
     return;
   }
-  unsigned bits = ((e - 896u) << 23) | ((w & 0xfffffu) << 3) | (l >> 29);
+  // exponent (rebiased, mod 2^32) and top 23 mantissa bits in one funnel shift
+  unsigned bits = __funnelshift_l(l, w, 3) - 0xC0000000u;
   int rem = (int)(l & 0x1fffffffu);    // the 29 bits below hi's last place
-  const bool up = rem > (1 << 28) || (rem == (1 << 28) && (bits & 1u));
+  const bool up = (unsigned)rem + (bits & 1u) > (1u << 28);   // to nearest, ties to even
   bits += up ? 1u : 0u;
   if (up) rem -= (1 << 29);
   hi = __uint_as_float(sign | bits);
