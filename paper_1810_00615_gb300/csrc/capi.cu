@@ -785,6 +785,10 @@ cudaError_t neumann(Ctx &c, int terms, const double *x, YT *y, int tr, cudaStrea
   return cudaSuccess;
 }
 
+// Pieces of the host-buffer solve's final combination x = Z y, each copied
+// to the host as soon as it is written.
+constexpr int64_t kCopyPieces = 8;
+
 // Flexible GMRES(m), right preconditioning, FP64 Arnoldi.
 //
 // Shifted Arnoldi: with a good circulant, A P^{-1} is close to the identity,
@@ -1116,18 +1120,37 @@ int solve_core(Ctx &c, int tr, const double *b, double *x, int m, double rtol, i
     for (int i = 0; i < jd; i++) hs[480 + i] = y[(size_t)i] * sc[(size_t)i];   // z_i = sc_i Z_i
     AAO_CK(c, cudaMemcpyAsync(d_y, hs + 480, jd * sizeof(double), cudaMemcpyHostToDevice, s));
     if (copy_pending) AAO_CK(c, cudaStreamWaitEvent(s, c.ev_copy, 0));   // x is read by it
-    AAO_CK(c, run(c, AAO_K_COMBINE, s, [&] {
-      return zf ? aao::launch_combine(Zf.data(), jd, d_y, x, N, s, x_unset)
-                : aao::launch_combine(Z.data(), jd, d_y, x, N, s, x_unset);
-    }));
-    if (jd > 0) x_unset = false;
     if (x_host && jd > 0) {
-      AAO_CK(c, cudaEventRecord(c.ev_x, s));
-      AAO_CK(c, cudaStreamWaitEvent(c.copy_stream, c.ev_x, 0));
-      AAO_CK(c, cudaMemcpyAsync(x_host, x, vb, cudaMemcpyDeviceToHost, c.copy_stream));
+      // x = Z y in kCopyPieces pieces, each sent to the host as soon as it
+      // is written, so the copy (bound by the host link) overlaps the rest
+      // of the combination as well as the true-residual check after it
+      const int64_t per = round_up((size_t)((N + kCopyPieces - 1) / kCopyPieces), 32);
+      std::vector<const double *> Zp((size_t)jd);
+      std::vector<const float *> Zfp((size_t)jd);
+      for (int64_t off = 0; off < N; off += per) {
+        const int64_t cnt = std::min<int64_t>(per, N - off);
+        for (int i = 0; i < jd; i++) {
+          if (zf) Zfp[(size_t)i] = Zf[(size_t)i] + off;
+          else Zp[(size_t)i] = Z[(size_t)i] + off;
+        }
+        AAO_CK(c, run(c, AAO_K_COMBINE, s, [&] {
+          return zf ? aao::launch_combine(Zfp.data(), jd, d_y, x + off, cnt, s, x_unset)
+                    : aao::launch_combine(Zp.data(), jd, d_y, x + off, cnt, s, x_unset);
+        }));
+        AAO_CK(c, cudaEventRecord(c.ev_x, s));
+        AAO_CK(c, cudaStreamWaitEvent(c.copy_stream, c.ev_x, 0));
+        AAO_CK(c, cudaMemcpyAsync(x_host + off, x + off, (size_t)cnt * sizeof(double),
+                                  cudaMemcpyDeviceToHost, c.copy_stream));
+      }
       AAO_CK(c, cudaEventRecord(c.ev_copy, c.copy_stream));
       copy_pending = host_current = true;
+    } else {
+      AAO_CK(c, run(c, AAO_K_COMBINE, s, [&] {
+        return zf ? aao::launch_combine(Zf.data(), jd, d_y, x, N, s, x_unset)
+                  : aao::launch_combine(Z.data(), jd, d_y, x, N, s, x_unset);
+      }));
     }
+    if (jd > 0) x_unset = false;
     restarts++;
   }
   if (x_unset) {                                          // stopped before the first update
