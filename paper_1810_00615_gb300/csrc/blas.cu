@@ -9,6 +9,7 @@
 // deterministic: fixed per-block order, then a fixed-order pass over the
 // block partials.
 #include "aao_internal.cuh"
+#include <type_traits>
 
 namespace aao {
 
@@ -385,6 +386,11 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
   const double *pv = SUB ? pv0 + kPre * step : nullptr;
   const double *pd = (DK == 1) ? pd0 + kPre * step : nullptr;
   double *py = y + (int64_t)t0 * n + ic;
+  // FULL: every column of the warp and every walked step lie inside the
+  // system (no per-step range checks); RNG: results below or above the FP64
+  // normal range are possible (FP64 input with an extreme tile exponent)
+  auto walk = [&](auto full_c, auto rng_c) {
+  constexpr bool FULL = decltype(full_c)::value, RNG = decltype(rng_c)::value;
   long long q1 = 0, q2 = 0, q3 = 0;             // q of the previous steps walked
 #pragma unroll 1
   for (int kb = 0; kb < IN; kb += kPre) {
@@ -397,9 +403,10 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
       {
         const int tn = t + kPre * dir;
         const bool inb = k + kPre < IN;
-        zpre[u] = (inb && z_ok(tn)) ? __ldg(zaddr(tn, pz)) : (XT)0;
-        if (SUB) vpre[u] = (inb && col_ok && t_ok(tn)) ? __ldg(pv) : 0.0;
-        if (DK == 1) dpre[u] = (inb && col_ok && t_ok(tn)) ? __ldg(pd) : 0.0;
+        const bool vin = inb && (FULL || (col_ok && t_ok(tn)));
+        zpre[u] = (inb && (FULL || z_ok(tn))) ? __ldg(FULL ? pz : zaddr(tn, pz)) : (XT)0;
+        if (SUB) vpre[u] = vin ? __ldg(pv) : 0.0;
+        if (DK == 1) dpre[u] = vin ? __ldg(pd) : 0.0;
         pz += step;
         if (SUB) pv += step;
         if (DK == 1) pd += step;
@@ -411,7 +418,7 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
       if (lane == 31) Xr = s_halo[warp][1][k < IN ? k : 0];
       const long long P = Xl + Xr;
       const long long q = 4 * X + P;
-      if (k >= NB - 1 && k < IN && col_ok && t_ok(t)) {
+      if (k >= NB - 1 && k < IN && (FULL || (col_ok && t_ok(t)))) {
         long long sm;
         if (NB == 2) {
           sm = q - q1;
@@ -433,8 +440,7 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
         const unsigned long long so_abs = ((unsigned long long)s_oth ^ so_neg) - so_neg;
         const long long prod = (long long)__umul64hi(so_abs, rw.frac);
         const long long T = s_main + (so_neg ? -prod : prod);
-        constexpr bool RANGE = sizeof(XT) == 8;
-        const double td = fx_to_f64<RANGE>(T, unit);
+        const double td = fx_to_f64<RNG>(T, unit);
         const double yv = SUB ? fma(rw.coef, td, -vk) : rw.coef * td;
         py[(int64_t)k * step] = yv;
         if constexpr (DK == 1) {
@@ -452,6 +458,14 @@ k_matvec_fx(const XT *__restrict__ x, double *__restrict__ y, int n, int ell,
       q1 = q;
     }
   }
+  };
+  // |S| < 2^63, so S 2^unit stays a normal FP64 number or zero for
+  // -1022 <= unit <= 960; FP32 input always does
+  constexpr bool RANGE = sizeof(XT) == 8;
+  const bool in_range = !RANGE || (unit >= -1022 && unit <= 960);
+  const bool full = iw + 31 < n && t_min >= 0 && t_max < ell;   // the same for the warp
+  if (full && in_range) walk(std::true_type{}, std::false_type{});
+  else walk(std::false_type{}, std::integral_constant<bool, RANGE>{});
   if constexpr (DK >= 0) dots_commit<ND, kWarps>(dacc, s_dot, &s_cnt, dpart);
 }
 
