@@ -350,7 +350,9 @@ int aao_workspace_check(aao_ctx *ctx, int64_t *damaged);
  *     FP32; larger systems get AAO_EINVAL and aao_last_error says why.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept per device and CUDA
+ *     context, so the first call in a new context (e.g. after
+ *     cudaDeviceReset) looks it up again.
  *   - All calls on a device share the one array and leave their spectrum in
  *     it.  Nothing needs to start at zero (every call overwrites what it
  *     reads), but two calls whose kernels overlap on the GPU (different
