@@ -263,12 +263,14 @@ k_fft4_forward2_solve(const cx<float> *__restrict__ inter, cx<float> *__restrict
   // clipped to the row's 16 P values
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rowlen = 16 * nchunks - 2 * cb;                 // values of this CTA's segment
-  for (int fr = warp; fr < G.nf; fr += kFourT / 32) {
-    const int kr = G.freq(fr);
-    if (2 * lane < rowlen) {
+  constexpr int NR = (L2 + kFourT / 32 - 1) / (kFourT / 32);   // rows per warp, at most
+#pragma unroll
+  for (int u = 0; u < NR; u++) {
+    const int fr = warp + u * (kFourT / 32);
+    if (fr < G.nf && 2 * lane < rowlen) {
       const float4 val = *reinterpret_cast<const float4 *>(T + fr * TWS + 2 * lane);
-      st_hint4(reinterpret_cast<float4 *>(spec + (size_t)kr * n_pad + 2 * cb + 2 * lane), val,
-               pol_keep);
+      st_hint4(reinterpret_cast<float4 *>(spec + (size_t)G.freq(fr) * n_pad + 2 * cb + 2 * lane),
+               val, pol_keep);
     }
   }
 }
@@ -403,17 +405,34 @@ k_fft4_inverseA_correct(const cx<float> *__restrict__ spec, const cx<float> *__r
   if (G.pair) dft_columns<L2, W, L, +1, SW>(S1, tw);
   // two adjacent columns per thread: one 16-byte read, one twiddle, one
   // 16-byte store
-  constexpr int HW = W / 2;
-  for (int e = threadIdx.x; e < 2 * L2 * HW; e += kFourT) {
-    const int mm = e / (L2 * HW);
+  // (the loop is unrolled in batches so that the twiddle loads of a batch
+  // are in flight together, not one per iteration)
+  constexpr int HW = W / 2, NE = L2 * HW / kFourT;   // pairs per thread and member
+  static_assert(NE >= 1 && (L2 * HW) % kFourT == 0, "whole pairs per thread");
+  constexpr int NBT = NE < 4 ? NE : 4;
+#pragma unroll
+  for (int mm = 0; mm < 2; mm++) {
     if (mm == 1 && !G.pair) break;
-    const int r = e - mm * L2 * HW, t2 = r / HW, c = 2 * (r - t2 * HW);
     const int kk1 = mm ? G.gb : G.g;
-    const float4 v2 = *reinterpret_cast<const float4 *>((mm ? S1 : S0) + t2 * SW + c);
-    const cx<float> w = tw[t2 * kk1];
-    st_hint2(inter + ((size_t)kk1 * L2 + t2) * ncx + cb + c,
-             twiddle<float, +1>(mk(v2.x, v2.y), w), twiddle<float, +1>(mk(v2.z, v2.w), w),
-             pol_keep);
+    const cx<float> *Sm = mm ? S1 : S0;
+#pragma unroll
+    for (int u0 = 0; u0 < NE; u0 += NBT) {
+      float4 v2[NBT];
+      cx<float> w[NBT];
+#pragma unroll
+      for (int u = 0; u < NBT; u++) {
+        const int r = threadIdx.x + (u0 + u) * kFourT, t2 = r / HW, c = 2 * (r - t2 * HW);
+        v2[u] = *reinterpret_cast<const float4 *>(Sm + t2 * SW + c);
+        w[u] = tw[t2 * kk1];
+      }
+#pragma unroll
+      for (int u = 0; u < NBT; u++) {
+        const int r = threadIdx.x + (u0 + u) * kFourT, t2 = r / HW, c = 2 * (r - t2 * HW);
+        st_hint2(inter + ((size_t)kk1 * L2 + t2) * ncx + cb + c,
+                 twiddle<float, +1>(mk(v2[u].x, v2[u].y), w[u]),
+                 twiddle<float, +1>(mk(v2[u].z, v2[u].w), w[u]), pol_keep);
+      }
+    }
   }
 }
 
