@@ -42,15 +42,19 @@ HEADLINE_PREC = "fp32_refined"
 PREC_LABEL = {"fp32_refined": "fp32 circulant + one refinement sweep",
               "fp32": "fp32 circulant", "fp64": "fp64 circulant"}
 L2_BYTES = 135528448
-# ncu summary keys of the two kernels the roofline line is taken on: the
-# corrections + first inverse kernel of the FP32 apply and the fixed-point
-# matvec with the second Arnoldi step's dots fused.  Which of the two is the
-# "roofline" (the other stays beside it) is read from the committed launch
-# list of the timed region: the one with the larger share there.
+# ncu summary keys of the three kernels the roofline line is taken on: the
+# corrections + first inverse kernel of the FP32 apply, the fixed-point
+# matvec with the second Arnoldi step's dots fused, and the compensated
+# circulant residual of the refined apply (each about 11% of the headline
+# solve's kernel time).  Which one is the "roofline" (the others stay beside
+# it) is read from the committed launch list of the timed region: the one
+# with the largest share there.
 ROOFLINE_KEY = "fft4_inverseA_correct"
 MATVEC_KEY = "matvec_dots1_double"
+RESIDUAL_KEY = "circ_residual_df"
 DOMINANT_NAMES = {"k_fft4_inverseA_correct<4096, 32>": "correction",
-                  "k_matvec_fx<2, 0, 1, double, 0, 1>": "matvec"}
+                  "k_matvec_fx<2, 0, 1, double, 0, 1>": "matvec",
+                  "k_circ_residual_df<2, 0, float>": "residual"}
 
 
 def _peaks():
@@ -821,25 +825,44 @@ def run_gpu(args):
                        "busiest_pipe": ({"pipe": _profile_value_text("busiest_pipe_name",
                                                                      MATVEC_KEY),
                                          "pct_active": mpipe} if mpipe else None)}
-    # the roofline line is the kernel with the larger share of the committed
+    # the compensated circulant residual of the refined apply (two launches
+    # per headline solve), timed by the 'refine' class of the solve profile:
+    # z0 (FP32) and x (FP64) read, r (FP32) written = 16 B per element
+    rf_ms, rf_n = prof.get("refine", (0.0, 0))
+    rf_s = rf_ms * 1e-3 / rf_n if rf_n else None
+    rf_bytes = Nel * (4 + 8 + 4)
+    rpipe = _profile_value("busiest_pipe_pct", RESIDUAL_KEY)
+    roofline_residual = {"bound": "hbm",
+                         "kernel": "k_circ_residual_df: r = P z0 - x in compensated FP32 "
+                                   "(refined apply)",
+                         "achieved": round(rf_bytes / rf_s / 1e9, 1) if rf_s else None,
+                         "peak": hbm_peak, "unit": "GB/s",
+                         "frac": round(rf_bytes / rf_s / 1e9 / hbm_peak, 4) if rf_s else None,
+                         "traffic": _traffic(RESIDUAL_KEY),
+                         "us": round(rf_s * 1e6, 1) if rf_s else None,
+                         "algorithmic_bytes": rf_bytes,
+                         "busiest_pipe": ({"pipe": _profile_value_text("busiest_pipe_name",
+                                                                       RESIDUAL_KEY),
+                                           "pct_active": rpipe} if rpipe else None)}
+    # the roofline line is the kernel with the largest share of the committed
     # timed-region launch list (ncu, cold-cache shares); without a current
-    # list, the one with the longer time per headline solve here
+    # list, the one with the longest time per headline solve here
+    cands = {"correction": (roofline, "roofline_correction_kernel"),
+             "matvec": (roofline_matvec, "roofline_matvec_dots"),
+             "residual": (roofline_residual, "roofline_circ_residual")}
     lshares = _launch_list_shares()
     sh = {DOMINANT_NAMES[k]: v for k, v in lshares.items() if k in DOMINANT_NAMES}
-    roofline["launch_list_share"] = sh.get("correction")
-    roofline_matvec["launch_list_share"] = sh.get("matvec")
+    for name, (d, _key) in cands.items():
+        d["launch_list_share"] = sh.get(name)
+        d["chosen_by"] = "ncu launch list share" if sh else "time per headline solve"
     if sh:
         pick = max(sh, key=sh.get)
-        roofline_matvec["chosen_by"] = roofline["chosen_by"] = "ncu launch list share"
-    else:
-        per_solve_sia = 4 * (sia_s or 0.0)          # four FP32 applies per headline solve
-        pick = "matvec" if 2 * mv_s > per_solve_sia else "correction"
-        roofline_matvec["chosen_by"] = roofline["chosen_by"] = "time per headline solve"
-    if pick == "matvec":
-        roofline, roofline_other, roofline_other_key = (roofline_matvec, roofline,
-                                                        "roofline_correction_kernel")
-    else:
-        roofline_other, roofline_other_key = roofline_matvec, "roofline_matvec_dots"
+    else:   # per headline solve: 4 applies, 2 fused-dots matvecs, 2 residuals
+        per_solve = {"correction": 4 * (sia_s or 0.0), "matvec": 2 * mv_s,
+                     "residual": 2 * (rf_s or 0.0)}
+        pick = max(per_solve, key=per_solve.get)
+    roofline = cands[pick][0]
+    roofline_others = {key: d for name, (d, key) in cands.items() if name != pick}
     # the preconditioner apply against the same roofline: 32 B per element
     # (the three-pass accounting of the method's preconditioner) and the
     # irreducible 16 B per element (x read, y written)
@@ -903,7 +926,7 @@ def run_gpu(args):
                                       "note": "FP32 apply, compensated FP32 circulant residual, FP32 "
                                               "correction; FP64 output"},
             "kernel_share": shares, "solve_kernels": solve_kernels, "roofline": roofline,
-            roofline_other_key: roofline_other, "roofline_precond_apply": apply_roof,
+            **roofline_others, "roofline_precond_apply": apply_roof,
             "cpu_baseline": cpu,
             "cpu_references": cpu_refs,
             "e2e": {"value": e2e_v, "unit": "s", "h2d_bytes_per_step": 8 * N_SPACE,

@@ -335,6 +335,12 @@ struct CircDF {
   float hi[4][2];
   float lo[4][2];
   int taps;
+  // the same stencil as P z_t = mh sum_j a_j q_{t-j} + bp k_t with q = z_{i-1}
+  // + 4 z_i + z_{i+1}, k = 2 z_i - z_{i-1} - z_{i+1} and the integer time
+  // weights a_j of the equation (heat 1, -1; BD2 1, -2, 1; BD4 2, -5, 4, -1):
+  // mh = h/6 and bp as FP32 hi + lo pairs
+  float mh_hi, mh_lo, bp_hi, bp_lo;
+  int int_weights;   // 1 where the a_j are those integers (not the literal heat form)
 };
 
 // ------------------------------------------------------------ context

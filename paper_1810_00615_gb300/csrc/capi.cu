@@ -491,6 +491,11 @@ int refresh_constants(Ctx &c) {
         cf.lo[j][q] = (float)(cc[q] - (double)cf.hi[j][q]);
       }
     }
+    cf.mh_hi = (float)mh;
+    cf.mh_lo = (float)(mh - (double)cf.mh_hi);
+    cf.bp_hi = (float)bp;
+    cf.bp_lo = (float)(bp - (double)cf.bp_hi);
+    cf.int_weights = c.equation == AAO_HEAT_LITERAL ? 0 : 1;
     c.circ_df = cf;
   }
   // fixed-point matvec output stages for A (per step) and P (constant step)
