@@ -54,7 +54,7 @@ MATVEC_KEY = "matvec_dots1_double"
 RESIDUAL_KEY = "circ_residual_df"
 DOMINANT_NAMES = {"k_fft4_inverseA_correct<4096, 32>": "correction",
                   "k_matvec_fx<2, 0, 1, double, 0, 1>": "matvec",
-                  "k_circ_residual_df<2, 0, float>": "residual"}
+                  "k_circ_residual_q<2, 0, float>": "residual"}
 
 
 def _peaks():
@@ -833,7 +833,7 @@ def run_gpu(args):
     rf_bytes = Nel * (4 + 8 + 4)
     rpipe = _profile_value("busiest_pipe_pct", RESIDUAL_KEY)
     roofline_residual = {"bound": "hbm",
-                         "kernel": "k_circ_residual_df: r = P z0 - x in compensated FP32 "
+                         "kernel": "k_circ_residual_q: r = P z0 - x in compensated FP32 "
                                    "(refined apply)",
                          "achieved": round(rf_bytes / rf_s / 1e9, 1) if rf_s else None,
                          "peak": hbm_peak, "unit": "GB/s",
